@@ -1,0 +1,272 @@
+"""Exact upwind diagonal-norm dual-pair SBP operators (oracle).
+
+Test infrastructure only; see ``oracle/__init__.py``.
+
+Definition (Section 4.1, Eq. upw_SBP and the Definition that follows it): a
+triple (H, D-, D+) on n+1 nodes with H diagonal and positive,
+
+    (D+ f)^T H g + f^T H (D- g) = f_n g_n - f_0 g_0       for all f, g,
+
+i.e. H D+ + D-^T H = B with B = diag(-1, 0, ..., 0, 1), and with
+D+ + D+^T negative semi-definite.  Order 2p (Eq. acc and the paragraph after
+it): D(xi^m) = m xi^(m-1) for m <= 2p at interior rows and m <= p in the
+closure rows.
+
+The paper gives only the interior stencils (Table 1, Section 6.2) and cites
+Mattsson (2017) for the closures.  Readings taken here (every one is checked
+by tests/test_oracle_operators.py):
+
+* Interior rows of D+ are Table 1's alpha_j at offsets -r..q; interior rows of
+  D- use beta_j = -alpha_{-j} (Section 6.2).
+* Table 1 prints alpha_4 = 1/28 for order 8; with that sign the stencil is not
+  consistent (sum 1/14), with -1/28 every moment up to 8 holds.  The table
+  below carries -1/28.
+* D- is the mirror image of D+: D- = -J D+ J with J the index reversal, which
+  is what beta_j = -alpha_{-j} says inside.
+* Write M = H D+ (so D+ = H^-1 M and, from the SBP relation,
+  D- = H^-1 (B - M^T)).  M equals the Toeplitz interior stencil everywhere
+  except in a b-by-b corner block at each end; the lower-right block follows
+  from the upper-left one through M - J M^T J = B.  The unknowns are the
+  upper-left block of M and the first b weights of H; the equations are the
+  closure-row accuracy conditions of D+ and of D- (degree <= p).
+* The solution has free parameters (none for order 2, one for order 4, four
+  for order 6 with b = 6).  They are fixed at the simple rationals in
+  CLOSURE below, chosen (numerically, once) to keep M + M^T - B negative
+  semi-definite and the spectral radius of D+ at the value of the interior
+  stencil.  These closures are therefore NOT Mattsson's published ones; they
+  satisfy the same defining properties.
+"""
+from fractions import Fraction as Fr
+
+import numpy as np
+
+# Table 1: interior coefficients alpha_j of D+ (interior order, r, q, alpha_-r..alpha_q).
+TABLE1 = {
+    2: (0, 2, ("-3/2", "2", "-1/2")),
+    3: (1, 2, ("-1/3", "-1/2", "1", "-1/6")),
+    4: (1, 3, ("-1/4", "-5/6", "3/2", "-1/2", "1/12")),
+    5: (2, 3, ("1/20", "-1/2", "-1/3", "1", "-1/4", "1/30")),
+    6: (2, 4, ("1/30", "-2/5", "-7/12", "4/3", "-1/2", "2/15", "-1/60")),
+    7: (3, 4, ("-1/105", "1/10", "-3/5", "-1/4", "1", "-3/10", "1/15", "-1/140")),
+    8: (3, 5, ("-1/168", "1/14", "-1/2", "-9/20", "5/4", "-1/2", "1/6", "-1/28", "1/280")),
+    9: (4, 5, ("1/504", "-1/42", "1/7", "-2/3", "-1/5", "1", "-1/3", "2/21", "-1/56", "1/630")),
+}
+
+# Table 2: interior coefficients gamma_1..gamma_q of the traditional central SBP operator.
+TABLE2 = {
+    2: ("1/2",),
+    4: ("2/3", "-1/12"),
+    6: ("3/4", "-3/20", "1/60"),
+    8: ("4/5", "-1/5", "4/105", "-1/280"),
+}
+
+# Closure width b and the chosen values of the free entries of M = H D+ (upper-left block).
+CLOSURE = {
+    2: dict(b=2, free={}),
+    4: dict(b=4, free={(3, 3): Fr(-4, 5)}),
+    6: dict(b=6, free={(4, 4): Fr(-17, 25), (4, 5): Fr(131, 100),
+                       (5, 4): Fr(-29, 100), (5, 5): Fr(-3, 5)}),
+}
+
+
+def interior_stencil(order):
+    """alpha_j of Table 1 as {offset j: Fraction}."""
+    r, q, coeffs = TABLE1[order]
+    return {j: Fr(c) for j, c in zip(range(-r, q + 1), coeffs)}
+
+
+def interior_stencil_minus(order):
+    """beta_j = -alpha_{-j}, the interior stencil of D- (Section 6.2)."""
+    return {-j: -a for j, a in interior_stencil(order).items()}
+
+
+def _solve_exact(rows, rhs, nunk):
+    """Solve the linear system rows @ u = rhs exactly (Fractions, Gauss-Jordan).
+
+    Raises ValueError when the system is inconsistent or leaves unknowns free.
+    """
+    A = [list(r) + [b] for r, b in zip(rows, rhs)]
+    piv_cols = []
+    row = 0
+    for col in range(nunk):
+        pr = next((i for i in range(row, len(A)) if A[i][col] != 0), None)
+        if pr is None:
+            continue
+        A[row], A[pr] = A[pr], A[row]
+        p = A[row][col]
+        A[row] = [x / p for x in A[row]]
+        for i in range(len(A)):
+            if i != row and A[i][col] != 0:
+                f = A[i][col]
+                A[i] = [x - f * y for x, y in zip(A[i], A[row])]
+        piv_cols.append(col)
+        row += 1
+    if any(all(x == 0 for x in A[i][:nunk]) and A[i][nunk] != 0 for i in range(len(A))):
+        raise ValueError("inconsistent closure system")
+    if len(piv_cols) != nunk:
+        raise ValueError(f"closure system leaves {nunk - len(piv_cols)} unknowns free")
+    u = [Fr(0)] * nunk
+    for i, col in enumerate(piv_cols):
+        u[col] = A[i][nunk]
+    return u
+
+
+def closure(order):
+    """Upper-left block Mc (b x b) of M = H D+ and the boundary weights w_0..w_{b-1}.
+
+    Unknowns: Mc[i][j] (i, j < b) and w_i.  Equations, for closure rows i < b and
+    degrees m = 0..p (p = order/2), on unit spacing xi_j = j:
+      D+ rows:  sum_j M[i, j] j^m            = m w_i i^(m-1)
+      D- rows:  sum_j (B - M^T)[i, j] j^m    = m w_i i^(m-1)
+    plus one equation per free parameter of CLOSURE.
+    """
+    alpha = interior_stencil(order)
+    b = CLOSURE[order]["b"]
+    p = order // 2
+    nunk = b * b + b
+
+    def mi(i, j):
+        return i * b + j
+
+    def wi(i):
+        return b * b + i
+
+    rows, rhs = [], []
+    for i in range(b):
+        for m in range(p + 1):
+            # D+ accuracy at row i
+            row = [Fr(0)] * nunk
+            const = Fr(0)
+            for j in range(b):
+                row[mi(i, j)] += Fr(j) ** m
+            for j in range(b, i + max(alpha) + 1):
+                if j - i in alpha:
+                    const += alpha[j - i] * Fr(j) ** m
+            if m >= 1:
+                row[wi(i)] -= m * Fr(i) ** (m - 1)
+            rows.append(row)
+            rhs.append(-const)
+            # D- accuracy at row i: (B - M^T)[i, j] = B[j, i] - M[j, i]
+            row = [Fr(0)] * nunk
+            const = Fr(-1) if (i == 0 and m == 0) else Fr(0)
+            for j in range(b):
+                row[mi(j, i)] -= Fr(j) ** m
+            for j in range(b, i - min(alpha) + 1):
+                if i - j in alpha:
+                    const -= alpha[i - j] * Fr(j) ** m
+            if m >= 1:
+                row[wi(i)] -= m * Fr(i) ** (m - 1)
+            rows.append(row)
+            rhs.append(-const)
+    for (i, j), v in CLOSURE[order]["free"].items():
+        row = [Fr(0)] * nunk
+        row[mi(i, j)] = Fr(1)
+        rows.append(row)
+        rhs.append(v)
+    u = _solve_exact(rows, rhs, nunk)
+    Mc = [[u[mi(i, j)] for j in range(b)] for i in range(b)]
+    w = [u[wi(i)] for i in range(b)]
+    return Mc, w
+
+
+def min_nodes(order):
+    """Fewest nodes per axis for which the two closures stay disjoint and every
+    closure row of D- reaches only pure-stencil rows of M (N >= 2b + max(r, q))."""
+    r, q, _ = TABLE1[order]
+    return 2 * CLOSURE[order]["b"] + max(r, q)
+
+
+def upwind_pair_exact(order, N):
+    """(H, Dm, Dp, M, B) on N nodes with unit spacing, as lists of Fractions.
+
+    H is the list of diagonal weights.  Dp = H^-1 M, Dm = H^-1 (B - M^T).
+    """
+    if order not in CLOSURE:
+        raise ValueError("closures are built for orders 2, 4, 6")
+    if N < min_nodes(order):
+        raise ValueError(f"order {order} needs at least {min_nodes(order)} nodes")
+    alpha = interior_stencil(order)
+    b = CLOSURE[order]["b"]
+    Mc, w = closure(order)
+    n = N - 1
+    M = [[Fr(0)] * N for _ in range(N)]
+    for i in range(N):
+        for k, a in alpha.items():
+            if 0 <= i + k < N:
+                M[i][i + k] = a
+    Bm = [[Fr(0)] * N for _ in range(N)]
+    Bm[0][0] = Fr(-1)
+    Bm[n][n] = Fr(1)
+    for i in range(b):
+        for j in range(b):
+            M[i][j] = Mc[i][j]
+    for i in range(b):
+        for j in range(b):
+            M[n - j][n - i] = Mc[i][j] - Bm[i][j]
+    H = [Fr(1)] * N
+    for i in range(b):
+        H[i] = w[i]
+        H[n - i] = w[i]
+    Dp = [[M[i][j] / H[i] for j in range(N)] for i in range(N)]
+    Dm = [[(Bm[i][j] - M[j][i]) / H[i] for j in range(N)] for i in range(N)]
+    return H, Dm, Dp, M, Bm
+
+
+def upwind_pair(order, N, length=1.0):
+    """Float64 (H, Dm, Dp) on N nodes spanning [0, length]: spacing h = length/(N-1).
+
+    Dm and Dp are scipy CSR matrices.  D+- scale as 1/h and H as h
+    (Section 4.1).  Rows b..N-1-b are Table 1's stencils (alpha_j for D+,
+    beta_j = -alpha_{-j} for D-); the b closure rows at each end are taken
+    from the exact operator on min_nodes(order) nodes, whose left rows do not
+    depend on N and whose right rows are the mirror images
+    D+[N-1-i, N-1-j] = -D-[i, j] (tests check this against
+    upwind_pair_exact for several N).
+    """
+    import scipy.sparse as sps
+    if N < min_nodes(order):
+        raise ValueError(f"order {order} needs at least {min_nodes(order)} nodes")
+    b = CLOSURE[order]["b"]
+    H0, Dm0, Dp0, _, _ = upwind_pair_exact(order, min_nodes(order))
+    alpha = interior_stencil(order)
+    beta = interior_stencil_minus(order)
+    h = length / (N - 1)
+    rows = {"p": ([], [], []), "m": ([], [], [])}
+    for name, D0, Dother0, st in (("p", Dp0, Dm0, alpha), ("m", Dm0, Dp0, beta)):
+        ri, ci, vi = rows[name]
+        for i in range(N):
+            if i < b:
+                ent = [(j, D0[i][j]) for j in range(len(D0)) if D0[i][j] != 0]
+            elif i > N - 1 - b:
+                ii = N - 1 - i
+                ent = [(N - 1 - j, -Dother0[ii][j]) for j in range(len(Dother0)) if Dother0[ii][j] != 0]
+            else:
+                ent = [(i + k, a) for k, a in st.items()]
+            for j, a in ent:
+                ri.append(i)
+                ci.append(j)
+                vi.append(float(a) / h)
+    Dp = sps.csr_matrix((rows["p"][2], (rows["p"][0], rows["p"][1])), shape=(N, N))
+    Dm = sps.csr_matrix((rows["m"][2], (rows["m"][0], rows["m"][1])), shape=(N, N))
+    Hf = np.ones(N)
+    for i in range(b):
+        Hf[i] = float(H0[i])
+        Hf[N - 1 - i] = float(H0[i])
+    return Hf * h, Dm, Dp
+
+
+def dispersion_upwind(order, k):
+    """Numerical dispersion relation of the interior upwind stencil, c_s = 1
+    (Section 6.2, Eq. dispersion_relation_upwind): |sum_j alpha_j e^{i j k}|."""
+    alpha = interior_stencil(order)
+    k = np.asarray(k, dtype=float)
+    re = sum(float(a) * np.cos(j * k) for j, a in alpha.items())
+    im = sum(float(a) * np.sin(j * k) for j, a in alpha.items())
+    return np.sqrt(re ** 2 + im ** 2)
+
+
+def dispersion_traditional(order, k):
+    """Eq. dispersion_relation_traditional, c_s = 1: |sum_j 2 gamma_j sin(j k)|."""
+    g = [Fr(c) for c in TABLE2[order]]
+    k = np.asarray(k, dtype=float)
+    return np.abs(sum(2 * float(gj) * np.sin((j + 1) * k) for j, gj in enumerate(g)))
