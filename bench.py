@@ -1,0 +1,336 @@
+"""Throughput of the fused RHS + Runge-Kutta stage on one GB300.
+
+Workload: 1025 x 1025 x 401 nodes (421M), order-6 upwind SBP, FP32, 60 x 60 x 24 km
+block with a seeded sum-of-sinusoids top surface (free) and absorbing faces
+elsewhere, von Karman perturbed gradient medium.  A step is one full
+Runge-Kutta step: five fused stages over every node (interior kernel + boundary
+slab kernel per stage).  Metric: million node-stage updates per second,
+nodes * 5 * steps / time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+One JSON line on rank 0.  With --gpus N > 1 (torchrun) every rank runs an
+independent replica of the workload on its own GPU ("replicas only": the
+single-block path has no exchange step) and the value is the sum over ranks.
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Mpoint-updates/s per RK stage"
+UNIT = "Mnode-stage/s"
+WORKLOAD = "topo1025_o6_fp32"
+BYTES_PER_NODE_STAGE = 192        # 48 FP32 values per node per stage (algorithmic)
+BYTES_PER_NODE_STAGE0 = 156       # first stage: A_0 = 0, the RK register is not read
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = max(mx, float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_step_sample(sub, stages=5):
+    """Time the FP64 oracle on a sub-block (the top `sub` nodes of the workload's grid, same map,
+    medium and spacing): `stages` Runge-Kutta stages.  Returns (node-stages, seconds)."""
+    import numpy as np
+
+    from oracle import rk
+    from oracle.elastic import Scheme, rhs
+    from oracle.metrics import metrics
+    from workloads.configs import config_by_name
+    from workloads.fields import smooth_state
+    from workloads.geometry import make_map
+    from workloads.media import make_medium
+    cfg = config_by_name(WORKLOAD)
+    nq, nr, ns = cfg.nodes
+    i, j, k = np.arange(sub[0]), np.arange(sub[1]), np.arange(ns - sub[2], ns)
+    fmap, fmed = make_map(cfg), make_medium(cfg)
+    X = [np.broadcast_to(c, (sub[2], sub[1], sub[0])).copy()
+         for c in fmap(i[None, None, :] / (nq - 1), j[None, :, None] / (nr - 1), k[:, None, None] / (ns - 1))]
+    mat = fmed(*X)
+    J, a = metrics(*X, cfg.order)
+    sch = Scheme(cfg.order, sub)
+    I, Jj, K = np.meshgrid(i, j, k, indexing="ij")
+    Q = np.stack(smooth_state(cfg.nodes, 11, I.T, Jj.T, K.T))
+    dQ = np.zeros_like(Q)
+    t0 = time.perf_counter()
+    for s in range(stages):
+        dQ *= rk.A[s]
+        dQ += 1e-3 * rhs(Q, sch, J, a, mat, cfg.bc)
+        Q += rk.B[s] * dQ
+    return sub[0] * sub[1] * sub[2] * stages, time.perf_counter() - t0
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    sub = (257, 33, 17)
+    n_per_step = 0
+    for _ in range(args.warmup):
+        oracle_step_sample(sub)
+    tot = 0.0
+    for _ in range(args.steps):
+        n, t = oracle_step_sample(sub)
+        n_per_step = n
+        tot += t
+    value = n_per_step * args.steps / tot / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": f"top {sub[0]}x{sub[1]}x{sub[2]} nodes of the workload, one RK step",
+                   "nodes": list(sub), "order": 6},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one 5-stage RK step on the top {sub[0]}x{sub[1]}x{sub[2]} nodes per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl != "reference" else "gloo"
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
+    if args.warmup < 3:
+        args.warmup = 3
+
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_02600_gb300 import _lib as L
+    from paper_2011_02600_gb300.solver import _stream
+    from paper_2011_02600_gb300.workload_setup import build_solver
+    from workloads.configs import config_by_name
+    from workloads.fields import gaussian_pulse
+
+    cfg = config_by_name(WORKLOAD)
+    s, info = build_solver(cfg, precision=32, device=f"cuda:{local}")
+    nq, nr, ns = cfg.nodes
+    nodes = nq * nr * ns
+    dt = info["dt"]
+    # initial state: a Gaussian velocity pulse at the centre of the block (timing workload)
+    Lx, Ly, Lz = cfg.extent
+    st = s.state()
+    dev = s.device
+    xs = torch.arange(nq, device=dev, dtype=torch.float64).view(1, 1, nq) * (Lx / (nq - 1))
+    ys = torch.arange(nr, device=dev, dtype=torch.float64).view(1, nr, 1) * (Ly / (nr - 1))
+    for k0 in range(0, ns, 32):
+        k1 = min(ns, k0 + 32)
+        zs = (-Lz + torch.arange(k0, k1, device=dev, dtype=torch.float64).view(-1, 1, 1) * (Lz / (ns - 1)))
+        vals = gaussian_pulse(xs, ys, zs, (Lx / 2, Ly / 2, -Lz / 2), cfg.extra["pulse_width"], xp=torch)
+        for f in range(9):
+            st[f, k0:k1].copy_(vals[f].expand(k1 - k0, nr, nq))
+    s.dq.zero_()
+    stream = torch.cuda.current_stream()
+    h = s.h
+    for _ in range(args.warmup):
+        L.sbp_step_n(h, 1, dt, _stream())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    L.sbp_kernel_timing(h, True)
+    L.sbp_kernel_times(h)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        L.sbp_step_n(h, 1, dt, _stream())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kms, kn = L.sbp_kernel_times(h)
+    L.sbp_kernel_timing(h, False)
+    clk = clocks.stop()
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    energy = s.energy()
+    bits = s.status()
+    ms_per_step = ms / args.steps
+    value = world * nodes * 5 * args.steps / (ms / 1e3) / 1e6
+
+    # dominant kernel: the tiled interior kernel if it ran, else the general kernel
+    b = 6
+    interior_nodes = max(0, nq - 2 * b) * max(0, nr - 2 * b) * max(0, ns - 2 * b)
+    if kn[0] > 0:
+        kind, launches, kms_tot, knodes = "interior", kn[0], kms[0], interior_nodes
+    else:
+        kind, launches, kms_tot, knodes = "general", kn[1], kms[1], nodes
+    # per launch: stage 0 reads no RK register; average over the 5 stages of a step
+    avg_bytes = knodes * (BYTES_PER_NODE_STAGE * 4 + BYTES_PER_NODE_STAGE0) / 5.0
+    avg_ms = kms_tot / max(1, launches)
+    achieved = avg_bytes / (avg_ms / 1e3) / 1e9
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    prof_traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic_per_launch.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            if tj.get("kernel_source_digest") == _kernel_digest():
+                prof_traffic = tj.get("dram_bytes_per_launch")
+        except Exception:
+            prof_traffic = None
+
+    # end to end: state in from pinned host memory, one step, state and energy out, per step
+    e2e = None
+    try:
+        nbytes = 9 * s.fs * 4
+        host_in = torch.empty(9 * s.fs, dtype=torch.float32, pin_memory=True)
+        host_out = torch.empty(9 * s.fs, dtype=torch.float32, pin_memory=True)
+        host_in.copy_(s.qbuf[s.current].cpu())
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(args.e2e_steps):
+            s.qbuf[s.current].copy_(host_in, non_blocking=True)
+            L.sbp_step_n(h, 1, dt, _stream())
+            host_out.copy_(s.qbuf[s.current], non_blocking=True)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        e_ms = ev[0].elapsed_time(ev[1]) / args.e2e_steps
+        e2e = {"value": nodes * 5 / (e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": e_ms,
+               "what": "per step: the 9-field FP32 state copied in from pinned host memory, one RK step "
+                       "through the C ABI, the state copied back to pinned host memory"}
+        del host_in, host_out
+    except Exception as ex:  # pinned memory can be unavailable
+        e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+               "error": str(ex)[:200]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        sub = (1025, 97, 33)
+        n, t = oracle_step_sample(sub)
+        cpu = {"value": n / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one 5-stage RK step of the FP64 oracle (numpy/scipy, one thread) on the top "
+                         f"{sub[0]}x{sub[1]}x{sub[2]} nodes of the workload ({t:.1f} s)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "nodes": list(cfg.nodes), "order": cfg.order,
+                   "extent_m": list(cfg.extent), "stages_per_step": 5, "dt_s": dt,
+                   "l2": "inputs larger than L2 (39 fields x 1.74 GB resident)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": prof_traffic, "kernel": kind,
+                     "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms,
+                     "launches": launches, "peak_source": "measured" if peaks else "fallback"},
+        "kernel_ms": {"interior": kms[0], "slabs_or_general": kms[1], "launches": kn},
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "e2e": e2e,
+        "gpu_launches": 10 * args.steps if kn[0] > 0 else 5 * args.steps,
+        "energy_after": energy, "status_bits": bits,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2011_02600_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    main()

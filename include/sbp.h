@@ -1,0 +1,188 @@
+/*
+ * sbp.h - C ABI of the GB300 upwind-SBP elastic wave library.
+ *
+ * The library evaluates the semi-discrete velocity-stress elastic wave
+ * equation on one boundary-conforming curvilinear block (Duru, Fung &
+ * Williams, arXiv 2011.02600):
+ *
+ *   P~^-1 dQ/dt = sum_xi D-_xi F_xi(Q) + sum_xi B_xi(D+_xi Q) + sum SAT     (Sections 4.2, 5)
+ *
+ * with the upwind SBP pair (H, D-, D+) of interior order 2, 4 or 6 along q, r
+ * and s (Section 4.1, Table 1), metric terms e_xi = J grad(xi) (Section 2.2),
+ * the free-surface penalty (Eq. SAT_free_surface) or the general penalty with
+ * parameter gamma (Eq. SAT_General) on each face, fused with the stages of the
+ * five-stage 2N-storage fourth-order Runge-Kutta scheme the paper uses
+ * (Carpenter & Kennedy 1994, cited in Sections 1 and 7).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Nodes: nq x nr x ns (n_xi + 1 per axis), reference coordinates xi_i = i/(N-1).
+ * Layout: a "field" is one scalar grid function stored [s][r][q] with q
+ *   contiguous, row pitch ldq elements (ldq >= nq, rows start on 128-byte
+ *   boundaries) and field stride fs elements (sbp_layout).  Element (i,j,k) of
+ *   field f of a buffer is at  base + f*fs + k*ldq*nr + j*ldq + i.
+ *   Padding elements are never read as data and may hold anything.
+ * State Q: 9 fields (vx, vy, vz, sxx, syy, szz, sxy, sxz, syz) (Section 2.1).
+ * Metrics (solver precision): 9 fields a[xi][eta] = J xi_eta, xi in (q,r,s),
+ *   eta in (x,y,z), stored in the order a_qx a_qy a_qz a_rx ... a_sz.
+ * Coefficients (solver precision): 3 fields 1/(rho J), lambda/J, mu/J.
+ * Faces: 0..5 = (q=0, q=1, r=0, r=1, s=0, s=1).
+ * Precision: 32 (float) or 64 (double) for the state, metrics and
+ *   coefficients; setup inputs are always double.
+ * Memory ownership: every buffer passed in is owned by the caller; the library
+ *   never frees it.  Device buffers must stay valid while a grid uses them.
+ *   The library allocates only small internal buffers (reduction partials,
+ *   source weights, receiver indices, a status word), freed by sbp_destroy.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Calls
+ *   are asynchronous unless stated; they return after enqueueing work.
+ * Errors: every function returns SBP_OK (0) or a positive code; the message of
+ *   the last failure on the calling thread is in sbp_last_error().  Invalid
+ *   arguments are rejected on the host before any work is enqueued.  No kernel
+ *   traps or asserts; device-side problems (non-finite state, non-positive
+ *   Jacobian or moduli) are recorded in a status word read by sbp_status.
+ */
+#ifndef SBP_GB300_H
+#define SBP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SBP_OK 0
+#define SBP_ERR_ARG 1          /* invalid argument (sizes, order, precision, pointers) */
+#define SBP_ERR_UNSUPPORTED 2  /* valid request the library does not implement */
+#define SBP_ERR_CUDA 3         /* a CUDA runtime call failed */
+#define SBP_ERR_NONFINITE 4    /* the state or a reduction is NaN/Inf */
+#define SBP_ERR_STATE 5        /* call out of sequence (e.g. stepping before sbp_bind) */
+#define SBP_ERR_MESH 6         /* non-positive Jacobian or invalid moduli found on the device */
+
+#define SBP_BC_FREE 0  /* free surface, Eq. SAT_free_surface */
+#define SBP_BC_CHAR 1  /* general condition with gamma, Eq. BC_General2 / Eq. SAT_General */
+
+/* Status bits reported by sbp_status (device-side findings). */
+#define SBP_STATUS_NONFINITE 1u
+#define SBP_STATUS_BAD_MESH 2u
+#define SBP_STATUS_BAD_MATERIAL 4u
+
+typedef struct SbpGridDesc {
+  int32_t nq, nr, ns;     /* nodes per axis; each >= sbp_min_nodes(order) */
+  int32_t order;          /* interior order of the upwind pair: 2, 4 or 6 */
+  int32_t precision;      /* 32 or 64 */
+  int32_t bc_kind[6];     /* SBP_BC_FREE or SBP_BC_CHAR per face */
+  double bc_gamma[6];     /* gamma in [-1, 1] for SBP_BC_CHAR faces (Eq. BC_General2) */
+} SbpGridDesc;
+
+typedef struct SbpGrid SbpGrid;
+
+/* Moment-tensor point source (Section 7.1, Eq. momententor_pointsource): the
+ * stress rates receive -M g(t) delta_h, delta_h = phi_q phi_r phi_s /(J H)
+ * with 1D weights on order+2 nodes satisfying the discrete moment conditions
+ * up to degree order+1.  stf: 0 = Ricker (f0, t0), 1 = t/T^2 exp(-t/T) (T). */
+typedef struct SbpSource {
+  double ref[3];          /* reference coordinates (q, r, s) in [0,1] of the source */
+  double moment[6];       /* Mxx, Myy, Mzz, Mxy, Mxz, Myz (N m) */
+  int32_t stf;            /* 0 Ricker, 1 LOH1-type */
+  double f0, t0, T;       /* Ricker peak frequency and delay; LOH1 time constant */
+} SbpSource;
+
+/* Smallest node count per axis for an order: 2b + max(r, q) (b closure rows). */
+int sbp_min_nodes(int32_t order, int32_t* out);
+
+/* Validate desc and create a grid handle (host memory only).  ARG on bad sizes,
+ * order, precision, face kinds or gamma outside [-1, 1]. */
+int sbp_create_grid(const SbpGridDesc* desc, SbpGrid** out);
+
+/* Free the handle and the library's internal buffers (not the caller's). */
+int sbp_destroy(SbpGrid* grid);
+
+/* Layout of every field of this grid: row pitch ldq and field stride fs in
+ * elements, and the element size in bytes of the solver precision. */
+int sbp_layout(const SbpGrid* grid, int64_t* ldq, int64_t* fs, int64_t* elem_bytes);
+
+/* Bind the caller's device buffers (solver precision, layout of sbp_layout):
+ * q0, q1: 9 fields each (ping-pong state; q0 holds the state after binding),
+ * dq: 9 fields (Runge-Kutta register), met: 9 fields, mat: 3 fields.
+ * Pointers must be 256-byte aligned and distinct.  Allocates the library's
+ * internal buffers on the current device. */
+int sbp_bind(SbpGrid* grid, void* q0, void* q1, void* dq, void* met, void* mat);
+
+/* Section 2.2: from node coordinates xyz (3 FP64 fields x, y, z; device)
+ * compute J and a[xi][eta] = J xi_eta (Cramer's rule, derivatives with
+ * D_c = (D+ + D-)/2 of the grid's order) into jmet (10 FP64 fields: J, then
+ * the 9 metrics; device, caller-owned).  Flags SBP_STATUS_BAD_MESH where J <= 0. */
+int sbp_metrics(SbpGrid* grid, const double* xyz, double* jmet, void* stream);
+
+/* Fill the bound met (a[xi][eta] cast to the solver precision) and mat
+ * (1/(rho J), lambda/J, mu/J) from jmet (as produced by sbp_metrics) and rlm
+ * (3 FP64 fields rho, lambda, mu; device).  Flags SBP_STATUS_BAD_MATERIAL where
+ * rho <= 0, mu <= 0 or lambda + 2 mu <= 0.  Needs sbp_bind. */
+int sbp_set_material(SbpGrid* grid, const double* jmet, const double* rlm, void* stream);
+
+/* dQ/dt of the semi-discrete scheme with penalties (Eq.
+ * gen_hyp_transformed_discrete_SAT multiplied by P~) for the state q (9 fields,
+ * device) into out (9 fields, device); no time stepping, no source.  Needs
+ * sbp_bind and sbp_set_material. */
+int sbp_rhs(SbpGrid* grid, const void* q, void* out, void* stream);
+
+/* One fused Runge-Kutta stage k in 0..4 on the bound buffers:
+ * dq <- A_k dq + dt L(q_cur), q_next <- q_cur + B_k dq, then q_next becomes
+ * current.  The source (if set) is evaluated at t + c_k dt.  Does not advance t. */
+int sbp_rk_stage(SbpGrid* grid, int32_t stage, double dt, void* stream);
+
+/* n full steps of size dt (five fused stages each), source at the stage times,
+ * receivers recorded after each step; advances the grid time by n dt. */
+int sbp_step_n(SbpGrid* grid, int32_t n, double dt, void* stream);
+
+/* Kernel path for the stage: 0 (default) = tiled interior kernel over
+ * [b, N-1-b]^3 plus the boundary-slab kernel; 1 = the boundary-slab (general)
+ * kernel over every node.  Both compute the same scheme; path 1 exists to
+ * cross-check the tiled kernel. */
+int sbp_set_kernel_path(SbpGrid* grid, int32_t path);
+
+/* Per-kernel timing: when enabled, each stage-kernel launch is bracketed by
+ * CUDA events recorded on the launching stream.  sbp_kernel_times waits for
+ * the recorded events, returns the summed milliseconds and launch counts per
+ * kernel kind (index 0: tiled interior kernel, 1: boundary-slab / general
+ * kernel) since the previous call, and clears them. */
+int sbp_kernel_timing(SbpGrid* grid, int32_t enable);
+int sbp_kernel_times(SbpGrid* grid, double* ms, int64_t* launches);
+
+/* Which bound state buffer holds the current state: 0 (q0) or 1 (q1). */
+int sbp_current(const SbpGrid* grid, int32_t* which);
+
+/* Set / get the simulation time and the step counter (receivers record at
+ * column step). */
+int sbp_set_time(SbpGrid* grid, double t, int64_t step);
+int sbp_get_time(const SbpGrid* grid, double* t, int64_t* step);
+
+/* Discrete energy E = 1/2 <Q, P~^-1 Q>_H (Eq. physical_energy_discrete with the
+ * Jacobian weight) of the current state, accumulated in FP64.  Synchronises the
+ * stream; NONFINITE if E is not finite. */
+int sbp_energy(SbpGrid* grid, double* out, void* stream);
+
+/* Place a point source (replaces any previous one).  jmet as for
+ * sbp_set_material (J is read at the source's nodes). */
+int sbp_set_source(SbpGrid* grid, const SbpSource* src, const double* jmet, void* stream);
+
+/* Receivers: n nodes given by host int32 (i, j, k) triples; traces is a device
+ * buffer of n*3*n_t elements of the solver precision, trace[r][c][step]
+ * (velocity component c of receiver r after step `step`); steps beyond n_t are
+ * not recorded.  n = 0 removes the receivers. */
+int sbp_set_receivers(SbpGrid* grid, int32_t n, const int32_t* ijk, void* traces, int32_t n_t);
+
+/* Copy the device status word into *bits and clear it (synchronises). */
+int sbp_status(SbpGrid* grid, uint32_t* bits, void* stream);
+
+/* The 5-stage coefficients used by the kernels (A, B, and the derived stage
+ * times c = row sums of the equivalent Butcher tableau). */
+int sbp_rk_coefficients(double* A, double* B, double* C);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* sbp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBP_GB300_H */

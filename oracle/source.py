@@ -10,8 +10,9 @@ paper discretises the singular source "to high order" after Petersson et al.
   g integrates to one for the LOH1 time function).
 * delta_h at node (i, j, k) = phi_i phi_j phi_k / (J_ijk H_q,i H_r,j H_s,k),
   so that sum H J delta_h f = sum phi phi phi f.  Each 1D weight vector phi
-  lives on the m+1 nodes nearest to the source coordinate (shifted inwards
-  at a face) and satisfies the discrete moment conditions
+  lives on m+1 consecutive nodes starting at floor(xi_0/h) - (m-1)/2 (centred
+  on the cell holding the source, shifted inwards at a face) and satisfies
+  the discrete moment conditions
   sum_i phi_i (xi_i - xi_0)^k = delta_k0 for k = 0..m, with m = order + 1.
 * The moment tensor of a double couple is M = M0 (n d^T + d n^T) with n the
   fault normal and d the slip direction.
@@ -24,7 +25,7 @@ import numpy as np
 def delta_weights_1d(xi0, N, m):
     """(first node index, phi[0..m]) of the 1D discrete delta at reference coordinate xi0."""
     h = 1.0 / (N - 1)
-    c = int(round(xi0 / h - m / 2.0))
+    c = int(np.floor(xi0 / h)) - (m - 1) // 2     # m + 1 nodes centred on the source's cell
     c = max(0, min(N - 1 - m, c))
     xs = (np.arange(c, c + m + 1) * h - xi0) / h
     V = np.vander(xs, m + 1, increasing=True).T      # V[k, i] = xs_i^k

@@ -1,0 +1,217 @@
+"""ctypes binding of include/sbp.h: the same entry points, argument marshalling only.
+
+Every function here forwards to the CUDA library libsbp_gb300.so and raises
+SbpError on a non-zero status.  There is no CPU fallback: if the library is
+not built, ``lib()`` raises.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+SBP_BC_FREE = 0
+SBP_BC_CHAR = 1
+ERRORS = {1: "ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "NONFINITE", 5: "STATE", 6: "MESH"}
+
+EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sbp_bind", "sbp_metrics",
+            "sbp_set_material", "sbp_rhs", "sbp_rk_stage", "sbp_step_n", "sbp_set_kernel_path", "sbp_current",
+            "sbp_kernel_timing", "sbp_kernel_times",
+            "sbp_set_time", "sbp_get_time", "sbp_energy", "sbp_set_source", "sbp_set_receivers", "sbp_status",
+            "sbp_rk_coefficients", "sbp_last_error")
+
+
+class SbpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sbp error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class SbpGridDesc(ctypes.Structure):
+    _fields_ = [("nq", ctypes.c_int32), ("nr", ctypes.c_int32), ("ns", ctypes.c_int32),
+                ("order", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("bc_kind", ctypes.c_int32 * 6), ("bc_gamma", ctypes.c_double * 6)]
+
+
+class SbpSource(ctypes.Structure):
+    _fields_ = [("ref", ctypes.c_double * 3), ("moment", ctypes.c_double * 6), ("stf", ctypes.c_int32),
+                ("f0", ctypes.c_double), ("t0", ctypes.c_double), ("T", ctypes.c_double)]
+
+
+_LIB = None
+P = ctypes.c_void_p
+
+
+def lib(path=None):
+    """Load the library (built by ``paper_2011_02600_gb300.build.build()``)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2011_02600_gb300.build.build() "
+                           "(this package has no CPU fallback)")
+    L = ctypes.CDLL(path)
+    i32, i64, dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "sbp_min_nodes": [i32, ctypes.POINTER(i32)],
+        "sbp_create_grid": [ctypes.POINTER(SbpGridDesc), ctypes.POINTER(P)],
+        "sbp_destroy": [P],
+        "sbp_layout": [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)],
+        "sbp_bind": [P, P, P, P, P, P],
+        "sbp_metrics": [P, P, P, P],
+        "sbp_set_material": [P, P, P, P],
+        "sbp_rhs": [P, P, P, P],
+        "sbp_rk_stage": [P, i32, dbl, P],
+        "sbp_step_n": [P, i32, dbl, P],
+        "sbp_set_kernel_path": [P, i32],
+        "sbp_current": [P, ctypes.POINTER(i32)],
+        "sbp_kernel_timing": [P, i32],
+        "sbp_kernel_times": [P, ctypes.POINTER(dbl), ctypes.POINTER(i64)],
+        "sbp_set_time": [P, dbl, i64],
+        "sbp_get_time": [P, ctypes.POINTER(dbl), ctypes.POINTER(i64)],
+        "sbp_energy": [P, ctypes.POINTER(dbl), P],
+        "sbp_set_source": [P, ctypes.POINTER(SbpSource), P, P],
+        "sbp_set_receivers": [P, i32, P, P, i32],
+        "sbp_status": [P, ctypes.POINTER(ctypes.c_uint32), P],
+        "sbp_rk_coefficients": [ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.sbp_last_error.argtypes = []
+    L.sbp_last_error.restype = ctypes.c_char_p
+    _LIB = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise SbpError(rc, lib().sbp_last_error().decode())
+
+
+def _ptr(x):
+    """Device/host pointer of a torch tensor, an int address or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def sbp_min_nodes(order):
+    out = ctypes.c_int32()
+    _check(lib().sbp_min_nodes(order, ctypes.byref(out)))
+    return out.value
+
+
+def sbp_create_grid(nodes, order, precision, bc):
+    """bc: six entries ("free",) or ("char", gamma), faces (q0, q1, r0, r1, s0, s1)."""
+    d = SbpGridDesc()
+    d.nq, d.nr, d.ns = nodes
+    d.order, d.precision = order, precision
+    for f, c in enumerate(bc):
+        d.bc_kind[f] = SBP_BC_FREE if c[0] == "free" else SBP_BC_CHAR
+        d.bc_gamma[f] = 0.0 if c[0] == "free" else float(c[1])
+    h = P()
+    _check(lib().sbp_create_grid(ctypes.byref(d), ctypes.byref(h)))
+    return h
+
+
+def sbp_destroy(h):
+    _check(lib().sbp_destroy(h))
+
+
+def sbp_layout(h):
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().sbp_layout(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def sbp_bind(h, q0, q1, dq, met, mat):
+    _check(lib().sbp_bind(h, _ptr(q0), _ptr(q1), _ptr(dq), _ptr(met), _ptr(mat)))
+
+
+def sbp_metrics(h, xyz, jmet, stream):
+    _check(lib().sbp_metrics(h, _ptr(xyz), _ptr(jmet), stream))
+
+
+def sbp_set_material(h, jmet, rlm, stream):
+    _check(lib().sbp_set_material(h, _ptr(jmet), _ptr(rlm), stream))
+
+
+def sbp_rhs(h, q, out, stream):
+    _check(lib().sbp_rhs(h, _ptr(q), _ptr(out), stream))
+
+
+def sbp_rk_stage(h, stage, dt, stream):
+    _check(lib().sbp_rk_stage(h, stage, dt, stream))
+
+
+def sbp_step_n(h, n, dt, stream):
+    _check(lib().sbp_step_n(h, n, dt, stream))
+
+
+def sbp_set_kernel_path(h, path):
+    _check(lib().sbp_set_kernel_path(h, path))
+
+
+def sbp_kernel_timing(h, enable):
+    _check(lib().sbp_kernel_timing(h, 1 if enable else 0))
+
+
+def sbp_kernel_times(h):
+    """([ms_interior, ms_slab], [launches_interior, launches_slab]) since the previous call."""
+    ms, n = (ctypes.c_double * 2)(), (ctypes.c_int64 * 2)()
+    _check(lib().sbp_kernel_times(h, ms, n))
+    return list(ms), list(n)
+
+
+def sbp_current(h):
+    w = ctypes.c_int32()
+    _check(lib().sbp_current(h, ctypes.byref(w)))
+    return w.value
+
+
+def sbp_set_time(h, t, step):
+    _check(lib().sbp_set_time(h, t, step))
+
+
+def sbp_get_time(h):
+    t, s = ctypes.c_double(), ctypes.c_int64()
+    _check(lib().sbp_get_time(h, ctypes.byref(t), ctypes.byref(s)))
+    return t.value, s.value
+
+
+def sbp_energy(h, stream):
+    out = ctypes.c_double()
+    _check(lib().sbp_energy(h, ctypes.byref(out), stream))
+    return out.value
+
+
+def sbp_set_source(h, ref, moment, stf, f0, t0, T, jmet, stream):
+    s = SbpSource()
+    for a in range(3):
+        s.ref[a] = ref[a]
+    for c in range(6):
+        s.moment[c] = moment[c]
+    s.stf, s.f0, s.t0, s.T = stf, f0, t0, T
+    _check(lib().sbp_set_source(h, ctypes.byref(s), _ptr(jmet), stream))
+
+
+def sbp_set_receivers(h, ijk, traces, n_t):
+    import numpy as np
+    arr = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1, 3))
+    _check(lib().sbp_set_receivers(h, len(arr), arr.ctypes.data if len(arr) else None, _ptr(traces), n_t))
+
+
+def sbp_status(h, stream):
+    v = ctypes.c_uint32()
+    _check(lib().sbp_status(h, ctypes.byref(v), stream))
+    return v.value
+
+
+def sbp_rk_coefficients():
+    A, B, C = (ctypes.c_double * 5)(), (ctypes.c_double * 5)(), (ctypes.c_double * 5)()
+    _check(lib().sbp_rk_coefficients(A, B, C))
+    return list(A), list(B), list(C)

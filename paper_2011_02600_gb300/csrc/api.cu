@@ -1,0 +1,612 @@
+// C ABI (include/sbp.h): grid handle, validation, stage sequencing.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "sbp.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SBP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Carpenter & Kennedy (1994) five-stage 2N-storage fourth-order coefficients.
+const double kRkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                        -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kRkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                        1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                        2277821191437.0 / 14882151754819.0};
+
+// Stage times c_k: total weight of dt f_j in the state seen by stage k
+// (row sums of the equivalent Butcher tableau), so that they are consistent
+// with A and B to rounding.
+void rk_stage_times(double c[5]) {
+  double reg[5] = {0, 0, 0, 0, 0}, acc[5] = {0, 0, 0, 0, 0};
+  for (int k = 0; k < 5; ++k) {
+    double s = 0;
+    for (int j = 0; j < 5; ++j) s += acc[j];
+    c[k] = s;
+    for (int j = 0; j < 5; ++j) reg[j] = kRkA[k] * reg[j] + (j == k ? 1.0 : 0.0);
+    for (int j = 0; j < 5; ++j) acc[j] += kRkB[k] * reg[j];
+  }
+}
+
+int closure_b(int order) { return order == 2 ? 2 : order == 4 ? 4 : 6; }
+int stencil_reach(int order) { return order == 2 ? 2 : order == 4 ? 3 : 4; }  // max(r, q)
+
+}  // namespace
+
+struct SbpGrid {
+  SbpGridDesc desc;
+  sbp::Dims dims;
+  int elem;
+  void* q[2] = {nullptr, nullptr};
+  void* dq = nullptr;
+  void* met = nullptr;
+  void* mat = nullptr;
+  int cur = 0;
+  bool bound = false, material = false;
+  double t = 0.0;
+  long long step = 0;
+  double rkc[5];
+  // internal device buffers
+  double* partial = nullptr;
+  double* eout = nullptr;
+  unsigned* status = nullptr;
+  int32_t* src_off = nullptr;
+  double* src_w = nullptr;
+  int src_n = 0;
+  SbpSource src;
+  int32_t* rec_off = nullptr;
+  int rec_n = 0;
+  void* traces = nullptr;
+  int n_t = 0;
+  bool use_interior = true;
+  // optional per-kernel CUDA-event timing of the stage kernels (kind 0 = interior, 1 = slabs/general)
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+};
+
+namespace {
+
+sbp::BoxList slab_boxes(const SbpGrid* g, bool with_interior_box, sbp::Box* interior) {
+  const int b = closure_b(g->desc.order);
+  const int nq = g->desc.nq, nr = g->desc.nr, ns = g->desc.ns;
+  sbp::BoxList L;
+  L.n = 0;
+  auto add = [&](int i0, int i1, int j0, int j1, int k0, int k1) {
+    if (i1 <= i0 || j1 <= j0 || k1 <= k0) return;
+    L.b[L.n] = sbp::Box{i0, i1, j0, j1, k0, k1};
+    ++L.n;
+  };
+  const sbp::Box in{b, nq - b, b, nr - b, b, ns - b};
+  const bool has_in = in.i1 > in.i0 && in.j1 > in.j0 && in.k1 > in.k0;
+  if (!has_in || with_interior_box) {
+    add(0, nq, 0, nr, 0, ns);
+    if (interior) *interior = sbp::Box{0, 0, 0, 0, 0, 0};
+  } else {
+    add(0, nq, 0, nr, 0, b);             // s = 0 slab
+    add(0, nq, 0, nr, ns - b, ns);       // s = 1 slab
+    add(0, nq, 0, b, b, ns - b);         // r = 0 slab
+    add(0, nq, nr - b, nr, b, ns - b);   // r = 1 slab
+    add(0, b, b, nr - b, b, ns - b);     // q = 0 slab
+    add(nq - b, nq, b, nr - b, b, ns - b);  // q = 1 slab
+    if (interior) *interior = in;
+  }
+  L.off[0] = 0;
+  for (int m = 0; m < L.n; ++m) {
+    const sbp::Box& x = L.b[m];
+    L.off[m + 1] = L.off[m] + (long long)(x.i1 - x.i0) * (x.j1 - x.j0) * (x.k1 - x.k0);
+  }
+  return L;
+}
+
+template <typename T>
+sbp::StageArgs<T> make_args(const SbpGrid* g, const void* q, void* qout, int mode, double a, double bcoef,
+                            double dt) {
+  sbp::StageArgs<T> A;
+  A.q = (const T*)q;
+  A.qout = (T*)qout;
+  A.dq = (T*)g->dq;
+  A.met = (const T*)g->met;
+  A.mat = (const T*)g->mat;
+  A.d = g->dims;
+  A.rk_a = (T)a;
+  A.rk_b = (T)bcoef;
+  A.dt = (T)dt;
+  A.mode = mode;
+  const int N[3] = {g->desc.nq, g->desc.nr, g->desc.ns};
+  const int b = closure_b(g->desc.order);
+  (void)b;
+  for (int f = 0; f < 6; ++f) {
+    A.bc_kind[f] = g->desc.bc_kind[f];
+    A.bc_gamma[f] = (T)g->desc.bc_gamma[f];
+  }
+  double w0 = g->desc.order == 2 ? sbp::OpCoef<2>::w(0) : g->desc.order == 4 ? sbp::OpCoef<4>::w(0)
+                                                                               : sbp::OpCoef<6>::w(0);
+  for (int x = 0; x < 3; ++x) {
+    A.inv_h[x] = (T)(N[x] - 1);
+    A.inv_h0[x] = (T)((double)(N[x] - 1) / w0);
+  }
+  return A;
+}
+
+cudaEvent_t pool_event(SbpGrid* g) {
+  if (!g->ev_pool.empty()) {
+    cudaEvent_t e = g->ev_pool.back();
+    g->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Record events around one kernel launch when timing is on.
+struct TimedLaunch {
+  SbpGrid* g;
+  int kind;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  TimedLaunch(SbpGrid* g_, int kind_, cudaStream_t st_) : g(g_), kind(kind_), st(st_) {
+    if (g->timing) {
+      a = pool_event(g);
+      b = pool_event(g);
+      cudaEventRecord(a, st);
+    }
+  }
+  void done() {
+    if (g->timing && a && b) {
+      cudaEventRecord(b, st);
+      g->ev_pending.push_back({kind, {a, b}});
+    }
+  }
+};
+
+template <typename T>
+int run_stage_kernels(SbpGrid* g, const void* q, void* qout, int mode, double a, double bcoef, double dt,
+                      cudaStream_t st) {
+  sbp::StageArgs<T> A = make_args<T>(g, q, qout, mode, a, bcoef, dt);
+  sbp::Box in;
+  bool interior_done = false;
+  if (g->use_interior) {
+    sbp::BoxList L = slab_boxes(g, false, &in);
+    if (in.i1 > in.i0) {
+      TimedLaunch ti(g, 0, st);
+      cudaError_t e = sbp::launch_stage_interior<T>(A, g->desc.order, in, st);
+      if (e == cudaSuccess) {
+        ti.done();
+        interior_done = true;
+        TimedLaunch ts(g, 1, st);
+        e = sbp::launch_stage_general<T>(A, g->desc.order, L, st);
+        if (e != cudaSuccess) return cuda_fail(e, "stage (boundary slabs)");
+        ts.done();
+      } else if (e != cudaErrorNotSupported) {
+        return cuda_fail(e, "stage (interior)");
+      } else {
+        cudaGetLastError();
+      }
+    }
+  }
+  if (!interior_done) {
+    sbp::BoxList L = slab_boxes(g, true, nullptr);
+    TimedLaunch ts(g, 1, st);
+    cudaError_t e = sbp::launch_stage_general<T>(A, g->desc.order, L, st);
+    if (e != cudaSuccess) return cuda_fail(e, "stage (general)");
+    ts.done();
+  }
+  return SBP_OK;
+}
+
+double stf_value(const SbpSource& s, double t) {
+  if (s.stf == 0) {
+    const double a = M_PI * s.f0 * (t - s.t0);
+    return (1.0 - 2.0 * a * a) * exp(-a * a);
+  }
+  return t > 0 ? t / (s.T * s.T) * exp(-t / s.T) : 0.0;
+}
+
+template <typename T>
+int stage_impl(SbpGrid* g, int k, double dt, cudaStream_t st) {
+  const void* qin = g->q[g->cur];
+  void* qout = g->q[1 - g->cur];
+  const int mode = k == 0 ? sbp::kModeStage0 : sbp::kModeStage;
+  int rc = run_stage_kernels<T>(g, qin, qout, mode, kRkA[k], kRkB[k], dt, st);
+  if (rc) return rc;
+  if (g->src_n > 0) {
+    const double gdt = stf_value(g->src, g->t + g->rkc[k] * dt) * dt;
+    cudaError_t e = sbp::launch_source<T>((T*)qout, (T*)g->dq, g->dims, g->src_off, g->src_w, g->src_n, gdt,
+                                          kRkB[k], mode, st);
+    if (e != cudaSuccess) return cuda_fail(e, "source");
+  }
+  g->cur = 1 - g->cur;
+  return SBP_OK;
+}
+
+int check_ready(const SbpGrid* g) {
+  if (!g) return fail(SBP_ERR_ARG, "null grid");
+  if (!g->bound) return fail(SBP_ERR_STATE, "buffers not bound (sbp_bind)");
+  return SBP_OK;
+}
+
+// 1D discrete delta: m+1 consecutive nodes from floor(xi0/h) - (m-1)/2 (centred on the
+// source's cell, shifted inwards at a face), moment conditions up to degree m.
+void delta_1d(double xi0, int N, int m, int* start, double* phi) {
+  const double h = 1.0 / (N - 1);
+  int c = (int)floor(xi0 / h) - (m - 1) / 2;
+  c = std::max(0, std::min(N - 1 - m, c));
+  *start = c;
+  // solve V^T phi = e0 with V[k][i] = x_i^k (Gaussian elimination, partial pivoting)
+  const int n = m + 1;
+  std::vector<double> A(n * (n + 1));
+  for (int k = 0; k < n; ++k) {
+    for (int i = 0; i < n; ++i) A[k * (n + 1) + i] = pow(((c + i) * h - xi0) / h, k);
+    A[k * (n + 1) + n] = k == 0 ? 1.0 : 0.0;
+  }
+  for (int col = 0; col < n; ++col) {
+    int p = col;
+    for (int r = col + 1; r < n; ++r)
+      if (fabs(A[r * (n + 1) + col]) > fabs(A[p * (n + 1) + col])) p = r;
+    for (int x = 0; x <= n; ++x) std::swap(A[col * (n + 1) + x], A[p * (n + 1) + x]);
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double f = A[r * (n + 1) + col] / A[col * (n + 1) + col];
+      for (int x = col; x <= n; ++x) A[r * (n + 1) + x] -= f * A[col * (n + 1) + x];
+    }
+  }
+  for (int i = 0; i < n; ++i) phi[i] = A[i * (n + 1) + n] / A[i * (n + 1) + i];
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sbp_last_error(void) { return g_last_error.c_str(); }
+
+int sbp_min_nodes(int32_t order, int32_t* out) {
+  if (order != 2 && order != 4 && order != 6) return fail(SBP_ERR_ARG, "order must be 2, 4 or 6");
+  if (!out) return fail(SBP_ERR_ARG, "null output");
+  *out = 2 * closure_b(order) + stencil_reach(order);
+  return SBP_OK;
+}
+
+int sbp_rk_coefficients(double* A, double* B, double* C) {
+  double c[5];
+  rk_stage_times(c);
+  for (int k = 0; k < 5; ++k) {
+    if (A) A[k] = kRkA[k];
+    if (B) B[k] = kRkB[k];
+    if (C) C[k] = c[k];
+  }
+  return SBP_OK;
+}
+
+int sbp_create_grid(const SbpGridDesc* desc, SbpGrid** out) {
+  if (!desc || !out) return fail(SBP_ERR_ARG, "null argument");
+  *out = nullptr;
+  int32_t nmin;
+  if (sbp_min_nodes(desc->order, &nmin)) return SBP_ERR_ARG;
+  if (desc->nq < nmin || desc->nr < nmin || desc->ns < nmin)
+    return fail(SBP_ERR_ARG, "order %d needs at least %d nodes per axis (got %d x %d x %d)", desc->order, nmin,
+                desc->nq, desc->nr, desc->ns);
+  if (desc->precision != 32 && desc->precision != 64) return fail(SBP_ERR_ARG, "precision must be 32 or 64");
+  for (int f = 0; f < 6; ++f) {
+    if (desc->bc_kind[f] != SBP_BC_FREE && desc->bc_kind[f] != SBP_BC_CHAR)
+      return fail(SBP_ERR_ARG, "face %d: unknown boundary kind %d", f, desc->bc_kind[f]);
+    if (desc->bc_kind[f] == SBP_BC_CHAR && !(fabs(desc->bc_gamma[f]) <= 1.0))
+      return fail(SBP_ERR_ARG, "face %d: gamma must lie in [-1, 1]", f);
+  }
+  const int elem = desc->precision == 32 ? 4 : 8;
+  const int align = 128 / elem;
+  const long long ldq = ((long long)desc->nq + align - 1) / align * align;
+  const long long plane = ldq * desc->nr;
+  long long fs = plane * desc->ns;
+  fs = (fs + 255) / 256 * 256;  // 256-byte aligned field starts for either precision
+  if (fs >= (1LL << 31) || plane >= (1LL << 31))
+    return fail(SBP_ERR_ARG, "grid too large: %lld elements per field (limit 2^31)", fs);
+  SbpGrid* g = new SbpGrid();
+  g->desc = *desc;
+  g->elem = elem;
+  g->dims = sbp::Dims{desc->nq, desc->nr, desc->ns, (int)ldq, (int)plane, fs};
+  rk_stage_times(g->rkc);
+  g->use_interior = true;
+  *out = g;
+  return SBP_OK;
+}
+
+int sbp_destroy(SbpGrid* g) {
+  if (!g) return SBP_OK;
+  for (auto& p : g->ev_pending) {
+    cudaEventDestroy(p.second.first);
+    cudaEventDestroy(p.second.second);
+  }
+  for (auto e : g->ev_pool) cudaEventDestroy(e);
+  cudaFree(g->partial);
+  cudaFree(g->eout);
+  cudaFree(g->status);
+  cudaFree(g->src_off);
+  cudaFree(g->src_w);
+  cudaFree(g->rec_off);
+  delete g;
+  return SBP_OK;
+}
+
+int sbp_layout(const SbpGrid* g, int64_t* ldq, int64_t* fs, int64_t* elem) {
+  if (!g) return fail(SBP_ERR_ARG, "null grid");
+  if (ldq) *ldq = g->dims.ldq;
+  if (fs) *fs = g->dims.fs;
+  if (elem) *elem = g->elem;
+  return SBP_OK;
+}
+
+int sbp_bind(SbpGrid* g, void* q0, void* q1, void* dq, void* met, void* mat) {
+  if (!g) return fail(SBP_ERR_ARG, "null grid");
+  void* p[5] = {q0, q1, dq, met, mat};
+  for (int i = 0; i < 5; ++i) {
+    if (!p[i]) return fail(SBP_ERR_ARG, "buffer %d is null", i);
+    if ((uintptr_t)p[i] % 256) return fail(SBP_ERR_ARG, "buffer %d is not 256-byte aligned", i);
+    for (int j = 0; j < i; ++j)
+      if (p[i] == p[j]) return fail(SBP_ERR_ARG, "buffers %d and %d alias", j, i);
+  }
+  g->q[0] = q0;
+  g->q[1] = q1;
+  g->dq = dq;
+  g->met = met;
+  g->mat = mat;
+  g->cur = 0;
+  if (!g->partial) {
+    cudaError_t e = cudaMalloc(&g->partial, sizeof(double) * sbp::energy_blocks());
+    if (e == cudaSuccess) e = cudaMalloc(&g->eout, sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(g->status, 0, sizeof(unsigned));
+    if (e != cudaSuccess) return cuda_fail(e, "internal buffers");
+  }
+  g->bound = true;
+  return SBP_OK;
+}
+
+int sbp_metrics(SbpGrid* g, const double* xyz, double* jmet, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!xyz || !jmet) return fail(SBP_ERR_ARG, "null coordinate or metric buffer");
+  cudaError_t e = sbp::launch_metrics(xyz, jmet, g->dims, g->desc.order, g->status, (cudaStream_t)stream);
+  return e == cudaSuccess ? SBP_OK : cuda_fail(e, "metrics");
+}
+
+int sbp_set_material(SbpGrid* g, const double* jmet, const double* rlm, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!jmet || !rlm) return fail(SBP_ERR_ARG, "null metric or material buffer");
+  cudaError_t e = g->elem == 4 ? sbp::launch_material<float>(jmet, rlm, (float*)g->met, (float*)g->mat, g->dims,
+                                                             g->status, (cudaStream_t)stream)
+                               : sbp::launch_material<double>(jmet, rlm, (double*)g->met, (double*)g->mat, g->dims,
+                                                              g->status, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "material");
+  g->material = true;
+  return SBP_OK;
+}
+
+int sbp_rhs(SbpGrid* g, const void* q, void* out, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
+  if (!q || !out || q == out) return fail(SBP_ERR_ARG, "rhs needs distinct input and output buffers");
+  return g->elem == 4 ? run_stage_kernels<float>(g, q, out, sbp::kModeRhs, 0, 0, 0, (cudaStream_t)stream)
+                      : run_stage_kernels<double>(g, q, out, sbp::kModeRhs, 0, 0, 0, (cudaStream_t)stream);
+}
+
+int sbp_rk_stage(SbpGrid* g, int32_t stage, double dt, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
+  if (stage < 0 || stage > 4) return fail(SBP_ERR_ARG, "stage must be 0..4");
+  if (!(dt > 0) || !isfinite(dt)) return fail(SBP_ERR_ARG, "dt must be positive and finite");
+  return g->elem == 4 ? stage_impl<float>(g, stage, dt, (cudaStream_t)stream)
+                      : stage_impl<double>(g, stage, dt, (cudaStream_t)stream);
+}
+
+int sbp_step_n(SbpGrid* g, int32_t n, double dt, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
+  if (n < 0) return fail(SBP_ERR_ARG, "negative step count");
+  if (!(dt > 0) || !isfinite(dt)) return fail(SBP_ERR_ARG, "dt must be positive and finite");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int s = 0; s < n; ++s) {
+    for (int k = 0; k < 5; ++k) {
+      int rc = g->elem == 4 ? stage_impl<float>(g, k, dt, st) : stage_impl<double>(g, k, dt, st);
+      if (rc) return rc;
+    }
+    g->t += dt;
+    if (g->rec_n > 0) {
+      cudaError_t e = g->elem == 4
+                          ? sbp::launch_receivers<float>((const float*)g->q[g->cur], g->dims, g->rec_off, g->rec_n,
+                                                         (float*)g->traces, g->n_t, g->step, st)
+                          : sbp::launch_receivers<double>((const double*)g->q[g->cur], g->dims, g->rec_off,
+                                                          g->rec_n, (double*)g->traces, g->n_t, g->step, st);
+      if (e != cudaSuccess) return cuda_fail(e, "receivers");
+    }
+    ++g->step;
+  }
+  return SBP_OK;
+}
+
+int sbp_set_kernel_path(SbpGrid* g, int32_t path) {
+  if (!g) return fail(SBP_ERR_ARG, "null grid");
+  if (path != 0 && path != 1) return fail(SBP_ERR_ARG, "kernel path must be 0 or 1");
+  g->use_interior = path == 0;
+  return SBP_OK;
+}
+
+int sbp_kernel_timing(SbpGrid* g, int32_t enable) {
+  if (!g) return fail(SBP_ERR_ARG, "null grid");
+  g->timing = enable != 0;
+  return SBP_OK;
+}
+
+int sbp_kernel_times(SbpGrid* g, double* ms, int64_t* launches) {
+  if (!g || !ms || !launches) return fail(SBP_ERR_ARG, "null argument");
+  ms[0] = ms[1] = 0.0;
+  launches[0] = launches[1] = 0;
+  for (auto& p : g->ev_pending) {
+    cudaError_t e = cudaEventSynchronize(p.second.second);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, p.second.first, p.second.second);
+    if (e != cudaSuccess) return cuda_fail(e, "kernel timing events");
+    ms[p.first] += t;
+    launches[p.first] += 1;
+    g->ev_pool.push_back(p.second.first);
+    g->ev_pool.push_back(p.second.second);
+  }
+  g->ev_pending.clear();
+  return SBP_OK;
+}
+
+int sbp_current(const SbpGrid* g, int32_t* which) {
+  if (!g || !which) return fail(SBP_ERR_ARG, "null argument");
+  *which = g->cur;
+  return SBP_OK;
+}
+
+int sbp_set_time(SbpGrid* g, double t, int64_t step) {
+  if (!g) return fail(SBP_ERR_ARG, "null grid");
+  g->t = t;
+  g->step = step;
+  return SBP_OK;
+}
+
+int sbp_get_time(const SbpGrid* g, double* t, int64_t* step) {
+  if (!g) return fail(SBP_ERR_ARG, "null grid");
+  if (t) *t = g->t;
+  if (step) *step = g->step;
+  return SBP_OK;
+}
+
+int sbp_energy(SbpGrid* g, double* out, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
+  if (!out) return fail(SBP_ERR_ARG, "null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = g->elem == 4 ? sbp::launch_energy<float>((const float*)g->q[g->cur], (const float*)g->mat,
+                                                           g->dims, g->desc.order, g->partial, sbp::energy_blocks(),
+                                                           g->eout, g->status, st)
+                               : sbp::launch_energy<double>((const double*)g->q[g->cur], (const double*)g->mat,
+                                                            g->dims, g->desc.order, g->partial,
+                                                            sbp::energy_blocks(), g->eout, g->status, st);
+  if (e != cudaSuccess) return cuda_fail(e, "energy");
+  double v = 0.0;
+  e = cudaMemcpyAsync(&v, g->eout, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "energy readback");
+  *out = v;
+  if (!isfinite(v)) return fail(SBP_ERR_NONFINITE, "energy is not finite");
+  return SBP_OK;
+}
+
+int sbp_set_source(SbpGrid* g, const SbpSource* src, const double* jmet, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!src) {
+    g->src_n = 0;
+    return SBP_OK;
+  }
+  if (!jmet) return fail(SBP_ERR_ARG, "set_source needs the FP64 Jacobian (jmet)");
+  for (int a = 0; a < 3; ++a)
+    if (!(src->ref[a] >= 0.0 && src->ref[a] <= 1.0)) return fail(SBP_ERR_ARG, "source outside the reference cube");
+  if (src->stf != 0 && src->stf != 1) return fail(SBP_ERR_ARG, "unknown source time function");
+  const int order = g->desc.order;
+  const int m = order + 1;
+  const int N[3] = {g->desc.nq, g->desc.nr, g->desc.ns};
+  int start[3];
+  double phi[3][8];
+  for (int a = 0; a < 3; ++a) delta_1d(src->ref[a], N[a], m, &start[a], phi[a]);
+  const int n1 = m + 1, nn = n1 * n1 * n1;
+  std::vector<int32_t> off(nn);
+  std::vector<double> J(nn), w(nn * 6);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(st);
+  for (int kk = 0, n = 0; kk < n1; ++kk)
+    for (int jj = 0; jj < n1; ++jj)
+      for (int ii = 0; ii < n1; ++ii, ++n) {
+        off[n] = (int32_t)((long long)(start[2] + kk) * g->dims.plane + (long long)(start[1] + jj) * g->dims.ldq +
+                           start[0] + ii);
+        if (e == cudaSuccess) e = cudaMemcpy(&J[n], jmet + off[n], sizeof(double), cudaMemcpyDeviceToHost);
+      }
+  if (e != cudaSuccess) return cuda_fail(e, "source Jacobian readback");
+  auto wgt = [&](int a, int pos) {
+    const double w0 = order == 2 ? sbp::norm_weight<2>(pos, N[a])
+                      : order == 4 ? sbp::norm_weight<4>(pos, N[a]) : sbp::norm_weight<6>(pos, N[a]);
+    return w0 / (N[a] - 1);
+  };
+  for (int kk = 0, n = 0; kk < n1; ++kk)
+    for (int jj = 0; jj < n1; ++jj)
+      for (int ii = 0; ii < n1; ++ii, ++n) {
+        const double H = wgt(0, start[0] + ii) * wgt(1, start[1] + jj) * wgt(2, start[2] + kk);
+        const double delta = phi[0][ii] * phi[1][jj] * phi[2][kk] / (J[n] * H);
+        for (int c = 0; c < 6; ++c) w[n * 6 + c] = -src->moment[c] * delta;
+      }
+  cudaFree(g->src_off);
+  cudaFree(g->src_w);
+  g->src_off = nullptr;
+  g->src_w = nullptr;
+  e = cudaMalloc(&g->src_off, sizeof(int32_t) * nn);
+  if (e == cudaSuccess) e = cudaMalloc(&g->src_w, sizeof(double) * nn * 6);
+  if (e == cudaSuccess) e = cudaMemcpy(g->src_off, off.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->src_w, w.data(), sizeof(double) * nn * 6, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "source buffers");
+  g->src = *src;
+  g->src_n = nn;
+  return SBP_OK;
+}
+
+int sbp_set_receivers(SbpGrid* g, int32_t n, const int32_t* ijk, void* traces, int32_t n_t) {
+  if (int rc = check_ready(g)) return rc;
+  cudaFree(g->rec_off);
+  g->rec_off = nullptr;
+  g->rec_n = 0;
+  if (n == 0) return SBP_OK;
+  if (n < 0 || !ijk || !traces || n_t <= 0) return fail(SBP_ERR_ARG, "bad receiver arguments");
+  std::vector<int32_t> off(n);
+  for (int r = 0; r < n; ++r) {
+    const int i = ijk[3 * r], j = ijk[3 * r + 1], k = ijk[3 * r + 2];
+    if (i < 0 || i >= g->desc.nq || j < 0 || j >= g->desc.nr || k < 0 || k >= g->desc.ns)
+      return fail(SBP_ERR_ARG, "receiver %d outside the grid", r);
+    off[r] = (int32_t)((long long)k * g->dims.plane + (long long)j * g->dims.ldq + i);
+  }
+  cudaError_t e = cudaMalloc(&g->rec_off, sizeof(int32_t) * n);
+  if (e == cudaSuccess) e = cudaMemcpy(g->rec_off, off.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "receiver buffers");
+  g->rec_n = n;
+  g->traces = traces;
+  g->n_t = n_t;
+  return SBP_OK;
+}
+
+int sbp_status(SbpGrid* g, uint32_t* bits, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!bits) return fail(SBP_ERR_ARG, "null output");
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned v = 0;
+  cudaError_t e = cudaMemcpyAsync(&v, g->status, sizeof(unsigned), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->status, 0, sizeof(unsigned), st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "status readback");
+  *bits = v;
+  return SBP_OK;
+}
+
+}  // extern "C"

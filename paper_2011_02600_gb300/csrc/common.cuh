@@ -1,0 +1,230 @@
+// Device-side building blocks shared by the stage, setup and reduction kernels.
+//
+// Notation (Duru, Fung & Williams, arXiv 2011.02600): state Q = (v, sigma) with
+// sigma in Voigt order (xx, yy, zz, xy, xz, yz); metrics a[xi][eta] = J xi_eta
+// (the basis e_xi = J grad xi of Section 2.2); coefficients 1/(rho J), lambda/J,
+// mu/J so that dQ/dt = P~ (P~^-1 dQ/dt) needs no division (P~ = J^-1 P,
+// Eq. S matrix).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sbp_coeffs.h"
+
+namespace sbp {
+
+// Field layout: [s][r][q], q contiguous, row pitch ldq, plane pitch ldq*nr,
+// field stride fs.  In-field offsets fit in 32 bits (checked at grid creation).
+struct Dims {
+  int nq, nr, ns;
+  int ldq;
+  int plane;     // ldq * nr
+  long long fs;  // field stride in elements
+};
+
+enum StageMode : int {
+  kModeRhs = 0,     // write dQ/dt to qout
+  kModeStage = 1,   // dq <- A dq + dt L; qout <- q + B dq
+  kModeStage0 = 2,  // same with A = 0 (dq is not read)
+};
+
+template <typename T>
+struct StageArgs {
+  const T* __restrict__ q;
+  T* __restrict__ qout;
+  T* __restrict__ dq;
+  const T* __restrict__ met;
+  const T* __restrict__ mat;
+  Dims d;
+  T rk_a, rk_b, dt;
+  int mode;
+  int bc_kind[6];
+  T bc_gamma[6];
+  T inv_h[3];       // N_xi - 1 (reference spacing 1/(N_xi - 1))
+  T inv_h0[3];      // 1 / H_xi[0] = (N_xi - 1) / w_0
+};
+
+// Closure rows of D+ and D- (unit spacing), one private copy per translation unit.
+#define SBP_DECLARE_TABLES(O, B, CW)                                   \
+  static __constant__ double kDpD##O[B][CW] = SBP_DP##O##_ROWS;        \
+  static __constant__ double kDmD##O[B][CW] = SBP_DM##O##_ROWS;        \
+  static __constant__ float kDpF##O[B][CW] = SBP_DP##O##_ROWS;         \
+  static __constant__ float kDmF##O[B][CW] = SBP_DM##O##_ROWS;
+SBP_DECLARE_TABLES(2, 2, 4)
+SBP_DECLARE_TABLES(4, 4, 7)
+SBP_DECLARE_TABLES(6, 6, 10)
+#undef SBP_DECLARE_TABLES
+
+template <typename T, int O>
+struct Tab;
+#define SBP_TAB(T, SUF, O)                                                              \
+  template <>                                                                           \
+  struct Tab<T, O> {                                                                    \
+    __device__ __forceinline__ static T p(int i, int c) { return kDp##SUF##O[i][c]; }   \
+    __device__ __forceinline__ static T m(int i, int c) { return kDm##SUF##O[i][c]; }   \
+  };
+SBP_TAB(double, D, 2)
+SBP_TAB(double, D, 4)
+SBP_TAB(double, D, 6)
+SBP_TAB(float, F, 2)
+SBP_TAB(float, F, 4)
+SBP_TAB(float, F, 6)
+#undef SBP_TAB
+
+// Row `pos` of D+ (PLUS) or D- on N nodes, unit spacing, applied through
+// fn(node_index_along_axis, weight).  Interior rows are Table 1's stencil
+// (alpha_j for D+, beta_j = -alpha_{-j} for D-); the b rows at each end are
+// the closure tables, the right end by D+[N-1-i][N-1-j] = -D-[i][j].
+template <typename T, int O, bool PLUS, class Fn>
+__device__ __forceinline__ void apply_row(int pos, int N, Fn&& fn) {
+  using C = OpCoef<O>;
+  if (pos < C::b) {
+#pragma unroll
+    for (int c = 0; c < C::cw; ++c) {
+      const T w = PLUS ? Tab<T, O>::p(pos, c) : Tab<T, O>::m(pos, c);
+      if (w != T(0)) fn(c, w);
+    }
+  } else if (pos > N - 1 - C::b) {
+    const int ii = N - 1 - pos;
+#pragma unroll
+    for (int c = 0; c < C::cw; ++c) {
+      const T w = PLUS ? Tab<T, O>::m(ii, c) : Tab<T, O>::p(ii, c);
+      if (w != T(0)) fn(N - 1 - c, -w);
+    }
+  } else {
+    if (PLUS) {
+#pragma unroll
+      for (int j = -C::r; j <= C::q; ++j) fn(pos + j, T(C::alpha(j)));
+    } else {
+#pragma unroll
+      for (int j = -C::q; j <= C::r; ++j) fn(pos + j, T(-C::alpha(-j)));
+    }
+  }
+}
+
+template <int O>
+__host__ __device__ __forceinline__ double norm_weight(int pos, int N) {
+  const int e = pos < N - 1 - pos ? pos : N - 1 - pos;
+  return OpCoef<O>::w(e);
+}
+
+// Flux rows of Eq. split_form with e_xi = a: F = sigma a.
+template <typename T>
+__device__ __forceinline__ void flux(const T a[3], const T s[6], T F[3]) {
+  F[0] = a[0] * s[0] + a[1] * s[3] + a[2] * s[4];
+  F[1] = a[0] * s[3] + a[1] * s[1] + a[2] * s[5];
+  F[2] = a[0] * s[4] + a[1] * s[5] + a[2] * s[2];
+}
+
+// B_xi rows of Eq. split_form applied to dv = D+_xi v, accumulated into e.
+template <typename T>
+__device__ __forceinline__ void add_strain(const T a[3], const T dv[3], T e[6]) {
+  e[0] += a[0] * dv[0];
+  e[1] += a[1] * dv[1];
+  e[2] += a[2] * dv[2];
+  e[3] += a[1] * dv[0] + a[0] * dv[1];
+  e[4] += a[2] * dv[0] + a[0] * dv[2];
+  e[5] += a[2] * dv[1] + a[1] * dv[2];
+}
+
+// Penalty of one face at one face node, added to the velocity rows rv and the
+// stress rows e of P~^-1 dQ/dt.
+//  free (Eq. SAT_free_surface): rv += +-(1/H0) J|grad xi| T = +-(1/H0) sigma a
+//    (+ at xi = 0, - at xi = 1);
+//  general with gamma (Eq. SAT_General via Eq. penalty_terms and Eq. data_hat):
+//    with Z equal on the two tangential directions the rotation R only splits
+//    normal and tangential parts, G_n = ((1-g) Zp v_n -+ (1+g) T_n)/2 and
+//    G_t = ((1-g) Zs v_t -+ (1+g) T_t)/2 (- at xi = 0, + at xi = 1),
+//    G = G_n n + G_t, G~ = G_n/Zp n + G_t/Zs;
+//    rv -= |a| G / H0,  e -= |a| (-+)(n (x) G~)_sym / H0.
+template <typename T>
+__device__ __forceinline__ void add_penalty(int side, int kind, T gamma, T inv_h0, const T v[3],
+                                            const T s[6], const T a[3], T irhoJ, T lamJ, T muJ,
+                                            T rv[3], T e[6]) {
+  if (kind == 0) {
+    T Fa[3];
+    flux(a, s, Fa);
+    const T sg = side == 0 ? inv_h0 : -inv_h0;
+    rv[0] += sg * Fa[0];
+    rv[1] += sg * Fa[1];
+    rv[2] += sg * Fa[2];
+    return;
+  }
+  const T an = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  const T n[3] = {a[0] / an, a[1] / an, a[2] / an};
+  T Tr[3];
+  flux(n, s, Tr);
+  const T Zp = sqrt((lamJ + T(2) * muJ) / irhoJ);
+  const T Zs = sqrt(muJ / irhoJ);
+  const T vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  const T Tn = Tr[0] * n[0] + Tr[1] * n[1] + Tr[2] * n[2];
+  const T sgT = side == 0 ? T(-1) : T(1);
+  const T cv = T(0.5) * (T(1) - gamma);
+  const T cT = T(0.5) * (T(1) + gamma) * sgT;
+  const T Gn = cv * Zp * vn + cT * Tn;
+  T G[3], Gt[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T gt = cv * Zs * (v[c] - vn * n[c]) + cT * (Tr[c] - Tn * n[c]);
+    G[c] = Gn * n[c] + gt;
+    Gt[c] = Gn / Zp * n[c] + gt / Zs;
+  }
+  const T f = an * inv_h0;
+  rv[0] -= f * G[0];
+  rv[1] -= f * G[1];
+  rv[2] -= f * G[2];
+  const T fs = side == 0 ? f : -f;   // e -= f * (side ? +1 : -1) * (n (x) G~)
+  e[0] += fs * n[0] * Gt[0];
+  e[1] += fs * n[1] * Gt[1];
+  e[2] += fs * n[2] * Gt[2];
+  e[3] += fs * (n[1] * Gt[0] + n[0] * Gt[1]);
+  e[4] += fs * (n[2] * Gt[0] + n[0] * Gt[2]);
+  e[5] += fs * (n[2] * Gt[1] + n[1] * Gt[2]);
+}
+
+// dQ/dt = P~ (rv, e): velocity rows / (rho J); stress rows C e / J.
+template <typename T>
+__device__ __forceinline__ void apply_P(const T rv[3], const T e[6], T irhoJ, T lamJ, T muJ, T d[9]) {
+  d[0] = irhoJ * rv[0];
+  d[1] = irhoJ * rv[1];
+  d[2] = irhoJ * rv[2];
+  const T tr = lamJ * (e[0] + e[1] + e[2]);
+  const T m2 = T(2) * muJ;
+  d[3] = tr + m2 * e[0];
+  d[4] = tr + m2 * e[1];
+  d[5] = tr + m2 * e[2];
+  d[6] = muJ * e[3];
+  d[7] = muJ * e[4];
+  d[8] = muJ * e[5];
+}
+
+// Write the stage result for one node at in-field offset off.
+template <typename T>
+__device__ __forceinline__ void stage_epilogue(const StageArgs<T>& A, long long off, const T d[9],
+                                               const T qc[9]) {
+  const long long fs = A.d.fs;
+  if (A.mode == kModeRhs) {
+#pragma unroll
+    for (int f = 0; f < 9; ++f) A.qout[f * fs + off] = d[f];
+    return;
+  }
+#pragma unroll
+  for (int f = 0; f < 9; ++f) {
+    T dn = A.dt * d[f];
+    if (A.mode == kModeStage) dn += A.rk_a * A.dq[f * fs + off];
+    A.dq[f * fs + off] = dn;
+    A.qout[f * fs + off] = qc[f] + A.rk_b * dn;
+  }
+}
+
+struct Box {
+  int i0, i1, j0, j1, k0, k1;
+};
+struct BoxList {
+  int n;
+  Box b[8];
+  long long off[9];  // prefix sums of box sizes
+};
+
+}  // namespace sbp

@@ -1,0 +1,259 @@
+// Setup kernels (metrics, material) and the small per-step kernels (energy,
+// source, receivers).
+#include <math.h>
+
+#include "common.cuh"
+#include "launch.h"
+
+namespace sbp {
+
+// ---------------------------------------------------------------------------
+// Section 2.2: J and a[xi][eta] = J xi_eta from node coordinates, FP64.
+// Coordinate derivatives use D_c = (D+ + D-)/2 along each axis.
+template <int O>
+__global__ void metrics_kernel(const double* __restrict__ xyz, double* __restrict__ jmet, Dims d,
+                               unsigned* status) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)d.nq * d.nr * d.ns;
+  if (t >= total) return;
+  const int i = (int)(t % d.nq);
+  const int j = (int)((t / d.nq) % d.nr);
+  const int k = (int)(t / ((long long)d.nq * d.nr));
+  const long long n0 = (long long)k * d.plane + (long long)j * d.ldq + i;
+  const int pos[3] = {i, j, k};
+  const int N[3] = {d.nq, d.nr, d.ns};
+  const long long stride[3] = {1, d.ldq, d.plane};
+  double der[3][3];  // der[xi][c] = d x_c / d xi
+#pragma unroll
+  for (int xi = 0; xi < 3; ++xi) {
+    double s[3] = {0, 0, 0};
+    auto acc = [&](int c, double w) {
+      const long long nb = n0 + (long long)(c - pos[xi]) * stride[xi];
+      s[0] += 0.5 * w * xyz[nb];
+      s[1] += 0.5 * w * xyz[d.fs + nb];
+      s[2] += 0.5 * w * xyz[2 * d.fs + nb];
+    };
+    apply_row<double, O, true>(pos[xi], N[xi], acc);
+    apply_row<double, O, false>(pos[xi], N[xi], acc);
+    const double ih = (double)(N[xi] - 1);
+    der[xi][0] = s[0] * ih;
+    der[xi][1] = s[1] * ih;
+    der[xi][2] = s[2] * ih;
+  }
+  // cross products: a_q = x_r x x_s, a_r = x_s x x_q, a_s = x_q x x_r (cofactors, Cramer's rule)
+  double a[3][3];
+#pragma unroll
+  for (int xi = 0; xi < 3; ++xi) {
+    const double* u = der[(xi + 1) % 3];
+    const double* v = der[(xi + 2) % 3];
+    a[xi][0] = u[1] * v[2] - u[2] * v[1];
+    a[xi][1] = u[2] * v[0] - u[0] * v[2];
+    a[xi][2] = u[0] * v[1] - u[1] * v[0];
+  }
+  const double J = der[0][0] * a[0][0] + der[0][1] * a[0][1] + der[0][2] * a[0][2];
+  jmet[n0] = J;
+#pragma unroll
+  for (int xi = 0; xi < 3; ++xi)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) jmet[(1 + 3 * xi + c) * d.fs + n0] = a[xi][c];
+  if (!(J > 0.0)) atomicOr(status, 2u);
+}
+
+cudaError_t launch_metrics(const double* xyz, double* jmet, const Dims& d, int order, unsigned* status,
+                           cudaStream_t st) {
+  const long long total = (long long)d.nq * d.nr * d.ns;
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  switch (order) {
+    case 2: metrics_kernel<2><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
+    case 4: metrics_kernel<4><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
+    case 6: metrics_kernel<6><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Solver coefficients: met = a (cast), mat = (1/(rho J), lambda/J, mu/J).
+template <typename T>
+__global__ void material_kernel(const double* __restrict__ jmet, const double* __restrict__ rlm,
+                                T* __restrict__ met, T* __restrict__ mat, Dims d, unsigned* status) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)d.nq * d.nr * d.ns;
+  if (t >= total) return;
+  const int i = (int)(t % d.nq);
+  const int j = (int)((t / d.nq) % d.nr);
+  const int k = (int)(t / ((long long)d.nq * d.nr));
+  const long long n0 = (long long)k * d.plane + (long long)j * d.ldq + i;
+  const double J = jmet[n0];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) met[c * d.fs + n0] = (T)jmet[(1 + c) * d.fs + n0];
+  const double rho = rlm[n0], lam = rlm[d.fs + n0], mu = rlm[2 * d.fs + n0];
+  mat[n0] = (T)(1.0 / (rho * J));
+  mat[d.fs + n0] = (T)(lam / J);
+  mat[2 * d.fs + n0] = (T)(mu / J);
+  if (!(rho > 0.0) || !(mu > 0.0) || !(lam + 2.0 * mu > 0.0)) atomicOr(status, 4u);
+  if (!(J > 0.0)) atomicOr(status, 2u);
+}
+
+template <typename T>
+cudaError_t launch_material(const double* jmet, const double* rlm, T* met, T* mat, const Dims& d,
+                            unsigned* status, cudaStream_t st) {
+  const long long total = (long long)d.nq * d.nr * d.ns;
+  material_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(jmet, rlm, met, mat, d, status);
+  return cudaGetLastError();
+}
+template cudaError_t launch_material<float>(const double*, const double*, float*, float*, const Dims&,
+                                            unsigned*, cudaStream_t);
+template cudaError_t launch_material<double>(const double*, const double*, double*, double*,
+                                             const Dims&, unsigned*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Energy (Eq. physical_energy_discrete with P~): 1/2 sum H J (rho |v|^2 + sigma^T S sigma),
+// written with the stored coefficients: J rho = 1/(1/(rho J)), and
+// J sigma^T S sigma = [sum s_ii^2 + 2 sum s_ij^2 - l/(3 l + 2 m) tr^2] / (2 m)
+// with l = lambda/J, m = mu/J.  Accumulated in FP64; warp shuffles, then a
+// fixed-order block reduction.
+constexpr int kEnergyBlocks = 1184;  // 152 SMs x 8
+constexpr int kEnergyThreads = 256;
+int energy_blocks() { return kEnergyBlocks; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T, int O>
+__global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const T* __restrict__ q, const T* __restrict__ mat,
+                                                                Dims d, double* __restrict__ partial,
+                                                                unsigned* status) {
+  const long long total = (long long)d.nq * d.nr * d.ns;
+  const double hq = 1.0 / (d.nq - 1), hr = 1.0 / (d.nr - 1), hs = 1.0 / (d.ns - 1);
+  double acc = 0.0;
+  bool bad = false;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t % d.nq);
+    const long long rest = t / d.nq;
+    const int j = (int)(rest % d.nr);
+    const int k = (int)(rest / d.nr);
+    const long long n0 = (long long)k * d.plane + (long long)j * d.ldq + i;
+    const double H = hq * norm_weight<O>(i, d.nq) * hr * norm_weight<O>(j, d.nr) * hs * norm_weight<O>(k, d.ns);
+    double v2 = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double v = (double)q[c * d.fs + n0];
+      v2 += v * v;
+    }
+    double s[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s[c] = (double)q[(3 + c) * d.fs + n0];
+    const double irhoJ = (double)mat[n0], l = (double)mat[d.fs + n0], m = (double)mat[2 * d.fs + n0];
+    const double tr = s[0] + s[1] + s[2];
+    const double sSs = (s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + 2.0 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]) -
+                        l / (3.0 * l + 2.0 * m) * tr * tr) / (2.0 * m);
+    const double dens = v2 / irhoJ + sSs;
+    bad |= !isfinite(dens);
+    acc += H * dens;
+  }
+  __shared__ double red[kEnergyThreads / 32];
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < kEnergyThreads / 32 ? red[threadIdx.x] : 0.0;
+    v = warp_sum(v);
+    if (threadIdx.x == 0) partial[blockIdx.x] = 0.5 * v;
+  }
+  if (bad) atomicOr(status, 1u);
+}
+
+__global__ void sum_partials_kernel(const double* __restrict__ partial, int n, double* out) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) v += partial[t];
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double w = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    w = warp_sum(w);
+    if (threadIdx.x == 0) *out = w;
+  }
+}
+
+template <typename T>
+cudaError_t launch_energy(const T* q, const T* mat, const Dims& d, int order, double* partial, int nblocks,
+                          double* out, unsigned* status, cudaStream_t st) {
+  switch (order) {
+    case 2: energy_kernel<T, 2><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
+    case 4: energy_kernel<T, 4><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
+    case 6: energy_kernel<T, 6><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
+    default: return cudaErrorInvalidValue;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  sum_partials_kernel<<<1, 1024, 0, st>>>(partial, nblocks, out);
+  return cudaGetLastError();
+}
+template cudaError_t launch_energy<float>(const float*, const float*, const Dims&, int, double*, int, double*,
+                                          unsigned*, cudaStream_t);
+template cudaError_t launch_energy<double>(const double*, const double*, const Dims&, int, double*, int,
+                                           double*, unsigned*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Point source: wsrc[n*6 + c] = -M_c delta_h at source node n; in a stage the
+// stress rates gain g(t) * wsrc, i.e. dq += dt g w and qout += B dt g w
+// (the stage update is linear in the rate).
+template <typename T>
+__global__ void source_kernel(T* __restrict__ qout, T* __restrict__ dq, Dims d, const int32_t* __restrict__ off,
+                              const double* __restrict__ wsrc, int nnodes, double gdt, double rk_b, int mode) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nnodes * 6) return;
+  const int n = t / 6, c = t % 6;
+  const long long idx = (long long)(3 + c) * d.fs + off[n];
+  const double add = gdt * wsrc[t];
+  if (mode == kModeRhs) {
+    qout[idx] = (T)((double)qout[idx] + add);
+    return;
+  }
+  dq[idx] = (T)((double)dq[idx] + add);
+  qout[idx] = (T)((double)qout[idx] + rk_b * add);
+}
+
+template <typename T>
+cudaError_t launch_source(T* qout, T* dq, const Dims& d, const int32_t* off, const double* wsrc, int nnodes,
+                          double gdt, double rk_b, int mode, cudaStream_t st) {
+  if (nnodes == 0) return cudaSuccess;
+  source_kernel<T><<<(nnodes * 6 + 127) / 128, 128, 0, st>>>(qout, dq, d, off, wsrc, nnodes, gdt, rk_b, mode);
+  return cudaGetLastError();
+}
+template cudaError_t launch_source<float>(float*, float*, const Dims&, const int32_t*, const double*, int,
+                                          double, double, int, cudaStream_t);
+template cudaError_t launch_source<double>(double*, double*, const Dims&, const int32_t*, const double*, int,
+                                           double, double, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Receivers: trace[r][c][step] = v_c at the receiver node.
+template <typename T>
+__global__ void receivers_kernel(const T* __restrict__ q, Dims d, const int32_t* __restrict__ off, int n,
+                                 T* __restrict__ traces, int n_t, long long step) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * 3 || step >= n_t) return;
+  const int r = t / 3, c = t % 3;
+  traces[(long long)t * n_t + step] = q[(long long)c * d.fs + off[r]];
+}
+
+template <typename T>
+cudaError_t launch_receivers(const T* q, const Dims& d, const int32_t* off, int n, T* traces, int n_t,
+                             long long step, cudaStream_t st) {
+  if (n == 0 || step >= n_t) return cudaSuccess;
+  receivers_kernel<T><<<(n * 3 + 127) / 128, 128, 0, st>>>(q, d, off, n, traces, n_t, step);
+  return cudaGetLastError();
+}
+template cudaError_t launch_receivers<float>(const float*, const Dims&, const int32_t*, int, float*, int,
+                                             long long, cudaStream_t);
+template cudaError_t launch_receivers<double>(const double*, const Dims&, const int32_t*, int, double*, int,
+                                              long long, cudaStream_t);
+
+}  // namespace sbp

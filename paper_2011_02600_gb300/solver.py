@@ -1,0 +1,151 @@
+"""Torch-backed convenience layer over the C ABI: device buffers and streams.
+
+PyTorch provides device memory and the current CUDA stream; every step of the
+scheme runs in the library's kernels.
+"""
+import torch
+
+from . import _lib as L
+
+FACES = ("q0", "q1", "r0", "r1", "s0", "s1")
+
+
+def _stream():
+    return ctypes_stream(torch.cuda.current_stream())
+
+
+def ctypes_stream(s):
+    return s.cuda_stream
+
+
+class ElasticSolver:
+    """One curvilinear block on one GPU.
+
+    nodes = (nq, nr, ns); order in {2, 4, 6}; precision in {32, 64};
+    bc: six face conditions ("free",) / ("char", gamma).
+    """
+
+    def __init__(self, nodes, order, precision=32, bc=None, device="cuda"):
+        if bc is None:
+            bc = [("char", 0.0)] * 5 + [("free",)]
+        self.nodes = tuple(int(n) for n in nodes)
+        self.order = order
+        self.precision = precision
+        self.bc = list(bc)
+        self.device = torch.device(device)
+        self.dtype = torch.float32 if precision == 32 else torch.float64
+        self.h = L.sbp_create_grid(self.nodes, order, precision, self.bc)
+        self.ldq, self.fs, self.elem = L.sbp_layout(self.h)
+        kw = dict(dtype=self.dtype, device=self.device)
+        self.qbuf = [torch.zeros(9 * self.fs, **kw), torch.zeros(9 * self.fs, **kw)]
+        self.dq = torch.zeros(9 * self.fs, **kw)
+        self.met = torch.zeros(9 * self.fs, **kw)
+        self.mat = torch.zeros(3 * self.fs, **kw)
+        L.sbp_bind(self.h, self.qbuf[0], self.qbuf[1], self.dq, self.met, self.mat)
+        self.jmet = None
+        self.traces = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None) is not None:
+                L.sbp_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    # -- layout helpers -------------------------------------------------------
+    def view(self, flat, nf):
+        """(nf, ns, nr, nq) strided view of a flat buffer in the library layout."""
+        nq, nr, ns = self.nodes
+        return flat[: nf * self.fs].view(nf, self.fs)[:, : ns * nr * self.ldq].view(nf, ns, nr, self.ldq)[..., :nq]
+
+    def new_fields(self, nf, dtype=None):
+        return torch.zeros(nf * self.fs, dtype=dtype or self.dtype, device=self.device)
+
+    def to_layout(self, arr, dtype=None):
+        """Copy an (nf, ns, nr, nq) tensor into a fresh flat buffer in the library layout."""
+        nf = arr.shape[0]
+        buf = self.new_fields(nf, dtype or arr.dtype)
+        self.view(buf, nf).copy_(arr.to(device=self.device, dtype=buf.dtype))
+        return buf
+
+    # -- setup ----------------------------------------------------------------
+    def setup(self, xyz, rlm, keep_metrics=False):
+        """xyz: (3, ns, nr, nq) coordinates; rlm: (3, ns, nr, nq) rho, lambda, mu (FP64 or castable)."""
+        st = _stream()
+        xyz_b = self.to_layout(torch.as_tensor(xyz), torch.float64)
+        jmet = self.new_fields(10, torch.float64)
+        L.sbp_metrics(self.h, xyz_b, jmet, st)
+        del xyz_b
+        rlm_b = self.to_layout(torch.as_tensor(rlm), torch.float64)
+        L.sbp_set_material(self.h, jmet, rlm_b, st)
+        del rlm_b
+        bits = L.sbp_status(self.h, st)
+        if bits & 2:
+            raise L.SbpError(6, "non-positive Jacobian")
+        if bits & 4:
+            raise L.SbpError(6, "invalid material (rho, mu > 0 and lambda + 2 mu > 0 required)")
+        self.jmet = jmet if keep_metrics else None
+        return jmet
+
+    def metrics(self):
+        """(J, a) as (ns, nr, nq) and (3, 3, ns, nr, nq) views of the FP64 metric buffer."""
+        v = self.view(self.jmet, 10)
+        return v[0], v[1:].reshape(3, 3, *v.shape[1:])
+
+    # -- state ------------------------------------------------------------------
+    @property
+    def current(self):
+        return L.sbp_current(self.h)
+
+    def state(self):
+        """(9, ns, nr, nq) view of the current state."""
+        return self.view(self.qbuf[self.current], 9)
+
+    def set_state(self, Q, reset_register=True):
+        self.state().copy_(torch.as_tensor(Q).to(device=self.device, dtype=self.dtype))
+        if reset_register:
+            self.dq.zero_()
+
+    def set_time(self, t, step=0):
+        L.sbp_set_time(self.h, t, step)
+
+    @property
+    def time(self):
+        return L.sbp_get_time(self.h)[0]
+
+    def set_kernel_path(self, path):
+        L.sbp_set_kernel_path(self.h, path)
+
+    # -- compute ----------------------------------------------------------------
+    def rhs(self, Q=None):
+        """dQ/dt (9, ns, nr, nq) of the given state (default: the current one)."""
+        src = self.qbuf[self.current] if Q is None else self.to_layout(torch.as_tensor(Q), self.dtype)
+        out = self.new_fields(9)
+        L.sbp_rhs(self.h, src, out, _stream())
+        return self.view(out, 9)
+
+    def rk_stage(self, k, dt):
+        L.sbp_rk_stage(self.h, k, dt, _stream())
+
+    def step(self, n, dt):
+        L.sbp_step_n(self.h, n, dt, _stream())
+
+    def energy(self):
+        return L.sbp_energy(self.h, _stream())
+
+    def status(self):
+        return L.sbp_status(self.h, _stream())
+
+    def set_source(self, ref, moment, stf="ricker", f0=2.0, t0=None, T=0.1):
+        if self.jmet is None:
+            raise RuntimeError("set_source needs setup(..., keep_metrics=True)")
+        kind = 0 if stf == "ricker" else 1
+        L.sbp_set_source(self.h, ref, moment, kind, f0, 1.2 / f0 if t0 is None else t0, T, self.jmet, _stream())
+
+    def set_receivers(self, ijk, n_t):
+        n = len(ijk)
+        self.traces = torch.zeros(max(n, 1) * 3 * n_t, dtype=self.dtype, device=self.device)
+        L.sbp_set_receivers(self.h, ijk, self.traces, n_t)
+        return self.traces.view(-1, 3, n_t)[:n]
+

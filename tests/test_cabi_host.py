@@ -1,0 +1,97 @@
+"""CPU tests of the C ABI: the library loads, exports every declared symbol, and
+rejects invalid arguments on the host (no compute calls, no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2011_02600_gb300 import _lib as L
+from paper_2011_02600_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return L.lib()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "sbp.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(sbp_\w+)\s*\(", text, re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(L.EXPORTED)
+
+
+def test_min_nodes(lib):
+    assert L.sbp_min_nodes(2) == 6 and L.sbp_min_nodes(4) == 11 and L.sbp_min_nodes(6) == 16
+    with pytest.raises(L.SbpError) as e:
+        L.sbp_min_nodes(3)
+    assert e.value.code == 1
+
+
+def _expect(code, fn, *a):
+    with pytest.raises(L.SbpError) as e:
+        fn(*a)
+    assert e.value.code == code, str(e.value)
+
+
+def test_create_grid_validation(lib):
+    free = [("free",)] * 6
+    _expect(1, L.sbp_create_grid, (15, 20, 20), 6, 32, free)        # too few nodes for order 6
+    _expect(1, L.sbp_create_grid, (20, 20, 20), 5, 32, free)        # odd order
+    _expect(1, L.sbp_create_grid, (20, 20, 20), 4, 16, free)        # precision
+    _expect(1, L.sbp_create_grid, (20, 20, 20), 4, 32, [("char", 1.5)] + free[1:])
+    _expect(1, L.sbp_create_grid, (40000, 40000, 4000), 2, 32, free)  # over 2^31 elements per field
+    h = L.sbp_create_grid((33, 17, 16), 6, 32, free)
+    ldq, fs, elem = L.sbp_layout(h)
+    assert elem == 4 and ldq == 64 and ldq % 32 == 0 and fs % 64 == 0 and fs >= ldq * 17 * 16
+    L.sbp_destroy(h)
+    h = L.sbp_create_grid((33, 17, 16), 6, 64, free)
+    ldq, fs, elem = L.sbp_layout(h)
+    assert elem == 8 and ldq == 48 and (fs * 8) % 256 == 0
+    L.sbp_destroy(h)
+
+
+def test_calls_out_of_sequence_are_rejected(lib):
+    h = L.sbp_create_grid((16, 16, 16), 6, 32, [("free",)] * 6)
+    _expect(5, L.sbp_rhs, h, 256, 512, None)       # before sbp_bind
+    _expect(5, L.sbp_step_n, h, 1, 1e-3, None)
+    _expect(5, L.sbp_energy, h, None)
+    _expect(1, L.sbp_bind, h, 0, 256, 512, 768, 1024)          # null
+    _expect(1, L.sbp_bind, h, 256, 256, 512, 768, 1024)        # aliasing
+    _expect(1, L.sbp_bind, h, 260, 512, 768, 1024, 1280)       # misaligned
+    L.sbp_destroy(h)
+
+
+def test_rk_coefficients_match_published_scheme(lib):
+    A, Bc, C = L.sbp_rk_coefficients()
+    from oracle import rk
+    for k in range(5):
+        assert A[k] == rk.A[k] and Bc[k] == rk.B[k]
+        assert abs(C[k] - rk.C[k]) < 1e-15
+
+
+def test_generated_coefficients_match_oracle():
+    """The kernel header's closures (package generator) equal the oracle's (independent derivation)."""
+    from fractions import Fraction
+    from oracle import operators as op
+    from paper_2011_02600_gb300 import opgen
+    for order in (2, 4, 6):
+        b, r, q, alpha, w, dp, dm = opgen.derive(order)
+        H, Dm, Dp, _, _ = op.upwind_pair_exact(order, op.min_nodes(order))
+        assert w == H[:b]
+        for i in range(b):
+            for j in range(b + q):
+                assert dp[i][j] == Dp[i][j] and dm[i][j] == Dm[i][j]
+        assert alpha == {j: Fraction(a) for j, a in op.interior_stencil(order).items()}
+    text = open(os.path.join(ROOT, "paper_2011_02600_gb300", "csrc", "sbp_coeffs.h")).read()
+    assert text == opgen.render()
