@@ -162,6 +162,8 @@ def main():
     ap.add_argument("--impl", default="gb300")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nodes", default=None,
+                    help="nq,nr,ns: a smaller instance of the workload (same generators; for profiling)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -191,6 +193,9 @@ def main():
     from workloads.fields import gaussian_pulse
 
     cfg = config_by_name(WORKLOAD)
+    if args.nodes:
+        import dataclasses
+        cfg = dataclasses.replace(cfg, nodes=tuple(int(x) for x in args.nodes.split(",")))
     s, info = build_solver(cfg, precision=32, device=f"cuda:{local}")
     nq, nr, ns = cfg.nodes
     nodes = nq * nr * ns
@@ -301,7 +306,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nodes": list(cfg.nodes), "order": cfg.order,
+        "config": {"workload": WORKLOAD if not args.nodes else WORKLOAD + " (reduced: profiling only)",
+                   "nodes": list(cfg.nodes), "order": cfg.order,
                    "extent_m": list(cfg.extent), "stages_per_step": 5, "dt_s": dt,
                    "l2": "inputs larger than L2 (39 fields x 1.74 GB resident)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},

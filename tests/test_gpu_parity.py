@@ -138,6 +138,23 @@ def test_fused_stage_parity_fp64(order, stage):
     assert _relerr(s.state().cpu().numpy(), q_new) < 1e-12
 
 
+@pytest.mark.parametrize("order,nodes", [(6, (101, 45, 40)), (4, (70, 33, 30)), (2, (67, 20, 13))])
+@pytest.mark.parametrize("prec", [32, 64])
+def test_tiled_interior_matches_general_kernel(order, nodes, prec):
+    """The tiled interior kernel (several tiles, ragged last tile, several s chunks) and the
+    general kernel compute the same right-hand side; also checked against the oracle."""
+    X, mat, J, a, sch = _problem(nodes, order)
+    s = _solver(nodes, order, prec, MIXED, X, mat)
+    Q = np.stack(smooth_state(nodes, 9, *_idx(nodes))) if prec == 32 else random_state(nodes, 9)
+    r_tiled = s.rhs(torch.from_numpy(Q)).cpu().numpy()
+    s.set_kernel_path(1)
+    r_gen = s.rhs(torch.from_numpy(Q)).cpu().numpy()
+    tol = 1e-12 if prec == 64 else 5e-6
+    assert _relerr(r_tiled, r_gen) < tol
+    want = rhs(Q, sch, J, a, mat, MIXED)
+    assert _relerr(r_tiled, want) < (1e-12 if prec == 64 else 5e-5)
+
+
 def test_deterministic_fp64():
     nodes, order = SIZES[6][1], 6
     X, mat, J, a, sch = _problem(nodes, order)
