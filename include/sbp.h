@@ -179,6 +179,27 @@ int sbp_status(SbpGrid* grid, uint32_t* bits, void* stream);
  * times c = row sums of the equivalent Butcher tableau). */
 int sbp_rk_coefficients(double* A, double* B, double* C);
 
+/* Energy of a state without allocating anything (no paper counterpart; an
+ * addition for callers that manage all device memory themselves, such as code
+ * whose framework owns a pooled allocator or that runs under a fixed memory
+ * budget reserved up front, and for which a cudaMalloc inside the library is
+ * not acceptable or may fail when device memory is nearly full).
+ * Computes what sbp_energy computes, from plain pointers instead of a bound
+ * grid: q (9 fields) and mat (3 fields: 1/(rho J), lambda/J, mu/J) in the
+ * layout of sbp_layout (row pitch ldq, field stride fs), precision 32 or 64,
+ * FP64 result in *out (host).  The partial sums live in a static device array
+ * of 4096 doubles (plus the result and a status word, 32.8 KB), one per device,
+ * kept until the process exits; nblocks (1..4096) partial sums are used, 0
+ * selects 1184 (what sbp_energy uses, which gives the same result).  Sizes
+ * outside these limits return SBP_ERR_ARG.  The first call on each device looks
+ * up the array's device address; make that first call before any stream
+ * capture.  Every call reuses the same array: calls that overlap on the GPU
+ * (other streams, other threads) race and must be serialised by the caller.
+ * Synchronises the stream; SBP_ERR_NONFINITE if the energy is not finite. */
+int sbp_energy_noalloc(const void* q, const void* mat, int32_t nq, int32_t nr, int32_t ns, int64_t ldq,
+                       int64_t fs, int32_t order, int32_t precision, int32_t nblocks, double* out,
+                       void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* sbp_last_error(void);
 

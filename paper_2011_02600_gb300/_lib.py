@@ -17,7 +17,7 @@ EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sb
             "sbp_set_material", "sbp_rhs", "sbp_rk_stage", "sbp_step_n", "sbp_set_kernel_path", "sbp_current",
             "sbp_kernel_timing", "sbp_kernel_times",
             "sbp_set_time", "sbp_get_time", "sbp_energy", "sbp_set_source", "sbp_set_receivers", "sbp_status",
-            "sbp_rk_coefficients", "sbp_last_error")
+            "sbp_rk_coefficients", "sbp_energy_noalloc", "sbp_last_error")
 
 
 class SbpError(RuntimeError):
@@ -74,6 +74,7 @@ def lib(path=None):
         "sbp_set_receivers": [P, i32, P, P, i32],
         "sbp_status": [P, ctypes.POINTER(ctypes.c_uint32), P],
         "sbp_rk_coefficients": [ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
+        "sbp_energy_noalloc": [P, P, i32, i32, i32, i64, i64, i32, i32, i32, ctypes.POINTER(dbl), P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -215,3 +216,12 @@ def sbp_rk_coefficients():
     A, B, C = (ctypes.c_double * 5)(), (ctypes.c_double * 5)(), (ctypes.c_double * 5)()
     _check(lib().sbp_rk_coefficients(A, B, C))
     return list(A), list(B), list(C)
+
+
+def sbp_energy_noalloc(q, mat, nodes, ldq, fs, order, precision, nblocks, stream):
+    """Energy from plain device pointers, with the library's static scratch (no allocation)."""
+    out = ctypes.c_double()
+    nq, nr, ns = nodes
+    _check(lib().sbp_energy_noalloc(_ptr(q), _ptr(mat), nq, nr, ns, ldq, fs, order, precision, nblocks,
+                                    ctypes.byref(out), stream))
+    return out.value

@@ -55,6 +55,10 @@ int stencil_reach(int order) { return order == 2 ? 2 : order == 4 ? 3 : 4; }  //
 
 }  // namespace
 
+namespace sbp {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace sbp
+
 struct SbpGrid {
   SbpGridDesc desc;
   sbp::Dims dims;
