@@ -246,8 +246,8 @@ def main():
     value = world * nodes * 5 * args.steps / (ms / 1e3) / 1e6
 
     # dominant kernel: the tiled interior kernel if it ran, else the general kernel
-    b = 6
-    interior_nodes = max(0, nq - 2 * b) * max(0, nr - 2 * b) * max(0, ns - 2 * b)
+    b, iq0 = 6, 8          # closure rows per face; the tiled box starts at q = 8 (16-byte aligned loads)
+    interior_nodes = max(0, nq - b - iq0) * max(0, nr - 2 * b) * max(0, ns - 2 * b)
     if kn[0] > 0:
         kind, launches, kms_tot, knodes = "interior", kn[0], kms[0], interior_nodes
     else:
@@ -259,14 +259,16 @@ def main():
     peaks = _peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     prof_traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic_per_launch.json")
-    if os.path.exists(tpath):
-        try:
-            tj = json.load(open(tpath))
-            if tj.get("kernel_source_digest") == _kernel_digest():
-                prof_traffic = tj.get("dram_bytes_per_launch")
-        except Exception:
-            prof_traffic = None
+    tpath = os.path.join(ROOT, "profiles", "stage_interior_traffic.txt")
+    if kind == "interior" and os.path.exists(tpath):
+        kv = {}
+        for ln in open(tpath):
+            if ":" in ln and not ln.startswith("#"):
+                a, b2 = ln.split(":", 1)
+                kv[a.strip()] = b2.strip()
+        if kv.get("kernel_source_digest") == _kernel_digest():
+            per_node = (float(kv["dram_bytes_per_node_stage0"]) + 4 * float(kv["dram_bytes_per_node_stage1to4"])) / 5
+            prof_traffic = per_node * knodes
 
     # end to end: state in from pinned host memory, one step, state and energy out, per step
     e2e = None

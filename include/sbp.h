@@ -65,6 +65,7 @@ extern "C" {
 #define SBP_STATUS_NONFINITE 1u
 #define SBP_STATUS_BAD_MESH 2u
 #define SBP_STATUS_BAD_MATERIAL 4u
+#define SBP_STATUS_TIMEOUT 8u      /* an asynchronous tile copy did not complete in time */
 
 typedef struct SbpGridDesc {
   int32_t nq, nr, ns;     /* nodes per axis; each >= sbp_min_nodes(order) */

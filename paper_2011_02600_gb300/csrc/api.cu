@@ -4,7 +4,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -52,6 +55,23 @@ void rk_stage_times(double c[5]) {
 
 int closure_b(int order) { return order == 2 ? 2 : order == 4 ? 4 : 6; }
 int stencil_reach(int order) { return order == 2 ? 2 : order == 4 ? 3 : 4; }  // max(r, q)
+// First q index of the tiled interior box: b rounded up to a multiple of 4 (and at least 4),
+// so that the tile loads, which start 4 nodes before the tile, begin on 16-byte boundaries.
+int interior_q0(int order) { return std::max(4, (closure_b(order) + 3) / 4 * 4); }
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
 
 }  // namespace
 
@@ -85,6 +105,9 @@ struct SbpGrid {
   void* traces = nullptr;
   int n_t = 0;
   bool use_interior = true;
+  // tensor maps of the tiled interior kernel, per state buffer (q0, q1)
+  bool tma_ok[2] = {false, false};
+  sbp::TmaSet tma[2];
   // optional per-kernel CUDA-event timing of the stage kernels (kind 0 = interior, 1 = slabs/general)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -103,7 +126,8 @@ sbp::BoxList slab_boxes(const SbpGrid* g, bool with_interior_box, sbp::Box* inte
     L.b[L.n] = sbp::Box{i0, i1, j0, j1, k0, k1};
     ++L.n;
   };
-  const sbp::Box in{b, nq - b, b, nr - b, b, ns - b};
+  const int iq0 = interior_q0(g->desc.order);
+  const sbp::Box in{iq0, nq - b, b, nr - b, b, ns - b};
   const bool has_in = in.i1 > in.i0 && in.j1 > in.j0 && in.k1 > in.k0;
   if (!has_in || with_interior_box) {
     add(0, nq, 0, nr, 0, ns);
@@ -113,7 +137,7 @@ sbp::BoxList slab_boxes(const SbpGrid* g, bool with_interior_box, sbp::Box* inte
     add(0, nq, 0, nr, ns - b, ns);       // s = 1 slab
     add(0, nq, 0, b, b, ns - b);         // r = 0 slab
     add(0, nq, nr - b, nr, b, ns - b);   // r = 1 slab
-    add(0, b, b, nr - b, b, ns - b);     // q = 0 slab
+    add(0, iq0, b, nr - b, b, ns - b);   // q = 0 slab (b rounded up to the tile alignment)
     add(nq - b, nq, b, nr - b, b, ns - b);  // q = 1 slab
     if (interior) *interior = in;
   }
@@ -139,6 +163,7 @@ sbp::StageArgs<T> make_args(const SbpGrid* g, const void* q, void* qout, int mod
   A.rk_b = (T)bcoef;
   A.dt = (T)dt;
   A.mode = mode;
+  A.status = g->status;
   const int N[3] = {g->desc.nq, g->desc.nr, g->desc.ns};
   const int b = closure_b(g->desc.order);
   (void)b;
@@ -187,6 +212,34 @@ struct TimedLaunch {
   }
 };
 
+// Tensor maps for the interior kernel's tile loads (see kernels_interior.cu): the state
+// (box 40 x 16 x 1 x 9), the metric vectors a_q (40 x 8 x 1 x 3), a_r (32 x 16 x 1 x 3),
+// a_s (32 x 8 x 1 x 3) and the coefficients (32 x 8 x 1 x 3).  Out-of-range elements
+// are filled with zeros.
+int encode_maps(const SbpGrid* g, const void* q, sbp::TmaSet* out) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return fail(SBP_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+  const sbp::Dims& d = g->dims;
+  const CUtensorMapDataType dt = g->elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  auto one = [&](CUtensorMap* m, const void* base, int nf, unsigned bx, unsigned by, unsigned bf) -> int {
+    const cuuint64_t dims[4] = {(cuuint64_t)d.nq, (cuuint64_t)d.nr, (cuuint64_t)d.ns, (cuuint64_t)nf};
+    const cuuint64_t strides[3] = {(cuuint64_t)d.ldq * g->elem, (cuuint64_t)d.plane * g->elem,
+                                   (cuuint64_t)d.fs * g->elem};
+    const cuuint32_t box[4] = {bx, by, 1, bf};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    CUresult r = enc(m, dt, 4, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SBP_OK : fail(SBP_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  };
+  int rc = one(&out->state, q, 9, 40, 16, 9);
+  if (!rc) rc = one(&out->met_q, g->met, 9, 40, 8, 3);
+  if (!rc) rc = one(&out->met_r, g->met, 9, 32, 16, 3);
+  if (!rc) rc = one(&out->met_s, g->met, 9, 32, 8, 3);
+  if (!rc) rc = one(&out->mat, g->mat, 3, 32, 8, 3);
+  return rc;
+}
+
 template <typename T>
 int run_stage_kernels(SbpGrid* g, const void* q, void* qout, int mode, double a, double bcoef, double dt,
                       cudaStream_t st) {
@@ -196,8 +249,20 @@ int run_stage_kernels(SbpGrid* g, const void* q, void* qout, int mode, double a,
   if (g->use_interior) {
     sbp::BoxList L = slab_boxes(g, false, &in);
     if (in.i1 > in.i0) {
+      sbp::TmaSet local;
+      const sbp::TmaSet* tm = &local;
+      const int which = q == g->q[0] ? 0 : q == g->q[1] ? 1 : -1;
+      if (which >= 0) {
+        if (!g->tma_ok[which]) {
+          if (int rc = encode_maps(g, q, &g->tma[which])) return rc;
+          g->tma_ok[which] = true;
+        }
+        tm = &g->tma[which];
+      } else if (int rc = encode_maps(g, q, &local)) {
+        return rc;
+      }
       TimedLaunch ti(g, 0, st);
-      cudaError_t e = sbp::launch_stage_interior<T>(A, g->desc.order, in, st);
+      cudaError_t e = sbp::launch_stage_interior<T>(A, g->desc.order, in, *tm, st);
       if (e == cudaSuccess) {
         ti.done();
         interior_done = true;
@@ -378,6 +443,7 @@ int sbp_bind(SbpGrid* g, void* q0, void* q1, void* dq, void* met, void* mat) {
   g->met = met;
   g->mat = mat;
   g->cur = 0;
+  g->tma_ok[0] = g->tma_ok[1] = false;
   if (!g->partial) {
     cudaError_t e = cudaMalloc(&g->partial, sizeof(double) * sbp::energy_blocks());
     if (e == cudaSuccess) e = cudaMalloc(&g->eout, sizeof(double));

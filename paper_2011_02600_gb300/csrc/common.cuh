@@ -43,6 +43,7 @@ struct StageArgs {
   T bc_gamma[6];
   T inv_h[3];       // N_xi - 1 (reference spacing 1/(N_xi - 1))
   T inv_h0[3];      // 1 / H_xi[0] = (N_xi - 1) / w_0
+  unsigned* status; // device status word (bit 8: a tile copy timed out)
 };
 
 // Closure rows of D+ and D- (unit spacing), one private copy per translation unit.

@@ -5,16 +5,18 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace sbp {
 
 template <typename T>
 cudaError_t launch_stage_general(const StageArgs<T>& A, int order, const BoxList& L, cudaStream_t st);
 
-// Tiled interior kernel over the box [b, N-1-b]^3 (returns cudaErrorNotSupported
-// when the interior is empty or the order has no tiled variant).
+// Tiled interior kernel over `box` (q-start a multiple of 4), tile data by TMA through
+// the tensor maps in `tm` (returns cudaErrorNotSupported when the box is empty).
 template <typename T>
-cudaError_t launch_stage_interior(const StageArgs<T>& A, int order, const Box& box, cudaStream_t st);
+cudaError_t launch_stage_interior(const StageArgs<T>& A, int order, const Box& box, const TmaSet& tm,
+                                  cudaStream_t st);
 
 cudaError_t launch_metrics(const double* xyz, double* jmet, const Dims& d, int order, unsigned* status,
                            cudaStream_t st);
