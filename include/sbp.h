@@ -173,6 +173,34 @@ int sbp_set_source(SbpGrid* grid, const SbpSource* src, const double* jmet, void
  * not recorded.  n = 0 removes the receivers. */
 int sbp_set_receivers(SbpGrid* grid, int32_t n, const int32_t* ijk, void* traces, int32_t n_t);
 
+/* Transposed operator: out = L^T w with L = P~ M the map Q -> dQ/dt of sbp_rhs
+ * (penalties included, no source), transposed in the plain Euclidean inner
+ * product of the 9-field vectors.  Built from the dual-pair relation of
+ * Section 4.1 (Eq. upw_SBP): D-^T = B H^-1 - H D+ H^-1, D+^T = B H^-1 - H D- H^-1,
+ * so it reuses the forward rows on H^-1 P~ w plus face terms.  w, out, scratch:
+ * 9 fields each (device, distinct). */
+int sbp_rhs_adjoint(SbpGrid* grid, const void* w, void* out, void* scratch, void* stream);
+
+/* Adjoint of fused Runge-Kutta stage k (the exact discrete adjoint of the
+ * 2N-storage stage; run k = 4..0 after the adjoint of a step's later stages):
+ *   wbar <- wbar + B_k ubar;  ubar <- ubar + dt L^T wbar;
+ *   grad += dt (d(L u_stage)/d(rho, lambda, mu))^T wbar;  wbar <- A_k wbar.
+ * ubar, wbar, scratch: 9 fields (solver precision, device, updated in place);
+ * u_stage: the forward stage input U_k (9 fields); rlmj: FP64 rho, lambda, mu, J
+ * (4 fields); grad: FP64 3 fields (accumulated; may be NULL to skip the gradient,
+ * then u_stage and rlmj may be NULL).  The impedances of the general penalty
+ * are differentiated too. */
+int sbp_adjoint_stage(SbpGrid* grid, int32_t stage, double dt, const void* u_stage, void* ubar, void* wbar,
+                      void* scratch, const double* rlmj, double* grad, void* stream);
+
+/* Receiver misfit of the state q (9 fields): for each receiver r and velocity
+ * component c, diff = v_c - data[3r + c] (data: FP64 device, 3 per receiver);
+ * acc[3r + c] += weight diff^2 / 2 (FP64 device, may be NULL) and, if ubar is
+ * not NULL, ubar_c += weight diff at the receiver node (the adjoint source).
+ * Needs sbp_set_receivers. */
+int sbp_misfit(SbpGrid* grid, const void* q, const double* data, double weight, double* acc, void* ubar,
+               void* stream);
+
 /* Copy the device status word into *bits and clear it (synchronises). */
 int sbp_status(SbpGrid* grid, uint32_t* bits, void* stream);
 

@@ -17,7 +17,8 @@ EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sb
             "sbp_set_material", "sbp_rhs", "sbp_rk_stage", "sbp_step_n", "sbp_set_kernel_path", "sbp_current",
             "sbp_kernel_timing", "sbp_kernel_times",
             "sbp_set_time", "sbp_get_time", "sbp_energy", "sbp_set_source", "sbp_set_receivers", "sbp_status",
-            "sbp_rk_coefficients", "sbp_energy_noalloc", "sbp_last_error")
+            "sbp_rk_coefficients", "sbp_energy_noalloc", "sbp_rhs_adjoint", "sbp_adjoint_stage",
+            "sbp_misfit", "sbp_last_error")
 
 
 class SbpError(RuntimeError):
@@ -75,6 +76,9 @@ def lib(path=None):
         "sbp_status": [P, ctypes.POINTER(ctypes.c_uint32), P],
         "sbp_rk_coefficients": [ctypes.POINTER(dbl), ctypes.POINTER(dbl), ctypes.POINTER(dbl)],
         "sbp_energy_noalloc": [P, P, i32, i32, i32, i64, i64, i32, i32, i32, ctypes.POINTER(dbl), P],
+        "sbp_rhs_adjoint": [P, P, P, P, P],
+        "sbp_adjoint_stage": [P, i32, dbl, P, P, P, P, P, P, P],
+        "sbp_misfit": [P, P, P, dbl, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -225,3 +229,16 @@ def sbp_energy_noalloc(q, mat, nodes, ldq, fs, order, precision, nblocks, stream
     _check(lib().sbp_energy_noalloc(_ptr(q), _ptr(mat), nq, nr, ns, ldq, fs, order, precision, nblocks,
                                     ctypes.byref(out), stream))
     return out.value
+
+
+def sbp_rhs_adjoint(h, w, out, scratch, stream):
+    _check(lib().sbp_rhs_adjoint(h, _ptr(w), _ptr(out), _ptr(scratch), stream))
+
+
+def sbp_adjoint_stage(h, stage, dt, u_stage, ubar, wbar, scratch, rlmj, grad, stream):
+    _check(lib().sbp_adjoint_stage(h, stage, dt, _ptr(u_stage), _ptr(ubar), _ptr(wbar), _ptr(scratch),
+                                   _ptr(rlmj), _ptr(grad), stream))
+
+
+def sbp_misfit(h, q, data, weight, acc, ubar, stream):
+    _check(lib().sbp_misfit(h, _ptr(q), _ptr(data), weight, _ptr(acc), _ptr(ubar), stream))

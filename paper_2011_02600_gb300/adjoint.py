@@ -1,0 +1,125 @@
+"""Receiver misfit and its material gradient by the discrete adjoint (torch autograd).
+
+The forward run is the library's fused Runge-Kutta stepping; the misfit
+Phi = sum_n 1/2 dt sum_r |v(x_r, t_{n+1}) - d_r,n|^2 is accumulated in FP64 by
+the misfit kernel.  The gradient with respect to rho, lambda and mu at every
+node comes from the exact adjoint of each fused stage (``sbp_adjoint_stage``)
+run backwards in time.  States are checkpointed every C = ceil(sqrt(N)) steps
+in the forward run; in the backward run each segment is recomputed from its
+checkpoint, and each step's five stage inputs are recomputed from the step's
+state before its adjoint stages run.
+"""
+import math
+
+import torch
+
+from . import _lib as L
+from .solver import _stream
+
+
+class MisfitProblem:
+    """solver: ElasticSolver set up with keep_metrics=True; receivers: (i, j, k) list;
+    data: FP64 tensor [n_rec][3][nsteps]; source: dict for ElasticSolver.set_source or None."""
+
+    def __init__(self, solver, receivers, data, dt, nsteps, source=None, checkpoint_every=None):
+        if solver.jmet is None:
+            raise ValueError("the solver must keep its metrics (setup(..., keep_metrics=True))")
+        self.s = solver
+        self.receivers = [tuple(int(x) for x in r) for r in receivers]
+        self.nsteps = int(nsteps)
+        self.dt = float(dt)
+        self.data = torch.as_tensor(data, dtype=torch.float64, device=solver.device).permute(2, 0, 1).contiguous()
+        self.C = int(checkpoint_every or max(1, math.ceil(math.sqrt(self.nsteps))))
+        self.source = source
+        s = solver
+        self.rlmj = s.new_fields(4, torch.float64)
+        self.acc = torch.zeros(len(self.receivers) * 3, dtype=torch.float64, device=s.device)
+        s.set_receivers(self.receivers, max(1, self.nsteps))
+        if source is not None:
+            s.set_source(**source)
+        self.ckpt = {}
+
+    def set_material(self, rho, lam, mu):
+        s = self.s
+        rlm = s.new_fields(3, torch.float64)
+        v = s.view(rlm, 3)
+        for f, m in enumerate((rho, lam, mu)):
+            v[f].copy_(torch.as_tensor(m, dtype=torch.float64))
+        L.sbp_set_material(s.h, s.jmet, rlm, _stream())
+        r = s.view(self.rlmj, 4)
+        r[:3].copy_(v)
+        r[3].copy_(s.view(s.jmet, 10)[0])
+        bits = s.status()
+        if bits & 6:
+            raise L.SbpError(6, f"material check failed (status {bits})")
+
+    def _reset(self):
+        s = self.s
+        for b in s.qbuf:
+            b.zero_()
+        s.dq.zero_()
+        s.set_time(0.0, 0)
+
+    def forward(self):
+        """Run the forward problem from rest; returns Phi (float) and keeps checkpoints."""
+        s = self.s
+        self._reset()
+        self.acc.zero_()
+        self.ckpt = {0: s.qbuf[s.current].clone()}
+        st = _stream()
+        for n in range(self.nsteps):
+            L.sbp_step_n(s.h, 1, self.dt, st)
+            L.sbp_misfit(s.h, s.qbuf[s.current], self.data[n], self.dt, self.acc, None, st)
+            if (n + 1) % self.C == 0 and n + 1 < self.nsteps:
+                self.ckpt[n + 1] = s.qbuf[s.current].clone()
+        return float(self.acc.sum())
+
+    def _load(self, q, n):
+        s = self.s
+        s.qbuf[s.current].copy_(q)
+        s.set_time(n * self.dt, n)
+
+    def gradient(self):
+        """d Phi / d(rho, lambda, mu): FP64 tensor [3][ns][nr][nq] (after forward())."""
+        s = self.s
+        st = _stream()
+        ubar = s.new_fields(9)
+        wbar = s.new_fields(9)
+        scratch = s.new_fields(9)
+        grad = s.new_fields(3, torch.float64)
+        stage_in = [s.new_fields(9) for _ in range(5)]
+        starts = sorted(self.ckpt)
+        for seg in reversed(starts):
+            end = min(seg + self.C, self.nsteps)
+            states = [self.ckpt[seg]]
+            self._load(self.ckpt[seg], seg)
+            for n in range(seg, end):
+                L.sbp_step_n(s.h, 1, self.dt, st)
+                states.append(s.qbuf[s.current].clone())
+            for n in reversed(range(seg, end)):
+                L.sbp_misfit(s.h, states[n + 1 - seg], self.data[n], self.dt, None, ubar, st)
+                self._load(states[n - seg], n)
+                for k in range(5):
+                    stage_in[k].copy_(s.qbuf[s.current])
+                    L.sbp_rk_stage(s.h, k, self.dt, st)
+                wbar.zero_()
+                for k in reversed(range(5)):
+                    L.sbp_adjoint_stage(s.h, k, self.dt, stage_in[k], ubar, wbar, scratch, self.rlmj, grad, st)
+            del states
+        return s.view(grad, 3).clone()
+
+
+class ElasticMisfit(torch.autograd.Function):
+    """Phi(rho, lambda, mu) with the adjoint gradient as backward."""
+
+    @staticmethod
+    def forward(ctx, rho, lam, mu, problem):
+        problem.set_material(rho, lam, mu)
+        phi = problem.forward()
+        ctx.problem = problem
+        return torch.tensor(phi, dtype=torch.float64, device=rho.device)
+
+    @staticmethod
+    def backward(ctx, g):
+        grad = ctx.problem.gradient()
+        return g * grad[0], g * grad[1], g * grad[2], None

@@ -348,6 +348,41 @@ void delta_1d(double xi0, int N, int m, int* start, double* phi) {
 
 }  // namespace
 
+namespace {
+template <typename T>
+int adjoint_impl(SbpGrid* g, int mode, int stage, double dt, const void* u, void* ubar, const void* win, void* wbar,
+                 void* scratch, const double* rlmj, double* grad, cudaStream_t st) {
+  sbp::AdjArgs<T> A;
+  A.ubar_next = mode == 1 ? (const T*)ubar : nullptr;
+  A.ubar_out = (T*)ubar;
+  A.wbar_in = (const T*)win;
+  A.wbar = (T*)wbar;
+  A.yhat = (T*)scratch;
+  A.u = (const T*)u;
+  A.met = (const T*)g->met;
+  A.mat = (const T*)g->mat;
+  A.rlmj = rlmj;
+  A.grad = grad;
+  A.d = g->dims;
+  A.rk_a = mode == 1 ? (T)kRkA[stage] : T(0);
+  A.rk_b = mode == 1 ? (T)kRkB[stage] : T(0);
+  A.dt = (T)dt;
+  A.mode = mode;
+  sbp::StageArgs<T> S = make_args<T>(g, nullptr, nullptr, 0, 0, 0, 0);
+  for (int f = 0; f < 6; ++f) {
+    A.bc_kind[f] = S.bc_kind[f];
+    A.bc_gamma[f] = S.bc_gamma[f];
+  }
+  for (int x = 0; x < 3; ++x) {
+    A.inv_h[x] = S.inv_h[x];
+    A.inv_h0[x] = S.inv_h0[x];
+  }
+  cudaError_t e = sbp::launch_adjoint<T>(A, g->desc.order, st);
+  return e == cudaSuccess ? SBP_OK : cuda_fail(e, "adjoint");
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* sbp_last_error(void) { return g_last_error.c_str(); }
@@ -664,6 +699,42 @@ int sbp_set_receivers(SbpGrid* g, int32_t n, const int32_t* ijk, void* traces, i
   g->traces = traces;
   g->n_t = n_t;
   return SBP_OK;
+}
+
+int sbp_rhs_adjoint(SbpGrid* g, const void* w, void* out, void* scratch, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
+  if (!w || !out || !scratch || w == out || w == scratch || out == scratch)
+    return fail(SBP_ERR_ARG, "rhs_adjoint needs distinct input, output and scratch buffers");
+  return g->elem == 4 ? adjoint_impl<float>(g, 0, 0, 0.0, nullptr, out, w, nullptr, scratch, nullptr, nullptr,
+                                            (cudaStream_t)stream)
+                      : adjoint_impl<double>(g, 0, 0, 0.0, nullptr, out, w, nullptr, scratch, nullptr, nullptr,
+                                             (cudaStream_t)stream);
+}
+
+int sbp_adjoint_stage(SbpGrid* g, int32_t stage, double dt, const void* u_stage, void* ubar, void* wbar,
+                      void* scratch, const double* rlmj, double* grad, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
+  if (stage < 0 || stage > 4) return fail(SBP_ERR_ARG, "stage must be 0..4");
+  if (!(dt > 0) || !isfinite(dt)) return fail(SBP_ERR_ARG, "dt must be positive and finite");
+  if (!ubar || !wbar || !scratch) return fail(SBP_ERR_ARG, "null adjoint buffer");
+  if (grad && (!u_stage || !rlmj)) return fail(SBP_ERR_ARG, "the gradient needs the stage state and rho, lambda, mu, J");
+  return g->elem == 4 ? adjoint_impl<float>(g, 1, stage, dt, u_stage, ubar, wbar, wbar, scratch, rlmj, grad,
+                                            (cudaStream_t)stream)
+                      : adjoint_impl<double>(g, 1, stage, dt, u_stage, ubar, wbar, wbar, scratch, rlmj, grad,
+                                             (cudaStream_t)stream);
+}
+
+int sbp_misfit(SbpGrid* g, const void* q, const double* data, double weight, double* acc, void* ubar, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (g->rec_n == 0) return fail(SBP_ERR_STATE, "no receivers set (sbp_set_receivers)");
+  if (!q || !data) return fail(SBP_ERR_ARG, "null state or data");
+  cudaError_t e = g->elem == 4 ? sbp::launch_misfit<float>((const float*)q, g->dims, g->rec_off, g->rec_n, data,
+                                                            weight, acc, (float*)ubar, (cudaStream_t)stream)
+                               : sbp::launch_misfit<double>((const double*)q, g->dims, g->rec_off, g->rec_n, data,
+                                                             weight, acc, (double*)ubar, (cudaStream_t)stream);
+  return e == cudaSuccess ? SBP_OK : cuda_fail(e, "misfit");
 }
 
 int sbp_status(SbpGrid* g, uint32_t* bits, void* stream) {

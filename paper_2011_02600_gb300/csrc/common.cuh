@@ -219,6 +219,71 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs<T>& A, long long 
   }
 }
 
+// Raw operator (P~^-1 dQ/dt: velocity rows rv, stress rows e, penalties included) of the
+// state q at one node with in-field offset n0 and axis positions pos, using every row of
+// D+ and D- (interior stencil or closure).  qc receives the node's own 9 values.
+template <typename T, int O>
+__device__ __forceinline__ void raw_operator_at(const T* __restrict__ q, const T* __restrict__ met,
+                                                const T* __restrict__ mat, const Dims& d, long long n0,
+                                                const int pos[3], const T inv_h[3], const T inv_h0[3],
+                                                const int bc_kind[6], const T bc_gamma[6], T rv[3], T e[6],
+                                                T qc[9]) {
+  const long long fs = d.fs;
+  const int N[3] = {d.nq, d.nr, d.ns};
+  const long long stride[3] = {1, d.ldq, d.plane};
+#pragma unroll
+  for (int c = 0; c < 3; ++c) rv[c] = T(0);
+#pragma unroll
+  for (int c = 0; c < 6; ++c) e[c] = T(0);
+#pragma unroll
+  for (int xi = 0; xi < 3; ++xi) {
+    const T* __restrict__ mx = met + (long long)(3 * xi) * fs;
+    T f[3] = {T(0), T(0), T(0)};
+    apply_row<T, O, false>(pos[xi], N[xi], [&](int c, T w) {
+      const long long nb = n0 + (long long)(c - pos[xi]) * stride[xi];
+      const T a[3] = {mx[nb], mx[fs + nb], mx[2 * fs + nb]};
+      T s[6];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) s[m] = q[(3 + m) * fs + nb];
+      T F[3];
+      flux(a, s, F);
+      f[0] += w * F[0];
+      f[1] += w * F[1];
+      f[2] += w * F[2];
+    });
+    rv[0] += inv_h[xi] * f[0];
+    rv[1] += inv_h[xi] * f[1];
+    rv[2] += inv_h[xi] * f[2];
+    T dv[3] = {T(0), T(0), T(0)};
+    apply_row<T, O, true>(pos[xi], N[xi], [&](int c, T w) {
+      const long long nb = n0 + (long long)(c - pos[xi]) * stride[xi];
+      dv[0] += w * q[nb];
+      dv[1] += w * q[fs + nb];
+      dv[2] += w * q[2 * fs + nb];
+    });
+    dv[0] *= inv_h[xi];
+    dv[1] *= inv_h[xi];
+    dv[2] *= inv_h[xi];
+    const T a0[3] = {mx[n0], mx[fs + n0], mx[2 * fs + n0]};
+    add_strain(a0, dv, e);
+  }
+#pragma unroll
+  for (int f = 0; f < 9; ++f) qc[f] = q[f * fs + n0];
+  const T irhoJ = mat[n0], lamJ = mat[fs + n0], muJ = mat[2 * fs + n0];
+#pragma unroll
+  for (int xi = 0; xi < 3; ++xi) {
+    const bool lo = pos[xi] == 0, hi = pos[xi] == N[xi] - 1;
+    if (!(lo || hi)) continue;
+    const T* __restrict__ mx = met + (long long)(3 * xi) * fs;
+    const T a0[3] = {mx[n0], mx[fs + n0], mx[2 * fs + n0]};
+    if (lo)
+      add_penalty<T>(0, bc_kind[2 * xi], bc_gamma[2 * xi], inv_h0[xi], qc, qc + 3, a0, irhoJ, lamJ, muJ, rv, e);
+    if (hi)
+      add_penalty<T>(1, bc_kind[2 * xi + 1], bc_gamma[2 * xi + 1], inv_h0[xi], qc, qc + 3, a0, irhoJ, lamJ, muJ,
+                     rv, e);
+  }
+}
+
 struct Box {
   int i0, i1, j0, j1, k0, k1;
 };
