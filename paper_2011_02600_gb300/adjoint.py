@@ -123,3 +123,43 @@ class ElasticMisfit(torch.autograd.Function):
     def backward(ctx, g):
         grad = ctx.problem.gradient()
         return g * grad[0], g * grad[1], g * grad[2], None
+
+
+def workload_materials(solver, cfg, anomaly):
+    """(rho, lambda, mu) of the workload's background (anomaly=False) or true model, on the device."""
+    from workloads.geometry import make_map, reference_axes
+    from workloads.media import make_medium
+    name = "smooth_anomaly" if anomaly else cfg.medium
+    fmap = make_map(cfg, xp=torch)
+    fmed = make_medium(name, xp=torch, **{**cfg.extra, "seed": cfg.seed})
+    q, r, s = reference_axes(cfg.nodes, torch, torch.float64, solver.device)
+    x, y, z = fmap(q, r, s)
+    shape = (cfg.nodes[2], cfg.nodes[1], cfg.nodes[0])
+    return tuple(m.expand(*shape).contiguous() for m in fmed(x, y, z))
+
+
+def workload_problem(cfg, precision, source_index=0, nsteps=None, checkpoint_every=None):
+    """MisfitProblem for the adjoint workload: data recorded with the true model (background
+    plus a Gaussian vs anomaly) for one of its seeded sources at the 64 surface receivers;
+    material set to the background.  Returns (problem, true_material, background_material)."""
+    from workloads.acquisition import moment_sources, surface_receivers
+    from .workload_setup import build_solver
+    from .source_util import moment_tensor_voigt
+    nsteps = nsteps or cfg.steps
+    s, info = build_solver(cfg, precision=precision, keep_metrics=True)
+    srcs = moment_sources(cfg.seed, cfg.extra.get("n_sources", 8))
+    sp = srcs[source_index]
+    Mv = moment_tensor_voigt(sp["strike"], sp["dip"], sp["rake"], sp["M0"])
+    rec = surface_receivers(cfg.nodes, 8)
+    n_rec = len(rec)
+    p = MisfitProblem(s, rec, torch.zeros(n_rec, 3, nsteps, dtype=torch.float64), info["dt"], nsteps,
+                      source=dict(ref=sp["ref"], moment=list(Mv), stf="ricker", f0=cfg.extra.get("f0", 2.0)),
+                      checkpoint_every=checkpoint_every)
+    true_m = workload_materials(s, cfg, anomaly=True)
+    back_m = workload_materials(s, cfg, anomaly=False)
+    p.set_material(*true_m)
+    p.forward()
+    data = s.traces.view(-1, 3, max(1, nsteps))[:n_rec].double()
+    p.data = data.permute(2, 0, 1).contiguous()
+    p.set_material(*back_m)
+    return p, true_m, back_m

@@ -57,9 +57,10 @@ CONFIGS = [
                    vk_hurst=0.5, vk_modes=64, pulse_width=600.0)),
     WorkloadConfig(
         name="adjoint129_o4", nodes=(129, 129, 97), extent=(20000.0, 20000.0, 15000.0),
-        geometry="gaussian_hill", order=4, precisions=(32,), medium="layered3",
+        geometry="gaussian_hill", order=4, precisions=(32,), medium="smooth_background",
         steps=1500, n_receivers=64, source="moment_tensor",
         extra=dict(hill_amp=1500.0, hill_sigma=4000.0, n_sources=8, anomaly_radius=500.0,
+                   anomaly_amp=0.1, anomaly_center=(10000.0, 10000.0, -3000.0), Lz=15000.0,
                    n_fd_directions=20, f0=2.0)),
     WorkloadConfig(
         name="surrogate97_o4", nodes=(97, 97, 97), extent=(20000.0, 20000.0, 15000.0),

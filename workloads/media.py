@@ -74,6 +74,24 @@ def make_medium(cfg_or_name, xp=np, **params):
             return lame(rho, math.sqrt(3.0) * vs, vs)
         return fmed
 
+    if name in ("smooth_background", "smooth_anomaly"):
+        # Smooth depth gradient over the block (vs 1.5 -> 3.5 km/s, rho 2200 -> 2700, vp = sqrt(3) vs);
+        # "smooth_anomaly" multiplies vs by 1 + a exp(-|x - x0|^2 / (2 r^2)) (a Gaussian vs anomaly).
+        Lz = params.get("Lz", 15000.0)
+        x0 = params.get("anomaly_center", (10000.0, 10000.0, -3000.0))
+        rad = params.get("anomaly_radius", 500.0)
+        amp = params.get("anomaly_amp", 0.1) if name == "smooth_anomaly" else 0.0
+
+        def fmed(x, y, z):
+            t = xp.clip(-z / Lz + 0 * x + 0 * y, 0.0, 1.0)
+            vs = 1500.0 + 2000.0 * t
+            rho = 2200.0 + 500.0 * t
+            if amp:
+                g = xp.exp(-((x - x0[0]) ** 2 + (y - x0[1]) ** 2 + (z - x0[2]) ** 2) / (2.0 * rad ** 2))
+                vs = vs * (1.0 + amp * g)
+            return lame(rho, math.sqrt(3.0) * vs, vs)
+        return fmed
+
     if name == "gradient_vonkarman":
         Lz = params.get("Lz", 24000.0)
         k, phi, A = vonkarman_modes(params.get("seed", 0), params.get("vk_modes", 64),
