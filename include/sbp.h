@@ -102,9 +102,16 @@ int sbp_destroy(SbpGrid* grid);
  * elements, and the element size in bytes of the solver precision. */
 int sbp_layout(const SbpGrid* grid, int64_t* ldq, int64_t* fs, int64_t* elem_bytes);
 
+/* Number of independent states B advanced together (the batched solver: many
+ * sources on one mesh and medium).  All B states share the metrics and
+ * coefficients; every stage kernel processes the B states in one launch.
+ * Call before sbp_bind; default 1.  B in 1..1024. */
+int sbp_set_batch(SbpGrid* grid, int32_t nb);
+
 /* Bind the caller's device buffers (solver precision, layout of sbp_layout):
- * q0, q1: 9 fields each (ping-pong state; q0 holds the state after binding),
- * dq: 9 fields (Runge-Kutta register), met: 9 fields, mat: 3 fields.
+ * q0, q1: 9 B fields each (ping-pong state; state b occupies fields 9b..9b+8;
+ * q0 holds the states after binding), dq: 9 B fields (Runge-Kutta register),
+ * met: 9 fields, mat: 3 fields (shared by the B states).
  * Pointers must be 256-byte aligned and distinct.  Allocates the library's
  * internal buffers on the current device. */
 int sbp_bind(SbpGrid* grid, void* q0, void* q1, void* dq, void* met, void* mat);
@@ -163,14 +170,18 @@ int sbp_get_time(const SbpGrid* grid, double* t, int64_t* step);
  * stream; NONFINITE if E is not finite. */
 int sbp_energy(SbpGrid* grid, double* out, void* stream);
 
-/* Place a point source (replaces any previous one).  jmet as for
- * sbp_set_material (J is read at the source's nodes). */
+/* Place a point source in state 0 (replaces any previous sources).  jmet as
+ * for sbp_set_material (J is read at the source's nodes). */
 int sbp_set_source(SbpGrid* grid, const SbpSource* src, const double* jmet, void* stream);
 
+/* One point source per state: srcs[b] acts on state b (n <= B).  The sources of
+ * one batch share their time function (stf, f0, t0, T); UNSUPPORTED otherwise. */
+int sbp_set_sources(SbpGrid* grid, int32_t n, const SbpSource* srcs, const double* jmet, void* stream);
+
 /* Receivers: n nodes given by host int32 (i, j, k) triples; traces is a device
- * buffer of n*3*n_t elements of the solver precision, trace[r][c][step]
- * (velocity component c of receiver r after step `step`); steps beyond n_t are
- * not recorded.  n = 0 removes the receivers. */
+ * buffer of B*n*3*n_t elements of the solver precision, trace[b][r][c][step]
+ * (velocity component c of receiver r in state b after step `step`); steps
+ * beyond n_t are not recorded.  n = 0 removes the receivers. */
 int sbp_set_receivers(SbpGrid* grid, int32_t n, const int32_t* ijk, void* traces, int32_t n_t);
 
 /* Transposed operator: out = L^T w with L = P~ M the map Q -> dQ/dt of sbp_rhs
@@ -181,7 +192,7 @@ int sbp_set_receivers(SbpGrid* grid, int32_t n, const int32_t* ijk, void* traces
  * 9 fields each (device, distinct). */
 int sbp_rhs_adjoint(SbpGrid* grid, const void* w, void* out, void* scratch, void* stream);
 
-/* Adjoint of fused Runge-Kutta stage k (the exact discrete adjoint of the
+/* (Unbatched grids only.)  Adjoint of fused Runge-Kutta stage k (the exact discrete adjoint of the
  * 2N-storage stage; run k = 4..0 after the adjoint of a step's later stages):
  *   wbar <- wbar + B_k ubar;  ubar <- ubar + dt L^T wbar;
  *   grad += dt (d(L u_stage)/d(rho, lambda, mu))^T wbar;  wbar <- A_k wbar.

@@ -18,7 +18,7 @@ EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sb
             "sbp_kernel_timing", "sbp_kernel_times",
             "sbp_set_time", "sbp_get_time", "sbp_energy", "sbp_set_source", "sbp_set_receivers", "sbp_status",
             "sbp_rk_coefficients", "sbp_energy_noalloc", "sbp_rhs_adjoint", "sbp_adjoint_stage",
-            "sbp_misfit", "sbp_last_error")
+            "sbp_misfit", "sbp_set_batch", "sbp_set_sources", "sbp_last_error")
 
 
 class SbpError(RuntimeError):
@@ -79,6 +79,8 @@ def lib(path=None):
         "sbp_rhs_adjoint": [P, P, P, P, P],
         "sbp_adjoint_stage": [P, i32, dbl, P, P, P, P, P, P, P],
         "sbp_misfit": [P, P, P, dbl, P, P, P],
+        "sbp_set_batch": [P, i32],
+        "sbp_set_sources": [P, i32, ctypes.POINTER(SbpSource), P, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -242,3 +244,19 @@ def sbp_adjoint_stage(h, stage, dt, u_stage, ubar, wbar, scratch, rlmj, grad, st
 
 def sbp_misfit(h, q, data, weight, acc, ubar, stream):
     _check(lib().sbp_misfit(h, _ptr(q), _ptr(data), weight, _ptr(acc), _ptr(ubar), stream))
+
+
+def sbp_set_batch(h, nb):
+    _check(lib().sbp_set_batch(h, nb))
+
+
+def sbp_set_sources(h, sources, jmet, stream):
+    """sources: list of dicts with ref, moment, stf (0/1), f0, t0, T."""
+    arr = (SbpSource * max(1, len(sources)))()
+    for m, src in enumerate(sources):
+        for a in range(3):
+            arr[m].ref[a] = src["ref"][a]
+        for c in range(6):
+            arr[m].moment[c] = src["moment"][c]
+        arr[m].stf, arr[m].f0, arr[m].t0, arr[m].T = src["stf"], src["f0"], src["t0"], src.get("T", 0.1)
+    _check(lib().sbp_set_sources(h, len(sources), arr, _ptr(jmet), stream))

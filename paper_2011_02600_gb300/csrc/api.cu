@@ -96,7 +96,8 @@ struct SbpGrid {
   double* partial = nullptr;
   double* eout = nullptr;
   unsigned* status = nullptr;
-  int32_t* src_off = nullptr;
+  int nb = 1;  // independent states bound together (sbp_set_batch)
+  long long* src_off = nullptr;
   double* src_w = nullptr;
   int src_n = 0;
   SbpSource src;
@@ -151,8 +152,10 @@ sbp::BoxList slab_boxes(const SbpGrid* g, bool with_interior_box, sbp::Box* inte
 
 template <typename T>
 sbp::StageArgs<T> make_args(const SbpGrid* g, const void* q, void* qout, int mode, double a, double bcoef,
-                            double dt) {
+                            double dt, int nb = 1) {
   sbp::StageArgs<T> A;
+  A.nb = nb;
+  A.bstride = 9 * g->dims.fs;
   A.q = (const T*)q;
   A.qout = (T*)qout;
   A.dq = (T*)g->dq;
@@ -216,7 +219,7 @@ struct TimedLaunch {
 // (box 40 x 16 x 1 x 9), the metric vectors a_q (40 x 8 x 1 x 3), a_r (32 x 16 x 1 x 3),
 // a_s (32 x 8 x 1 x 3) and the coefficients (32 x 8 x 1 x 3).  Out-of-range elements
 // are filled with zeros.
-int encode_maps(const SbpGrid* g, const void* q, sbp::TmaSet* out) {
+int encode_maps(const SbpGrid* g, const void* q, int nb, sbp::TmaSet* out) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return fail(SBP_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
   const sbp::Dims& d = g->dims;
@@ -232,7 +235,7 @@ int encode_maps(const SbpGrid* g, const void* q, sbp::TmaSet* out) {
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? SBP_OK : fail(SBP_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   };
-  int rc = one(&out->state, q, 9, 40, 16, 9);
+  int rc = one(&out->state, q, 9 * nb, 40, 16, 9);
   if (!rc) rc = one(&out->met_q, g->met, 9, 40, 8, 3);
   if (!rc) rc = one(&out->met_r, g->met, 9, 32, 16, 3);
   if (!rc) rc = one(&out->met_s, g->met, 9, 32, 8, 3);
@@ -242,8 +245,8 @@ int encode_maps(const SbpGrid* g, const void* q, sbp::TmaSet* out) {
 
 template <typename T>
 int run_stage_kernels(SbpGrid* g, const void* q, void* qout, int mode, double a, double bcoef, double dt,
-                      cudaStream_t st) {
-  sbp::StageArgs<T> A = make_args<T>(g, q, qout, mode, a, bcoef, dt);
+                      cudaStream_t st, int nb = 1) {
+  sbp::StageArgs<T> A = make_args<T>(g, q, qout, mode, a, bcoef, dt, nb);
   sbp::Box in;
   bool interior_done = false;
   if (g->use_interior) {
@@ -251,14 +254,14 @@ int run_stage_kernels(SbpGrid* g, const void* q, void* qout, int mode, double a,
     if (in.i1 > in.i0) {
       sbp::TmaSet local;
       const sbp::TmaSet* tm = &local;
-      const int which = q == g->q[0] ? 0 : q == g->q[1] ? 1 : -1;
+      const int which = nb == g->nb ? (q == g->q[0] ? 0 : q == g->q[1] ? 1 : -1) : -1;
       if (which >= 0) {
         if (!g->tma_ok[which]) {
-          if (int rc = encode_maps(g, q, &g->tma[which])) return rc;
+          if (int rc = encode_maps(g, q, nb, &g->tma[which])) return rc;
           g->tma_ok[which] = true;
         }
         tm = &g->tma[which];
-      } else if (int rc = encode_maps(g, q, &local)) {
+      } else if (int rc = encode_maps(g, q, nb, &local)) {
         return rc;
       }
       TimedLaunch ti(g, 0, st);
@@ -300,7 +303,7 @@ int stage_impl(SbpGrid* g, int k, double dt, cudaStream_t st) {
   const void* qin = g->q[g->cur];
   void* qout = g->q[1 - g->cur];
   const int mode = k == 0 ? sbp::kModeStage0 : sbp::kModeStage;
-  int rc = run_stage_kernels<T>(g, qin, qout, mode, kRkA[k], kRkB[k], dt, st);
+  int rc = run_stage_kernels<T>(g, qin, qout, mode, kRkA[k], kRkB[k], dt, st, g->nb);
   if (rc) return rc;
   if (g->src_n > 0) {
     const double gdt = stf_value(g->src, g->t + g->rkc[k] * dt) * dt;
@@ -541,9 +544,11 @@ int sbp_step_n(SbpGrid* g, int32_t n, double dt, void* stream) {
     if (g->rec_n > 0) {
       cudaError_t e = g->elem == 4
                           ? sbp::launch_receivers<float>((const float*)g->q[g->cur], g->dims, g->rec_off, g->rec_n,
-                                                         (float*)g->traces, g->n_t, g->step, st)
+                                                         g->nb, 9 * g->dims.fs, (float*)g->traces, g->n_t, g->step,
+                                                         st)
                           : sbp::launch_receivers<double>((const double*)g->q[g->cur], g->dims, g->rec_off,
-                                                          g->rec_n, (double*)g->traces, g->n_t, g->step, st);
+                                                          g->rec_n, g->nb, 9 * g->dims.fs, (double*)g->traces,
+                                                          g->n_t, g->step, st);
       if (e != cudaSuccess) return cuda_fail(e, "receivers");
     }
     ++g->step;
@@ -623,58 +628,79 @@ int sbp_energy(SbpGrid* g, double* out, void* stream) {
   return SBP_OK;
 }
 
-int sbp_set_source(SbpGrid* g, const SbpSource* src, const double* jmet, void* stream) {
+int sbp_set_sources(SbpGrid* g, int32_t n, const SbpSource* srcs, const double* jmet, void* stream) {
   if (int rc = check_ready(g)) return rc;
-  if (!src) {
+  if (n == 0 || !srcs) {
     g->src_n = 0;
     return SBP_OK;
   }
+  if (n < 0 || n > g->nb) return fail(SBP_ERR_ARG, "at most one source per bound state (%d states)", g->nb);
   if (!jmet) return fail(SBP_ERR_ARG, "set_source needs the FP64 Jacobian (jmet)");
-  for (int a = 0; a < 3; ++a)
-    if (!(src->ref[a] >= 0.0 && src->ref[a] <= 1.0)) return fail(SBP_ERR_ARG, "source outside the reference cube");
-  if (src->stf != 0 && src->stf != 1) return fail(SBP_ERR_ARG, "unknown source time function");
+  for (int m = 0; m < n; ++m) {
+    const SbpSource* src = &srcs[m];
+    for (int a = 0; a < 3; ++a)
+      if (!(src->ref[a] >= 0.0 && src->ref[a] <= 1.0)) return fail(SBP_ERR_ARG, "source outside the reference cube");
+    if (src->stf != 0 && src->stf != 1) return fail(SBP_ERR_ARG, "unknown source time function");
+    if (src->stf != srcs[0].stf || src->f0 != srcs[0].f0 || src->t0 != srcs[0].t0 || src->T != srcs[0].T)
+      return fail(SBP_ERR_UNSUPPORTED, "sources of one batch must share their time function");
+  }
   const int order = g->desc.order;
-  const int m = order + 1;
+  const int mo = order + 1;
   const int N[3] = {g->desc.nq, g->desc.nr, g->desc.ns};
-  int start[3];
-  double phi[3][8];
-  for (int a = 0; a < 3; ++a) delta_1d(src->ref[a], N[a], m, &start[a], phi[a]);
-  const int n1 = m + 1, nn = n1 * n1 * n1;
-  std::vector<int32_t> off(nn);
-  std::vector<double> J(nn), w(nn * 6);
+  const int n1 = mo + 1, per = n1 * n1 * n1;
+  std::vector<long long> off((size_t)per * n);
+  std::vector<double> w((size_t)per * n * 6);
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaStreamSynchronize(st);
-  for (int kk = 0, n = 0; kk < n1; ++kk)
-    for (int jj = 0; jj < n1; ++jj)
-      for (int ii = 0; ii < n1; ++ii, ++n) {
-        off[n] = (int32_t)((long long)(start[2] + kk) * g->dims.plane + (long long)(start[1] + jj) * g->dims.ldq +
-                           start[0] + ii);
-        if (e == cudaSuccess) e = cudaMemcpy(&J[n], jmet + off[n], sizeof(double), cudaMemcpyDeviceToHost);
-      }
-  if (e != cudaSuccess) return cuda_fail(e, "source Jacobian readback");
   auto wgt = [&](int a, int pos) {
     const double w0 = order == 2 ? sbp::norm_weight<2>(pos, N[a])
                       : order == 4 ? sbp::norm_weight<4>(pos, N[a]) : sbp::norm_weight<6>(pos, N[a]);
     return w0 / (N[a] - 1);
   };
-  for (int kk = 0, n = 0; kk < n1; ++kk)
-    for (int jj = 0; jj < n1; ++jj)
-      for (int ii = 0; ii < n1; ++ii, ++n) {
-        const double H = wgt(0, start[0] + ii) * wgt(1, start[1] + jj) * wgt(2, start[2] + kk);
-        const double delta = phi[0][ii] * phi[1][jj] * phi[2][kk] / (J[n] * H);
-        for (int c = 0; c < 6; ++c) w[n * 6 + c] = -src->moment[c] * delta;
-      }
+  for (int m = 0; m < n && e == cudaSuccess; ++m) {
+    const SbpSource* src = &srcs[m];
+    int start[3];
+    double phi[3][8];
+    for (int a = 0; a < 3; ++a) delta_1d(src->ref[a], N[a], mo, &start[a], phi[a]);
+    for (int kk = 0, c = 0; kk < n1; ++kk)
+      for (int jj = 0; jj < n1; ++jj)
+        for (int ii = 0; ii < n1; ++ii, ++c) {
+          const long long node = (long long)(start[2] + kk) * g->dims.plane + (long long)(start[1] + jj) * g->dims.ldq +
+                                 start[0] + ii;
+          double J = 0.0;
+          if (e == cudaSuccess) e = cudaMemcpy(&J, jmet + node, sizeof(double), cudaMemcpyDeviceToHost);
+          const double H = wgt(0, start[0] + ii) * wgt(1, start[1] + jj) * wgt(2, start[2] + kk);
+          const double delta = phi[0][ii] * phi[1][jj] * phi[2][kk] / (J * H);
+          const size_t idx = (size_t)m * per + c;
+          off[idx] = (long long)m * 9 * g->dims.fs + node;
+          for (int q = 0; q < 6; ++q) w[idx * 6 + q] = -src->moment[q] * delta;
+        }
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "source Jacobian readback");
   cudaFree(g->src_off);
   cudaFree(g->src_w);
   g->src_off = nullptr;
   g->src_w = nullptr;
-  e = cudaMalloc(&g->src_off, sizeof(int32_t) * nn);
+  const size_t nn = (size_t)per * n;
+  e = cudaMalloc(&g->src_off, sizeof(long long) * nn);
   if (e == cudaSuccess) e = cudaMalloc(&g->src_w, sizeof(double) * nn * 6);
-  if (e == cudaSuccess) e = cudaMemcpy(g->src_off, off.data(), sizeof(int32_t) * nn, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(g->src_off, off.data(), sizeof(long long) * nn, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(g->src_w, w.data(), sizeof(double) * nn * 6, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "source buffers");
-  g->src = *src;
-  g->src_n = nn;
+  g->src = srcs[0];
+  g->src_n = (int)nn;
+  return SBP_OK;
+}
+
+int sbp_set_source(SbpGrid* g, const SbpSource* src, const double* jmet, void* stream) {
+  return sbp_set_sources(g, src ? 1 : 0, src, jmet, stream);
+}
+
+int sbp_set_batch(SbpGrid* g, int32_t nb) {
+  if (!g) return fail(SBP_ERR_ARG, "null grid");
+  if (g->bound) return fail(SBP_ERR_STATE, "sbp_set_batch must come before sbp_bind");
+  if (nb < 1 || nb > 1024) return fail(SBP_ERR_ARG, "batch must lie in 1..1024");
+  g->nb = nb;
   return SBP_OK;
 }
 
@@ -715,6 +741,7 @@ int sbp_rhs_adjoint(SbpGrid* g, const void* w, void* out, void* scratch, void* s
 int sbp_adjoint_stage(SbpGrid* g, int32_t stage, double dt, const void* u_stage, void* ubar, void* wbar,
                       void* scratch, const double* rlmj, double* grad, void* stream) {
   if (int rc = check_ready(g)) return rc;
+  if (g->nb != 1) return fail(SBP_ERR_UNSUPPORTED, "the adjoint runs on unbatched grids");
   if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
   if (stage < 0 || stage > 4) return fail(SBP_ERR_ARG, "stage must be 0..4");
   if (!(dt > 0) || !isfinite(dt)) return fail(SBP_ERR_ARG, "dt must be positive and finite");

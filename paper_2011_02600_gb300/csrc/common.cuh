@@ -44,6 +44,8 @@ struct StageArgs {
   T inv_h[3];       // N_xi - 1 (reference spacing 1/(N_xi - 1))
   T inv_h0[3];      // 1 / H_xi[0] = (N_xi - 1) / w_0
   unsigned* status; // device status word (bit 8: a tile copy timed out)
+  int nb;           // independent states processed together (shared metrics and coefficients)
+  long long bstride;  // elements between consecutive states (9 fields)
 };
 
 // Closure rows of D+ and D- (unit spacing), one private copy per translation unit.

@@ -206,7 +206,7 @@ template cudaError_t launch_energy<double>(const double*, const double*, const D
 // stress rates gain g(t) * wsrc, i.e. dq += dt g w and qout += B dt g w
 // (the stage update is linear in the rate).
 template <typename T>
-__global__ void source_kernel(T* __restrict__ qout, T* __restrict__ dq, Dims d, const int32_t* __restrict__ off,
+__global__ void source_kernel(T* __restrict__ qout, T* __restrict__ dq, Dims d, const long long* __restrict__ off,
                               const double* __restrict__ wsrc, int nnodes, double gdt, double rk_b, int mode) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nnodes * 6) return;
@@ -222,38 +222,38 @@ __global__ void source_kernel(T* __restrict__ qout, T* __restrict__ dq, Dims d, 
 }
 
 template <typename T>
-cudaError_t launch_source(T* qout, T* dq, const Dims& d, const int32_t* off, const double* wsrc, int nnodes,
+cudaError_t launch_source(T* qout, T* dq, const Dims& d, const long long* off, const double* wsrc, int nnodes,
                           double gdt, double rk_b, int mode, cudaStream_t st) {
   if (nnodes == 0) return cudaSuccess;
   source_kernel<T><<<(nnodes * 6 + 127) / 128, 128, 0, st>>>(qout, dq, d, off, wsrc, nnodes, gdt, rk_b, mode);
   return cudaGetLastError();
 }
-template cudaError_t launch_source<float>(float*, float*, const Dims&, const int32_t*, const double*, int,
+template cudaError_t launch_source<float>(float*, float*, const Dims&, const long long*, const double*, int,
                                           double, double, int, cudaStream_t);
-template cudaError_t launch_source<double>(double*, double*, const Dims&, const int32_t*, const double*, int,
+template cudaError_t launch_source<double>(double*, double*, const Dims&, const long long*, const double*, int,
                                            double, double, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// Receivers: trace[r][c][step] = v_c at the receiver node.
+// Receivers: trace[b][r][c][step] = v_c of state b at the receiver node.
 template <typename T>
-__global__ void receivers_kernel(const T* __restrict__ q, Dims d, const int32_t* __restrict__ off, int n,
-                                 T* __restrict__ traces, int n_t, long long step) {
+__global__ void receivers_kernel(const T* __restrict__ q, Dims d, const int32_t* __restrict__ off, int n, int nb,
+                                 long long bstride, T* __restrict__ traces, int n_t, long long step) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * 3 || step >= n_t) return;
-  const int r = t / 3, c = t % 3;
-  traces[(long long)t * n_t + step] = q[(long long)c * d.fs + off[r]];
+  if (t >= nb * n * 3 || step >= n_t) return;
+  const int b = t / (3 * n), r = (t / 3) % n, c = t % 3;
+  traces[(long long)t * n_t + step] = q[(long long)b * bstride + (long long)c * d.fs + off[r]];
 }
 
 template <typename T>
-cudaError_t launch_receivers(const T* q, const Dims& d, const int32_t* off, int n, T* traces, int n_t,
-                             long long step, cudaStream_t st) {
+cudaError_t launch_receivers(const T* q, const Dims& d, const int32_t* off, int n, int nb, long long bstride,
+                             T* traces, int n_t, long long step, cudaStream_t st) {
   if (n == 0 || step >= n_t) return cudaSuccess;
-  receivers_kernel<T><<<(n * 3 + 127) / 128, 128, 0, st>>>(q, d, off, n, traces, n_t, step);
+  receivers_kernel<T><<<(nb * n * 3 + 127) / 128, 128, 0, st>>>(q, d, off, n, nb, bstride, traces, n_t, step);
   return cudaGetLastError();
 }
-template cudaError_t launch_receivers<float>(const float*, const Dims&, const int32_t*, int, float*, int,
-                                             long long, cudaStream_t);
-template cudaError_t launch_receivers<double>(const double*, const Dims&, const int32_t*, int, double*, int,
-                                              long long, cudaStream_t);
+template cudaError_t launch_receivers<float>(const float*, const Dims&, const int32_t*, int, int, long long, float*,
+                                             int, long long, cudaStream_t);
+template cudaError_t launch_receivers<double>(const double*, const Dims&, const int32_t*, int, int, long long,
+                                              double*, int, long long, cudaStream_t);
 
 }  // namespace sbp

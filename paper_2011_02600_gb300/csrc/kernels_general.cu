@@ -10,6 +10,11 @@ namespace sbp {
 
 template <typename T, int O>
 __global__ void __launch_bounds__(256) stage_general_kernel(StageArgs<T> A, BoxList L) {
+  // member blockIdx.y of a batch of independent states
+  const long long boff = (long long)blockIdx.y * A.bstride;
+  A.q += boff;
+  A.qout += boff;
+  if (A.mode != kModeRhs) A.dq += boff;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= L.off[L.n]) return;
   int bi = 0;
@@ -39,10 +44,11 @@ cudaError_t launch_stage_general(const StageArgs<T>& A, int order, const BoxList
   if (total == 0) return cudaSuccess;
   const int threads = 256;
   const long long blocks = (total + threads - 1) / threads;
+  const dim3 grid((unsigned)blocks, (unsigned)A.nb);
   switch (order) {
-    case 2: stage_general_kernel<T, 2><<<(unsigned)blocks, threads, 0, st>>>(A, L); break;
-    case 4: stage_general_kernel<T, 4><<<(unsigned)blocks, threads, 0, st>>>(A, L); break;
-    case 6: stage_general_kernel<T, 6><<<(unsigned)blocks, threads, 0, st>>>(A, L); break;
+    case 2: stage_general_kernel<T, 2><<<grid, threads, 0, st>>>(A, L); break;
+    case 4: stage_general_kernel<T, 4><<<grid, threads, 0, st>>>(A, L); break;
+    case 6: stage_general_kernel<T, 6><<<grid, threads, 0, st>>>(A, L); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

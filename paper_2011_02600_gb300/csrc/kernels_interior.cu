@@ -55,11 +55,11 @@ constexpr int interior_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
 
 template <typename T>
 __device__ __forceinline__ void issue_plane(InteriorShared<T>& S, int stage, const TmaSet& tm, int i0, int j0,
-                                            int k) {
+                                            int k, int member) {
   unsigned long long* bar = &S.bar[stage];
   mbar_expect_tx(bar, (unsigned)sizeof(Stage<T>));
   Stage<T>& st = S.st[stage];
-  tma_load_4d(&st.state[0][0][0], &tm.state, i0 - HX, j0 - HX, k, 0, bar);
+  tma_load_4d(&st.state[0][0][0], &tm.state, i0 - HX, j0 - HX, k, 9 * member, bar);
   tma_load_4d(&st.aq[0][0][0], &tm.met_q, i0 - HX, j0, k, 0, bar);
   tma_load_4d(&st.ar[0][0][0], &tm.met_r, i0, j0 - HX, k, 3, bar);
   tma_load_4d(&st.as[0][0][0], &tm.met_s, i0, j0, k, 6, bar);
@@ -84,12 +84,18 @@ __global__ void __launch_bounds__(TX* TY, interior_min_blocks<T>())
   const int i0 = box.i0 + blockIdx.x * TX;
   const int j0 = box.j0 + blockIdx.y * TY;
   const int i = i0 + tx, j = j0 + ty;
-  const int kb = box.k0 + blockIdx.z * chunk;
+  // blockIdx.z = chunk + nchunks * member (a batch of independent states)
+  const int nchunks = gridDim.z / A.nb;
+  const int member = blockIdx.z / nchunks;
+  const int kb = box.k0 + (blockIdx.z % nchunks) * chunk;
   const int ke = min(box.k1, kb + chunk);
   const bool in_grid = i < d.nq && j < d.nr;
   const bool active = i < box.i1 && j < box.j1;
   const T ihq = A.inv_h[0], ihr = A.inv_h[1], ihs = A.inv_h[2];
-  const T* __restrict__ q = A.q;
+  const long long boff = (long long)member * A.bstride;
+  const T* __restrict__ q = A.q + boff;
+  T* __restrict__ qout = A.qout + boff;
+  T* __restrict__ dqm = A.dq + (A.mode == kModeRhs ? 0 : boff);
   const T* __restrict__ met = A.met;
   const int col = j * d.ldq + i;
 
@@ -99,7 +105,7 @@ __global__ void __launch_bounds__(TX* TY, interior_min_blocks<T>())
     fence_mbar_init();
   }
   __syncthreads();
-  if (tid == 0) issue_plane(S, 0, tm, i0, j0, kb);
+  if (tid == 0) issue_plane(S, 0, tm, i0, j0, kb, member);
 
   auto ld = [&](const T* p, long long off) -> T { return in_grid ? __ldg(p + off) : T(0); };
   T vq[NV][3];  // v at planes k-R .. k+Q
@@ -148,7 +154,7 @@ __global__ void __launch_bounds__(TX* TY, interior_min_blocks<T>())
     T dqi[9];
     if (A.mode == kModeStage) {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) dqi[c] = ld(A.dq, c * fs + off);
+      for (int c = 0; c < 9; ++c) dqi[c] = ld(dqm, c * fs + off);
     }
 
     if (!mbar_wait_bounded(&S.bar[sidx], phase, kWaitLimit)) {
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(TX* TY, interior_min_blocks<T>())
     __syncthreads();
     if (tid == 0 && k + 1 < ke) {
       fence_proxy_async_smem();
-      issue_plane(S, sidx ^ 1, tm, i0, j0, k + 1);
+      issue_plane(S, sidx ^ 1, tm, i0, j0, k + 1, member);
     }
 
     T rv[3] = {T(0), T(0), T(0)};
@@ -247,14 +253,14 @@ __global__ void __launch_bounds__(TX* TY, interior_min_blocks<T>())
       for (int c = 0; c < 9; ++c) qc[c] = st.state[c][HX + ty][HX + tx];
       if (A.mode == kModeRhs) {
 #pragma unroll
-        for (int f = 0; f < 9; ++f) A.qout[f * fs + off] = dd[f];
+        for (int f = 0; f < 9; ++f) qout[f * fs + off] = dd[f];
       } else {
 #pragma unroll
         for (int f = 0; f < 9; ++f) {
           T dn = A.dt * dd[f];
           if (A.mode == kModeStage) dn += A.rk_a * dqi[f];
-          A.dq[f * fs + off] = dn;
-          A.qout[f * fs + off] = qc[f] + A.rk_b * dn;
+          dqm[f * fs + off] = dn;
+          qout[f * fs + off] = qc[f] + A.rk_b * dn;
         }
       }
     }
@@ -273,7 +279,8 @@ cudaError_t launch_interior_order(const StageArgs<T>& A, const Box& box, const T
   const int ni = box.i1 - box.i0, nj = box.j1 - box.j0, nk = box.k1 - box.k0;
   const int nchunks = (nk + 95) / 96;
   const int chunk = (nk + nchunks - 1) / nchunks;
-  dim3 grid((ni + TX - 1) / TX, (nj + TY - 1) / TY, (nk + chunk - 1) / chunk);
+  dim3 grid((ni + TX - 1) / TX, (nj + TY - 1) / TY, ((nk + chunk - 1) / chunk) * A.nb);
+  if (grid.z > 65535 || grid.y > 65535) return cudaErrorInvalidConfiguration;
   dim3 block(TX, TY);
   const size_t smem = sizeof(InteriorShared<T>);
   cudaError_t e = cudaFuncSetAttribute(stage_interior_kernel<T, O>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -61,11 +61,11 @@ cudaError_t launch_energy(const T* q, const T* mat, const Dims& d, int order, do
 int energy_blocks();
 
 template <typename T>
-cudaError_t launch_source(T* qout, T* dq, const Dims& d, const int32_t* off, const double* wsrc,
+cudaError_t launch_source(T* qout, T* dq, const Dims& d, const long long* off, const double* wsrc,
                           int nnodes, double gdt, double rk_b, int mode, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_receivers(const T* q, const Dims& d, const int32_t* off, int n, T* traces,
-                             int n_t, long long step, cudaStream_t st);
+cudaError_t launch_receivers(const T* q, const Dims& d, const int32_t* off, int n, int nb, long long bstride,
+                             T* traces, int n_t, long long step, cudaStream_t st);
 
 }  // namespace sbp

@@ -25,7 +25,7 @@ class ElasticSolver:
     bc: six face conditions ("free",) / ("char", gamma).
     """
 
-    def __init__(self, nodes, order, precision=32, bc=None, device="cuda"):
+    def __init__(self, nodes, order, precision=32, bc=None, device="cuda", batch=1):
         if bc is None:
             bc = [("char", 0.0)] * 5 + [("free",)]
         self.nodes = tuple(int(n) for n in nodes)
@@ -35,10 +35,14 @@ class ElasticSolver:
         self.device = torch.device(device)
         self.dtype = torch.float32 if precision == 32 else torch.float64
         self.h = L.sbp_create_grid(self.nodes, order, precision, self.bc)
+        self.batch = int(batch)
+        if self.batch != 1:
+            L.sbp_set_batch(self.h, self.batch)
         self.ldq, self.fs, self.elem = L.sbp_layout(self.h)
         kw = dict(dtype=self.dtype, device=self.device)
-        self.qbuf = [torch.zeros(9 * self.fs, **kw), torch.zeros(9 * self.fs, **kw)]
-        self.dq = torch.zeros(9 * self.fs, **kw)
+        nst = 9 * self.batch
+        self.qbuf = [torch.zeros(nst * self.fs, **kw), torch.zeros(nst * self.fs, **kw)]
+        self.dq = torch.zeros(nst * self.fs, **kw)
         self.met = torch.zeros(9 * self.fs, **kw)
         self.mat = torch.zeros(3 * self.fs, **kw)
         L.sbp_bind(self.h, self.qbuf[0], self.qbuf[1], self.dq, self.met, self.mat)
@@ -98,9 +102,9 @@ class ElasticSolver:
     def current(self):
         return L.sbp_current(self.h)
 
-    def state(self):
-        """(9, ns, nr, nq) view of the current state."""
-        return self.view(self.qbuf[self.current], 9)
+    def state(self, member=0):
+        """(9, ns, nr, nq) view of the current state (of batch member `member`)."""
+        return self.view(self.qbuf[self.current][member * 9 * self.fs:], 9)
 
     def set_state(self, Q, reset_register=True):
         self.state().copy_(torch.as_tensor(Q).to(device=self.device, dtype=self.dtype))
@@ -143,9 +147,19 @@ class ElasticSolver:
         kind = 0 if stf == "ricker" else 1
         L.sbp_set_source(self.h, ref, moment, kind, f0, 1.2 / f0 if t0 is None else t0, T, self.jmet, _stream())
 
+    def set_sources(self, sources, f0=2.0, t0=None):
+        """One Ricker point source per batch member: dicts with ref (q, r, s) and moment (Voigt)."""
+        if self.jmet is None:
+            raise RuntimeError("set_sources needs setup(..., keep_metrics=True)")
+        t0 = 1.2 / f0 if t0 is None else t0
+        L.sbp_set_sources(self.h, [dict(ref=sc["ref"], moment=sc["moment"], stf=0, f0=f0, t0=t0) for sc in sources],
+                          self.jmet, _stream())
+
     def set_receivers(self, ijk, n_t):
+        """Traces view [member][receiver][component][step] (the member axis only when batched)."""
         n = len(ijk)
-        self.traces = torch.zeros(max(n, 1) * 3 * n_t, dtype=self.dtype, device=self.device)
+        self.traces = torch.zeros(self.batch * max(n, 1) * 3 * n_t, dtype=self.dtype, device=self.device)
         L.sbp_set_receivers(self.h, ijk, self.traces, n_t)
-        return self.traces.view(-1, 3, n_t)[:n]
+        tr = self.traces.view(self.batch, -1, 3, n_t)[:, :n]
+        return tr if self.batch > 1 else tr[0]
 

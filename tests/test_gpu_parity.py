@@ -295,3 +295,30 @@ def test_full_size_topography_stage_sampled():
         scale = np.abs(want).max(axis=0)
         err = (np.abs(got - want) / scale).max(axis=0)
         assert np.all(err < 5e-5), (err, samples[int(np.argmax(np.abs(got - want).max(axis=1)))])
+
+
+def test_batched_solver_matches_single_runs():
+    """Batched solver: B states with their own sources, one launch per kernel; every member
+    equals its own unbatched run bit for bit (FP32 and FP64)."""
+    from paper_2011_02600_gb300 import ElasticSolver
+    nodes, order = (41, 37, 30), 4
+    X, mat, J, a, sch = _problem(nodes, order, ext=(3000.0, 2800.0, 2200.0))
+    bc = [("char", 0.0)] * 5 + [("free",)]
+    dt = stable_dt(*X, *mat, 0.5)
+    srcs = [dict(ref=(0.4, 0.5, 0.6), moment=list(moment_tensor(0.1, 1.0, 0.2, 1e12))),
+            dict(ref=(0.55, 0.35, 0.7), moment=list(moment_tensor(1.1, 0.7, -0.5, 3e12))),
+            dict(ref=(0.62, 0.61, 0.45), moment=list(moment_tensor(2.3, 1.3, 1.5, 2e12)))]
+    rec = [(10, 10, nodes[2] - 1), (30, 20, nodes[2] - 1)]
+    for prec in (32, 64):
+        sb = ElasticSolver(nodes, order, prec, bc, batch=3)
+        sb.setup(torch.from_numpy(np.stack(X)), torch.from_numpy(np.stack(mat)), keep_metrics=True)
+        sb.set_sources(srcs, f0=8.0)
+        trb = sb.set_receivers(rec, 40)
+        sb.step(40, dt)
+        for m, sc in enumerate(srcs):
+            s1 = _solver(nodes, order, prec, bc, X, mat, keep=True)
+            s1.set_sources([sc], f0=8.0)
+            tr1 = s1.set_receivers(rec, 40)
+            s1.step(40, dt)
+            assert torch.equal(sb.state(m), s1.state())
+            assert torch.equal(trb[m], tr1)
