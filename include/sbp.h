@@ -240,6 +240,53 @@ int sbp_energy_noalloc(const void* q, const void* mat, int32_t nq, int32_t nr, i
                        int64_t fs, int32_t order, int32_t precision, int32_t nblocks, double* out,
                        void* stream);
 
+/* ---- Learned surrogate (source parameters -> receiver traces) --------------
+ * Kernels of a small network trained on the batched solver's seismograms.  All
+ * pointers are device pointers owned by the caller; matrices are row-major;
+ * "BF16" buffers hold __nv_bfloat16 values.  ARG on invalid sizes or null
+ * pointers, CUDA on launch failures. */
+
+/* C[M x N] = beta C + op(A) op(B) (+ bias[m]) (ReLU): op(A) = A (M x K, lda) or
+ * A^T (A stored K x M) when transA; op(B) = B (K x N, ldb) or B^T (B stored
+ * N x K) when transB.  A, B BF16; accumulation FP32 on tensor cores; C FP32
+ * (c_bf16 = 0, beta 0 or 1) or BF16 (c_bf16 = 1, beta must be 0); bias FP32
+ * per row or NULL. */
+int sbp_nn_gemm(int32_t M, int32_t N, int32_t K, const void* A, int64_t lda, int32_t transA, const void* B,
+                int64_t ldb, int32_t transB, void* C, int64_t ldc, int32_t c_bf16, const float* bias, int32_t relu,
+                float beta, void* stream);
+/* 1D convolution lowering, activations laid out [channel][batch * T]:
+ * im2col: Xc[(c kw + k)][b T + t] = X[c][b T + t + k - pad] (zero outside the
+ * sample); col2im sums the kw shifted copies back (FP32 in and out). */
+int sbp_nn_im2col(const void* X, void* Xc, int32_t C, int32_t B, int32_t T, int32_t kw, int32_t pad, void* stream);
+int sbp_nn_col2im(const float* dXc, void* dX, int32_t C, int32_t B, int32_t T, int32_t kw, int32_t pad,
+                  void* stream);
+/* Nearest x2 upsampling along time of `rows` rows of length T, BF16 (backward:
+ * sum of pairs, FP32 in and out, X = gradient of the upsampled rows). */
+int sbp_nn_upsample2(const void* X, void* Y, int64_t rows, int32_t T, int32_t backward, void* stream);
+/* dZ = dA * (A > 0) (dA FP32, A and dZ BF16). */
+int sbp_nn_relu_backward(const float* dA, const void* A, void* dZ, int64_t n, void* stream);
+/* db[m] = sum_n dZ[m][n] (dZ BF16 M x N, db FP32). */
+int sbp_nn_bias_grad(const void* dZ, float* db, int32_t M, int64_t N, void* stream);
+/* Squared error: partial[b] = per-block FP64 sums of (Y - T)^2 over n values
+ * (nblocks blocks); dY = 2 (Y - T)/n in BF16 (dY may be NULL). */
+int sbp_nn_mse(const float* Y, const float* Tg, void* dY, int64_t n, double* partial, int32_t nblocks,
+               void* stream);
+/* Adam (bias-corrected, step >= 1) on FP32 weights w with gradient g and moments
+ * m, v; also writes the BF16 copy w_bf16 (may be NULL). */
+int sbp_nn_adam(float* w, const float* g, float* m, float* v, void* w_bf16, int64_t n, float lr, float b1, float b2,
+                float eps, int32_t step, void* stream);
+/* Reshape between the last MLP layer's output H [(c T0 + t)][b] and the
+ * convolution layout X [c][b T0 + t] (backward: X -> H). */
+int sbp_nn_mlp_to_conv(void* H, void* X, int32_t C, int32_t T0, int32_t B, int32_t backward, void* stream);
+/* Traces are linear in the moment tensor: y[o][b T + t] = sum_{c<6} m[c][b]
+ * G[(c n_out + o)][b T + t] with G the network's six Green's-function trace sets
+ * (FP32) and m the Voigt moment components per sample (FP32 [6][B]); backward
+ * (backward = 1): dG[(c n_out + o)][b T + t] = m[c][b] dy[o][b T + t] (dy, dG BF16). */
+int sbp_nn_moment_combine(const float* G, const float* m, float* y, const void* dy, void* dG, int32_t n_out,
+                          int32_t B, int32_t T, int32_t backward, void* stream);
+/* y = BF16(x). */
+int sbp_nn_cast_bf16(const float* x, void* y, int64_t n, void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* sbp_last_error(void);
 

@@ -18,7 +18,9 @@ EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sb
             "sbp_kernel_timing", "sbp_kernel_times",
             "sbp_set_time", "sbp_get_time", "sbp_energy", "sbp_set_source", "sbp_set_receivers", "sbp_status",
             "sbp_rk_coefficients", "sbp_energy_noalloc", "sbp_rhs_adjoint", "sbp_adjoint_stage",
-            "sbp_misfit", "sbp_set_batch", "sbp_set_sources", "sbp_last_error")
+            "sbp_misfit", "sbp_set_batch", "sbp_set_sources", "sbp_nn_gemm", "sbp_nn_im2col", "sbp_nn_col2im",
+            "sbp_nn_upsample2", "sbp_nn_relu_backward", "sbp_nn_bias_grad", "sbp_nn_mse", "sbp_nn_adam",
+            "sbp_nn_mlp_to_conv", "sbp_nn_cast_bf16", "sbp_nn_moment_combine", "sbp_last_error")
 
 
 class SbpError(RuntimeError):
@@ -80,6 +82,17 @@ def lib(path=None):
         "sbp_adjoint_stage": [P, i32, dbl, P, P, P, P, P, P, P],
         "sbp_misfit": [P, P, P, dbl, P, P, P],
         "sbp_set_batch": [P, i32],
+        "sbp_nn_gemm": [i32, i32, i32, P, i64, i32, P, i64, i32, P, i64, i32, P, i32, ctypes.c_float, P],
+        "sbp_nn_im2col": [P, P, i32, i32, i32, i32, i32, P],
+        "sbp_nn_col2im": [P, P, i32, i32, i32, i32, i32, P],
+        "sbp_nn_upsample2": [P, P, i64, i32, i32, P],
+        "sbp_nn_relu_backward": [P, P, P, i64, P],
+        "sbp_nn_bias_grad": [P, P, i32, i64, P],
+        "sbp_nn_mse": [P, P, P, i64, P, i32, P],
+        "sbp_nn_adam": [P, P, P, P, P, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i32, P],
+        "sbp_nn_mlp_to_conv": [P, P, i32, i32, i32, i32, P],
+        "sbp_nn_cast_bf16": [P, P, i64, P],
+        "sbp_nn_moment_combine": [P, P, P, P, P, i32, i32, i32, i32, P],
         "sbp_set_sources": [P, i32, ctypes.POINTER(SbpSource), P, P],
     }
     for name, args in sig.items():
@@ -260,3 +273,48 @@ def sbp_set_sources(h, sources, jmet, stream):
             arr[m].moment[c] = src["moment"][c]
         arr[m].stf, arr[m].f0, arr[m].t0, arr[m].T = src["stf"], src["f0"], src["t0"], src.get("T", 0.1)
     _check(lib().sbp_set_sources(h, len(sources), arr, _ptr(jmet), stream))
+
+
+def sbp_nn_gemm(M, N, K, A, lda, transA, B, ldb, transB, C, ldc, c_bf16, bias, relu, beta, stream):
+    _check(lib().sbp_nn_gemm(M, N, K, _ptr(A), lda, transA, _ptr(B), ldb, transB, _ptr(C), ldc, c_bf16, _ptr(bias),
+                             relu, beta, stream))
+
+
+def sbp_nn_im2col(X, Xc, C, B, T, kw, pad, stream):
+    _check(lib().sbp_nn_im2col(_ptr(X), _ptr(Xc), C, B, T, kw, pad, stream))
+
+
+def sbp_nn_col2im(dXc, dX, C, B, T, kw, pad, stream):
+    _check(lib().sbp_nn_col2im(_ptr(dXc), _ptr(dX), C, B, T, kw, pad, stream))
+
+
+def sbp_nn_upsample2(X, Y, rows, T, backward, stream):
+    _check(lib().sbp_nn_upsample2(_ptr(X), _ptr(Y), rows, T, backward, stream))
+
+
+def sbp_nn_relu_backward(dA, A, dZ, n, stream):
+    _check(lib().sbp_nn_relu_backward(_ptr(dA), _ptr(A), _ptr(dZ), n, stream))
+
+
+def sbp_nn_bias_grad(dZ, db, M, N, stream):
+    _check(lib().sbp_nn_bias_grad(_ptr(dZ), _ptr(db), M, N, stream))
+
+
+def sbp_nn_mse(Y, Tg, dY, n, partial, nblocks, stream):
+    _check(lib().sbp_nn_mse(_ptr(Y), _ptr(Tg), _ptr(dY), n, _ptr(partial), nblocks, stream))
+
+
+def sbp_nn_adam(w, g, m, v, w_bf16, n, lr, b1, b2, eps, step, stream):
+    _check(lib().sbp_nn_adam(_ptr(w), _ptr(g), _ptr(m), _ptr(v), _ptr(w_bf16), n, lr, b1, b2, eps, step, stream))
+
+
+def sbp_nn_mlp_to_conv(H, X, C, T0, B, backward, stream):
+    _check(lib().sbp_nn_mlp_to_conv(_ptr(H), _ptr(X), C, T0, B, backward, stream))
+
+
+def sbp_nn_cast_bf16(x, y, n, stream):
+    _check(lib().sbp_nn_cast_bf16(_ptr(x), _ptr(y), n, stream))
+
+
+def sbp_nn_moment_combine(G, m, y, dy, dG, n_out, B, T, backward, stream):
+    _check(lib().sbp_nn_moment_combine(_ptr(G), _ptr(m), _ptr(y), _ptr(dy), _ptr(dG), n_out, B, T, backward, stream))

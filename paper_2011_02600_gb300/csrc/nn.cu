@@ -1,0 +1,426 @@
+// Kernels of the learned surrogate: a BF16 tensor-core GEMM with FP32
+// accumulation and the small layer kernels around it (1D convolution as
+// im2col + GEMM, nearest upsampling, ReLU, bias gradients, MSE loss, Adam).
+//
+// Matrices are row-major.  The GEMM computes
+//     C[M x N] = beta * C + op(A)[M x K] op(B)[K x N] (+ bias[m]) (ReLU)
+// with op(A) = A (stored M x K) or A^T (stored K x M), op(B) = B (stored K x N) or
+// B^T (stored N x K).  A 128 x 128 block tile, 32-deep K steps, 8 warps of 64 x 32;
+// tiles are staged in shared memory as A[m][k] and B^T[n][k] and fed to
+// mma.sync.m16n8k16 (BF16 in, FP32 accumulate) through ldmatrix.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "sbp.h"
+
+namespace sbp_nn {
+
+constexpr int BM = 128, BN = 128, BK = 32, PAD = 8;
+constexpr int LDS = BK + PAD;  // shared row stride (bf16 elements)
+
+__device__ __forceinline__ unsigned s_addr(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(s_addr(p)));
+}
+
+__device__ __forceinline__ void mma_bf16(float c[4], const unsigned a[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(256) gemm_bf16_kernel(int M, int N, int K, const __nv_bfloat16* __restrict__ A,
+                                                        long long lda, int ta, const __nv_bfloat16* __restrict__ B,
+                                                        long long ldb, int tb, void* C, long long ldc, int c_bf16,
+                                                        const float* __restrict__ bias, int relu, float beta) {
+  __shared__ __align__(16) __nv_bfloat16 As[BM][LDS];
+  __shared__ __align__(16) __nv_bfloat16 Bs[BN][LDS];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = (warp >> 2) * 64;  // 2 x 4 warps: 64 (m) x 32 (n) each
+  const int wn = (warp & 3) * 32;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  float acc[4][4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  const __nv_bfloat16 zero = __float2bfloat16(0.f);
+
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    // stage op(A)[m0.., k0..] as As[m][k] and op(B)[k0.., n0..] as Bs[n][k]
+    for (int e = tid; e < BM * BK; e += 256) {
+      int m, k;
+      if (ta) {  // stored K x M: walk m fastest (coalesced)
+        m = e % BM;
+        k = e / BM;
+      } else {
+        k = e % BK;
+        m = e / BK;
+      }
+      const int gm = m0 + m, gk = k0 + k;
+      __nv_bfloat16 v = zero;
+      if (gm < M && gk < K) v = ta ? A[(long long)gk * lda + gm] : A[(long long)gm * lda + gk];
+      As[m][k] = v;
+    }
+    for (int e = tid; e < BN * BK; e += 256) {
+      int n, k;
+      if (tb) {  // stored N x K: walk k fastest
+        k = e % BK;
+        n = e / BK;
+      } else {
+        n = e % BN;
+        k = e / BN;
+      }
+      const int gn = n0 + n, gk = k0 + k;
+      __nv_bfloat16 v = zero;
+      if (gn < N && gk < K) v = tb ? B[(long long)gn * ldb + gk] : B[(long long)gk * ldb + gn];
+      Bs[n][k] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; kk += 16) {
+      unsigned af[4][4];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi) {
+        const int r = wm + mi * 16 + (lane & 15);
+        const int c = kk + (lane >> 4) * 8;
+        ldsm_x4(af[mi][0], af[mi][1], af[mi][2], af[mi][3], &As[r][c]);
+      }
+      unsigned bf[4][2];
+#pragma unroll
+      for (int nj = 0; nj < 4; nj += 2) {
+        // two n8 tiles at once: lanes 0-7 rows n..n+7 k, 8-15 k+8, 16-23 rows n+8.. k, 24-31 k+8
+        const int r = wn + nj * 8 + (lane & 7) + ((lane >> 4) << 3);
+        const int c = kk + ((lane >> 3) & 1) * 8;
+        unsigned r0, r1, r2, r3;
+        ldsm_x4(r0, r1, r2, r3, &Bs[r][c]);
+        bf[nj][0] = r0;
+        bf[nj][1] = r1;
+        bf[nj + 1][0] = r2;
+        bf[nj + 1][1] = r3;
+      }
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int nj = 0; nj < 4; ++nj) mma_bf16(acc[mi][nj], af[mi], bf[nj][0], bf[nj][1]);
+    }
+    __syncthreads();
+  }
+  // epilogue
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int nj = 0; nj < 4; ++nj)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int gm = m0 + wm + mi * 16 + (lane >> 2) + h * 8;
+        if (gm >= M) continue;
+        const float bv = bias ? bias[gm] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int gn = n0 + wn + nj * 8 + (lane & 3) * 2 + q;
+          if (gn >= N) continue;
+          float v = acc[mi][nj][h * 2 + q] + bv;
+          const long long idx = (long long)gm * ldc + gn;
+          if (c_bf16) {
+            if (relu) v = fmaxf(v, 0.f);
+            ((__nv_bfloat16*)C)[idx] = __float2bfloat16(v);
+          } else {
+            if (beta != 0.f) v += beta * ((float*)C)[idx];
+            if (relu) v = fmaxf(v, 0.f);
+            ((float*)C)[idx] = v;
+          }
+        }
+      }
+}
+
+// im2col of a 1D convolution (kernel width kw, zero padding pad): X [C][B*T] ->
+// Xc [(c*kw + k)][b*T + t] = X[c][b*T + t + k - pad] (zero outside 0..T-1).
+__global__ void im2col_kernel(const __nv_bfloat16* __restrict__ X, __nv_bfloat16* __restrict__ Xc, int C, int B,
+                              int T, int kw, int pad) {
+  const long long n = (long long)C * kw * B * T;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long col = e % ((long long)B * T);
+    const long long row = e / ((long long)B * T);
+    const int c = (int)(row / kw), k = (int)(row % kw);
+    const int b = (int)(col / T), t = (int)(col % T);
+    const int ts = t + k - pad;
+    Xc[e] = (ts >= 0 && ts < T) ? X[(long long)c * B * T + (long long)b * T + ts] : __float2bfloat16(0.f);
+  }
+}
+
+// col2im: dX[c][b*T + t] = sum_k dXc[(c*kw + k)][b*T + t - k + pad]  (FP32)
+__global__ void col2im_kernel(const float* __restrict__ dXc, float* __restrict__ dX, int C, int B, int T,
+                              int kw, int pad) {
+  const long long n = (long long)C * B * T;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e / ((long long)B * T));
+    const long long col = e % ((long long)B * T);
+    const int b = (int)(col / T), t = (int)(col % T);
+    float s = 0.f;
+    for (int k = 0; k < kw; ++k) {
+      const int tt = t - k + pad;
+      if (tt >= 0 && tt < T) s += dXc[((long long)c * kw + k) * B * T + (long long)b * T + tt];
+    }
+    dX[e] = s;
+  }
+}
+
+// nearest upsampling x2 along time: [C][B*T] -> [C][B*2T]; backward sums pairs.
+__global__ void upsample2_kernel(const __nv_bfloat16* __restrict__ X, __nv_bfloat16* __restrict__ Y, long long rows,
+                                 int T) {
+  const long long n = rows * 2 * T;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / (2 * T);
+    const int t2 = (int)(e % (2 * T));
+    Y[e] = X[r * T + t2 / 2];
+  }
+}
+
+__global__ void upsample2_bwd_kernel(const float* __restrict__ dY, float* __restrict__ dX, long long rows, int T) {
+  const long long n = rows * T;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / T;
+    const int t = (int)(e % T);
+    dX[e] = dY[r * 2 * T + 2 * t] + dY[r * 2 * T + 2 * t + 1];
+  }
+}
+
+// dZ = dA * (A > 0) for A = ReLU(Z): FP32 gradient in, BF16 out
+__global__ void relu_bwd_kernel(const float* __restrict__ dA, const __nv_bfloat16* __restrict__ A,
+                                __nv_bfloat16* __restrict__ dZ, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    dZ[e] = __float2bfloat16(__bfloat162float(A[e]) > 0.f ? dA[e] : 0.f);
+}
+
+// db[m] = sum_n dZ[m][n]  (one block per row, fixed order)
+__global__ void bias_grad_kernel(const __nv_bfloat16* __restrict__ dZ, float* __restrict__ db, int M, long long N) {
+  __shared__ float red[256];
+  const int m = blockIdx.x;
+  float s = 0.f;
+  for (long long n = threadIdx.x; n < N; n += blockDim.x) s += __bfloat162float(dZ[(long long)m * N + n]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) db[m] = red[0];
+}
+
+// mean squared error over n values: per-block FP64 partial sums of (y - t)^2 and dY = 2 (y - t) / n (BF16)
+__global__ void mse_kernel(const float* __restrict__ Y, const float* __restrict__ Tg, __nv_bfloat16* __restrict__ dY,
+                           long long n, double* __restrict__ partial) {
+  __shared__ double red[256];
+  double s = 0.0;
+  const float sc = 2.f / (float)n;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float d = Y[e] - Tg[e];
+    s += (double)d * d;
+    if (dY) dY[e] = __float2bfloat16(sc * d);
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+// Adam on FP32 master weights; writes the BF16 copy used by the GEMMs.
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, __nv_bfloat16* __restrict__ wb, long long n, float lr, float b1,
+                            float b2, float eps, float c1, float c2) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[e];
+    const float mi = b1 * m[e] + (1.f - b1) * gi;
+    const float vi = b2 * v[e] + (1.f - b2) * gi * gi;
+    m[e] = mi;
+    v[e] = vi;
+    const float wi = w[e] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[e] = wi;
+    if (wb) wb[e] = __float2bfloat16(wi);
+  }
+}
+
+// [F = C*T0][B] (feature-major MLP output) <-> [C][B*T0] (convolution layout), BF16
+__global__ void mlp_to_conv_kernel(const __nv_bfloat16* __restrict__ H, __nv_bfloat16* __restrict__ X, int C, int T0,
+                                   int B, int backward) {
+  const long long n = (long long)C * T0 * B;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e / ((long long)B * T0));
+    const long long col = e % ((long long)B * T0);
+    const int b = (int)(col / T0), t = (int)(col % T0);
+    const long long h = ((long long)c * T0 + t) * B + b;
+    if (backward)
+      ((__nv_bfloat16*)H)[h] = X[e];
+    else
+      X[e] = H[h];
+  }
+}
+
+// Moment combination: y[o][b*T + t] = sum_c m[c][b] G[(c*n_out + o)][b*T + t] (G FP32);
+// backward: dG[(c*n_out + o)][b*T + t] = m[c][b] dy[o][b*T + t] (BF16).
+__global__ void moment_combine_kernel(const float* __restrict__ G, const float* __restrict__ m, float* __restrict__ y,
+                                      int n_out, int B, int T) {
+  const long long n = (long long)n_out * B * T;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const int o = (int)(e / ((long long)B * T));
+    const long long col = e % ((long long)B * T);
+    const int b = (int)(col / T);
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s += m[c * B + b] * G[((long long)c * n_out + o) * B * T + col];
+    y[e] = s;
+  }
+}
+
+__global__ void moment_combine_bwd_kernel(const __nv_bfloat16* __restrict__ dy, const float* __restrict__ m,
+                                          __nv_bfloat16* __restrict__ dG, int n_out, int B, int T) {
+  const long long n = 6LL * n_out * B * T;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long row = e / ((long long)B * T);
+    const long long col = e % ((long long)B * T);
+    const int c = (int)(row / n_out), o = (int)(row % n_out);
+    const int b = (int)(col / T);
+    dG[e] = __float2bfloat16(m[c * B + b] * __bfloat162float(dy[(long long)o * B * T + col]));
+  }
+}
+
+__global__ void cast_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    y[e] = __float2bfloat16(x[e]);
+}
+
+inline unsigned grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (unsigned)(b > 152 * 16 ? 152 * 16 : (b < 1 ? 1 : b));
+}
+
+}  // namespace sbp_nn
+
+namespace sbp {
+void set_last_error(const char* msg);
+}
+
+namespace {
+int nn_status(cudaError_t e) {
+  if (e == cudaSuccess) return SBP_OK;
+  sbp::set_last_error(cudaGetErrorString(e));
+  return SBP_ERR_CUDA;
+}
+int nn_bad(const char* msg) {
+  sbp::set_last_error(msg);
+  return SBP_ERR_ARG;
+}
+}  // namespace
+
+using namespace sbp_nn;
+
+extern "C" {
+
+int sbp_nn_gemm(int32_t M, int32_t N, int32_t K, const void* A, int64_t lda, int32_t transA, const void* B,
+                int64_t ldb, int32_t transB, void* C, int64_t ldc, int32_t c_bf16, const float* bias, int32_t relu,
+                float beta, void* stream) {
+  if (M <= 0 || N <= 0 || K <= 0) return nn_bad("GEMM sizes must be positive");
+  if (!A || !B || !C) return nn_bad("null GEMM operand");
+  if (lda < (transA ? M : K) || ldb < (transB ? K : N) || ldc < N) return nn_bad("leading dimension too small");
+  if (c_bf16 && beta != 0.f) return nn_bad("accumulation (beta) needs an FP32 output");
+  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  if (grid.y > 65535) return nn_bad("M too large");
+  gemm_bf16_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(M, N, K, (const __nv_bfloat16*)A, lda, transA,
+                                                            (const __nv_bfloat16*)B, ldb, transB, C, ldc, c_bf16, bias,
+                                                            relu, beta);
+  return nn_status(cudaGetLastError());
+}
+
+int sbp_nn_im2col(const void* X, void* Xc, int32_t C, int32_t B, int32_t T, int32_t kw, int32_t pad, void* stream) {
+  if (!X || !Xc || C <= 0 || B <= 0 || T <= 0 || kw <= 0 || pad < 0) return nn_bad("bad im2col arguments");
+  const long long n = (long long)C * kw * B * T;
+  im2col_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)X, (__nv_bfloat16*)Xc, C, B, T,
+                                                                kw, pad);
+  return nn_status(cudaGetLastError());
+}
+
+int sbp_nn_col2im(const float* dXc, void* dX, int32_t C, int32_t B, int32_t T, int32_t kw, int32_t pad,
+                  void* stream) {
+  if (!dXc || !dX || C <= 0 || B <= 0 || T <= 0 || kw <= 0 || pad < 0) return nn_bad("bad col2im arguments");
+  const long long n = (long long)C * B * T;
+  col2im_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(dXc, (float*)dX, C, B, T, kw, pad);
+  return nn_status(cudaGetLastError());
+}
+
+int sbp_nn_upsample2(const void* X, void* Y, int64_t rows, int32_t T, int32_t backward, void* stream) {
+  if (!X || !Y || rows <= 0 || T <= 0) return nn_bad("bad upsample arguments");
+  if (backward)
+    upsample2_bwd_kernel<<<grid_for(rows * T), 256, 0, (cudaStream_t)stream>>>((const float*)X, (float*)Y, rows, T);
+  else
+    upsample2_kernel<<<grid_for(rows * 2 * T), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)X,
+                                                                                (__nv_bfloat16*)Y, rows, T);
+  return nn_status(cudaGetLastError());
+}
+
+int sbp_nn_relu_backward(const float* dA, const void* A, void* dZ, int64_t n, void* stream) {
+  if (!dA || !A || !dZ || n <= 0) return nn_bad("bad relu_backward arguments");
+  relu_bwd_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(dA, (const __nv_bfloat16*)A, (__nv_bfloat16*)dZ, n);
+  return nn_status(cudaGetLastError());
+}
+
+int sbp_nn_bias_grad(const void* dZ, float* db, int32_t M, int64_t N, void* stream) {
+  if (!dZ || !db || M <= 0 || N <= 0) return nn_bad("bad bias_grad arguments");
+  bias_grad_kernel<<<M, 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)dZ, db, M, N);
+  return nn_status(cudaGetLastError());
+}
+
+int sbp_nn_mse(const float* Y, const float* Tg, void* dY, int64_t n, double* partial, int32_t nblocks,
+               void* stream) {
+  if (!Y || !Tg || !partial || n <= 0 || nblocks <= 0) return nn_bad("bad mse arguments");
+  mse_kernel<<<nblocks, 256, 0, (cudaStream_t)stream>>>(Y, Tg, (__nv_bfloat16*)dY, n, partial);
+  return nn_status(cudaGetLastError());
+}
+
+int sbp_nn_adam(float* w, const float* g, float* m, float* v, void* w_bf16, int64_t n, float lr, float b1, float b2,
+                float eps, int32_t step, void* stream) {
+  if (!w || !g || !m || !v || n <= 0 || step < 1) return nn_bad("bad adam arguments");
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  adam_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(w, g, m, v, (__nv_bfloat16*)w_bf16, n, lr, b1, b2, eps,
+                                                              c1, c2);
+  return nn_status(cudaGetLastError());
+}
+
+int sbp_nn_mlp_to_conv(void* H, void* X, int32_t C, int32_t T0, int32_t B, int32_t backward, void* stream) {
+  if (!H || !X || C <= 0 || T0 <= 0 || B <= 0) return nn_bad("bad reshape arguments");
+  mlp_to_conv_kernel<<<grid_for((long long)C * T0 * B), 256, 0, (cudaStream_t)stream>>>(
+      (const __nv_bfloat16*)H, (__nv_bfloat16*)X, C, T0, B, backward);
+  return nn_status(cudaGetLastError());
+}
+
+int sbp_nn_moment_combine(const float* G, const float* m, float* y, const void* dy, void* dG, int32_t n_out,
+                          int32_t B, int32_t T, int32_t backward, void* stream) {
+  if (!m || n_out <= 0 || B <= 0 || T <= 0) return nn_bad("bad moment_combine arguments");
+  if (backward) {
+    if (!dy || !dG) return nn_bad("moment_combine backward needs dy and dG");
+    moment_combine_bwd_kernel<<<grid_for(6LL * n_out * B * T), 256, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16*)dy, m, (__nv_bfloat16*)dG, n_out, B, T);
+  } else {
+    if (!G || !y) return nn_bad("moment_combine needs G and y");
+    moment_combine_kernel<<<grid_for((long long)n_out * B * T), 256, 0, (cudaStream_t)stream>>>(G, m, y, n_out, B, T);
+  }
+  return nn_status(cudaGetLastError());
+}
+
+int sbp_nn_cast_bf16(const float* x, void* y, int64_t n, void* stream) {
+  if (!x || !y || n <= 0) return nn_bad("bad cast arguments");
+  cast_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(x, (__nv_bfloat16*)y, n);
+  return nn_status(cudaGetLastError());
+}
+
+}  // extern "C"

@@ -67,7 +67,7 @@ CONFIGS = [
         geometry="gaussian_hill", order=4, precisions=(32,), medium="layered3",
         steps=1024, n_receivers=64, source="moment_tensor",
         extra=dict(hill_amp=1500.0, hill_sigma=4000.0, n_train=4096, n_test=256,
-                   n_samples=1024, f0=2.0)),
+                   n_samples=1024, f0=0.5, n_side=8)),
 ]
 
 
