@@ -143,17 +143,16 @@ int sbp_rk_stage(SbpGrid* grid, int32_t stage, double dt, void* stream);
  * receivers recorded after each step; advances the grid time by n dt. */
 int sbp_step_n(SbpGrid* grid, int32_t n, double dt, void* stream);
 
-/* Kernel path for the stage: 0 (default) = tiled interior kernel over
- * [b, N-1-b]^3 plus the boundary-slab kernel; 1 = the boundary-slab (general)
- * kernel over every node.  Both compute the same scheme; path 1 exists to
- * cross-check the tiled kernel. */
+/* Kernel path for the stage: 0 (default) = the tiled kernel over every node
+ * (shared-memory tiles by TMA; closure rows and face penalties included);
+ * 1 = the general one-thread-per-node kernel over every node.  Both compute
+ * the same scheme; path 1 exists to cross-check the tiled kernel. */
 int sbp_set_kernel_path(SbpGrid* grid, int32_t path);
 
 /* Per-kernel timing: when enabled, each stage-kernel launch is bracketed by
  * CUDA events recorded on the launching stream.  sbp_kernel_times waits for
  * the recorded events, returns the summed milliseconds and launch counts per
- * kernel kind (index 0: tiled interior kernel, 1: boundary-slab / general
- * kernel) since the previous call, and clears them. */
+ * kernel kind (index 0: tiled kernel, 1: general kernel) since the previous call, and clears them. */
 int sbp_kernel_timing(SbpGrid* grid, int32_t enable);
 int sbp_kernel_times(SbpGrid* grid, double* ms, int64_t* launches);
 

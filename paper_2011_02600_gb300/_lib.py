@@ -181,7 +181,7 @@ def sbp_kernel_timing(h, enable):
 
 
 def sbp_kernel_times(h):
-    """([ms_interior, ms_slab], [launches_interior, launches_slab]) since the previous call."""
+    """([ms_tiled, ms_general], [launches_tiled, launches_general]) since the previous call."""
     ms, n = (ctypes.c_double * 2)(), (ctypes.c_int64 * 2)()
     _check(lib().sbp_kernel_times(h, ms, n))
     return list(ms), list(n)

@@ -55,9 +55,6 @@ void rk_stage_times(double c[5]) {
 
 int closure_b(int order) { return order == 2 ? 2 : order == 4 ? 4 : 6; }
 int stencil_reach(int order) { return order == 2 ? 2 : order == 4 ? 3 : 4; }  // max(r, q)
-// First q index of the tiled interior box: b rounded up to a multiple of 4 (and at least 4),
-// so that the tile loads, which start 4 nodes before the tile, begin on 16-byte boundaries.
-int interior_q0(int order) { return std::max(4, (closure_b(order) + 3) / 4 * 4); }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -105,11 +102,12 @@ struct SbpGrid {
   int rec_n = 0;
   void* traces = nullptr;
   int n_t = 0;
-  bool use_interior = true;
-  // tensor maps of the tiled interior kernel, per state buffer (q0, q1)
+  bool use_tiled = true;
+  void* sclose = nullptr;  // tiled kernel scratch (s-closure sums), owned by the library
+  // tensor maps of the tiled stage kernel, per state buffer (q0, q1)
   bool tma_ok[2] = {false, false};
   sbp::TmaSet tma[2];
-  // optional per-kernel CUDA-event timing of the stage kernels (kind 0 = interior, 1 = slabs/general)
+  // optional per-kernel CUDA-event timing of the stage kernels (kind 0 = tiled, 1 = general)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
@@ -117,36 +115,16 @@ struct SbpGrid {
 
 namespace {
 
-sbp::BoxList slab_boxes(const SbpGrid* g, bool with_interior_box, sbp::Box* interior) {
-  const int b = closure_b(g->desc.order);
-  const int nq = g->desc.nq, nr = g->desc.nr, ns = g->desc.ns;
+// Elements of the tiled kernel's s-closure scratch per state: 2 ends x b rows x 6 planes.
+long long sclose_elems(const SbpGrid* g) { return 2LL * closure_b(g->desc.order) * 6 * g->dims.plane; }
+
+// The whole grid as one box (the general kernel's work list).
+sbp::BoxList whole_grid(const SbpGrid* g) {
   sbp::BoxList L;
-  L.n = 0;
-  auto add = [&](int i0, int i1, int j0, int j1, int k0, int k1) {
-    if (i1 <= i0 || j1 <= j0 || k1 <= k0) return;
-    L.b[L.n] = sbp::Box{i0, i1, j0, j1, k0, k1};
-    ++L.n;
-  };
-  const int iq0 = interior_q0(g->desc.order);
-  const sbp::Box in{iq0, nq - b, b, nr - b, b, ns - b};
-  const bool has_in = in.i1 > in.i0 && in.j1 > in.j0 && in.k1 > in.k0;
-  if (!has_in || with_interior_box) {
-    add(0, nq, 0, nr, 0, ns);
-    if (interior) *interior = sbp::Box{0, 0, 0, 0, 0, 0};
-  } else {
-    add(0, nq, 0, nr, 0, b);             // s = 0 slab
-    add(0, nq, 0, nr, ns - b, ns);       // s = 1 slab
-    add(0, nq, 0, b, b, ns - b);         // r = 0 slab
-    add(0, nq, nr - b, nr, b, ns - b);   // r = 1 slab
-    add(0, iq0, b, nr - b, b, ns - b);   // q = 0 slab (b rounded up to the tile alignment)
-    add(nq - b, nq, b, nr - b, b, ns - b);  // q = 1 slab
-    if (interior) *interior = in;
-  }
+  L.n = 1;
+  L.b[0] = sbp::Box{0, g->desc.nq, 0, g->desc.nr, 0, g->desc.ns};
   L.off[0] = 0;
-  for (int m = 0; m < L.n; ++m) {
-    const sbp::Box& x = L.b[m];
-    L.off[m + 1] = L.off[m] + (long long)(x.i1 - x.i0) * (x.j1 - x.j0) * (x.k1 - x.k0);
-  }
+  L.off[1] = (long long)g->desc.nq * g->desc.nr * g->desc.ns;
   return L;
 }
 
@@ -167,6 +145,8 @@ sbp::StageArgs<T> make_args(const SbpGrid* g, const void* q, void* qout, int mod
   A.dt = (T)dt;
   A.mode = mode;
   A.status = g->status;
+  A.sclose = (T*)g->sclose;
+  A.sc_bstride = sclose_elems(g);
   const int N[3] = {g->desc.nq, g->desc.nr, g->desc.ns};
   const int b = closure_b(g->desc.order);
   (void)b;
@@ -215,7 +195,7 @@ struct TimedLaunch {
   }
 };
 
-// Tensor maps for the interior kernel's tile loads (see kernels_interior.cu): the state
+// Tensor maps for the tiled kernel's tile loads (see kernels_interior.cu): the state
 // (box 40 x 16 x 1 x 9), the metric vectors a_q (40 x 8 x 1 x 3), a_r (32 x 16 x 1 x 3),
 // a_s (32 x 8 x 1 x 3) and the coefficients (32 x 8 x 1 x 3).  Out-of-range elements
 // are filled with zeros.
@@ -247,46 +227,29 @@ template <typename T>
 int run_stage_kernels(SbpGrid* g, const void* q, void* qout, int mode, double a, double bcoef, double dt,
                       cudaStream_t st, int nb = 1) {
   sbp::StageArgs<T> A = make_args<T>(g, q, qout, mode, a, bcoef, dt, nb);
-  sbp::Box in;
-  bool interior_done = false;
-  if (g->use_interior) {
-    sbp::BoxList L = slab_boxes(g, false, &in);
-    if (in.i1 > in.i0) {
-      sbp::TmaSet local;
-      const sbp::TmaSet* tm = &local;
-      const int which = nb == g->nb ? (q == g->q[0] ? 0 : q == g->q[1] ? 1 : -1) : -1;
-      if (which >= 0) {
-        if (!g->tma_ok[which]) {
-          if (int rc = encode_maps(g, q, nb, &g->tma[which])) return rc;
-          g->tma_ok[which] = true;
-        }
-        tm = &g->tma[which];
-      } else if (int rc = encode_maps(g, q, nb, &local)) {
-        return rc;
+  if (g->use_tiled) {
+    sbp::TmaSet local;
+    const sbp::TmaSet* tm = &local;
+    const int which = nb == g->nb ? (q == g->q[0] ? 0 : q == g->q[1] ? 1 : -1) : -1;
+    if (which >= 0) {
+      if (!g->tma_ok[which]) {
+        if (int rc = encode_maps(g, q, nb, &g->tma[which])) return rc;
+        g->tma_ok[which] = true;
       }
-      TimedLaunch ti(g, 0, st);
-      cudaError_t e = sbp::launch_stage_interior<T>(A, g->desc.order, in, *tm, st);
-      if (e == cudaSuccess) {
-        ti.done();
-        interior_done = true;
-        TimedLaunch ts(g, 1, st);
-        e = sbp::launch_stage_general<T>(A, g->desc.order, L, st);
-        if (e != cudaSuccess) return cuda_fail(e, "stage (boundary slabs)");
-        ts.done();
-      } else if (e != cudaErrorNotSupported) {
-        return cuda_fail(e, "stage (interior)");
-      } else {
-        cudaGetLastError();
-      }
+      tm = &g->tma[which];
+    } else if (int rc = encode_maps(g, q, nb, &local)) {
+      return rc;
     }
+    TimedLaunch ti(g, 0, st);
+    cudaError_t e = sbp::launch_stage_tiled<T>(A, g->desc.order, *tm, st);
+    if (e != cudaSuccess) return cuda_fail(e, "stage (tiled)");
+    ti.done();
+    return SBP_OK;
   }
-  if (!interior_done) {
-    sbp::BoxList L = slab_boxes(g, true, nullptr);
-    TimedLaunch ts(g, 1, st);
-    cudaError_t e = sbp::launch_stage_general<T>(A, g->desc.order, L, st);
-    if (e != cudaSuccess) return cuda_fail(e, "stage (general)");
-    ts.done();
-  }
+  TimedLaunch ts(g, 1, st);
+  cudaError_t e = sbp::launch_stage_general<T>(A, g->desc.order, whole_grid(g), st);
+  if (e != cudaSuccess) return cuda_fail(e, "stage (general)");
+  ts.done();
   return SBP_OK;
 }
 
@@ -436,7 +399,7 @@ int sbp_create_grid(const SbpGridDesc* desc, SbpGrid** out) {
   g->elem = elem;
   g->dims = sbp::Dims{desc->nq, desc->nr, desc->ns, (int)ldq, (int)plane, fs};
   rk_stage_times(g->rkc);
-  g->use_interior = true;
+  g->use_tiled = true;
   *out = g;
   return SBP_OK;
 }
@@ -454,6 +417,7 @@ int sbp_destroy(SbpGrid* g) {
   cudaFree(g->src_off);
   cudaFree(g->src_w);
   cudaFree(g->rec_off);
+  cudaFree(g->sclose);
   delete g;
   return SBP_OK;
 }
@@ -488,6 +452,10 @@ int sbp_bind(SbpGrid* g, void* q0, void* q1, void* dq, void* met, void* mat) {
     if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(g->status, 0, sizeof(unsigned));
     if (e != cudaSuccess) return cuda_fail(e, "internal buffers");
+  }
+  if (!g->sclose) {
+    cudaError_t e = cudaMalloc(&g->sclose, (size_t)sclose_elems(g) * g->nb * g->elem);
+    if (e != cudaSuccess) return cuda_fail(e, "tiled kernel scratch");
   }
   g->bound = true;
   return SBP_OK;
@@ -559,7 +527,7 @@ int sbp_step_n(SbpGrid* g, int32_t n, double dt, void* stream) {
 int sbp_set_kernel_path(SbpGrid* g, int32_t path) {
   if (!g) return fail(SBP_ERR_ARG, "null grid");
   if (path != 0 && path != 1) return fail(SBP_ERR_ARG, "kernel path must be 0 or 1");
-  g->use_interior = path == 0;
+  g->use_tiled = path == 0;
   return SBP_OK;
 }
 

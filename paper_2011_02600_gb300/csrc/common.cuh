@@ -46,6 +46,8 @@ struct StageArgs {
   unsigned* status; // device status word (bit 8: a tile copy timed out)
   int nb;           // independent states processed together (shared metrics and coefficients)
   long long bstride;  // elements between consecutive states (9 fields)
+  T* sclose;          // tiled kernel scratch: s-closure sums, 2 b 6 planes per state
+  long long sc_bstride;  // elements between consecutive states' scratch
 };
 
 // Closure rows of D+ and D- (unit spacing), one private copy per translation unit.
@@ -221,6 +223,61 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs<T>& A, long long 
   }
 }
 
+// Contribution of axis xi to the raw operator at one node (in-field offset n0, position
+// pos along the axis of N nodes, neighbour stride `stride`), read from global memory with
+// every row of D+ and D- (interior stencil or closure):
+//   rv += inv_h D-_xi (sigma a^xi),   e += B_xi(a^xi at the node) inv_h D+_xi v.
+template <typename T, int O>
+__device__ __forceinline__ void axis_operator_global(const T* __restrict__ q, const T* __restrict__ met,
+                                                     long long fs, long long n0, int xi, int pos, int N,
+                                                     long long stride, T inv_h, T rv[3], T e[6]) {
+  const T* __restrict__ mx = met + (long long)(3 * xi) * fs;
+  T f[3] = {T(0), T(0), T(0)};
+  apply_row<T, O, false>(pos, N, [&](int c, T w) {
+    const long long nb = n0 + (long long)(c - pos) * stride;
+    const T a[3] = {mx[nb], mx[fs + nb], mx[2 * fs + nb]};
+    T s[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) s[m] = q[(3 + m) * fs + nb];
+    T F[3];
+    flux(a, s, F);
+    f[0] += w * F[0];
+    f[1] += w * F[1];
+    f[2] += w * F[2];
+  });
+  rv[0] += inv_h * f[0];
+  rv[1] += inv_h * f[1];
+  rv[2] += inv_h * f[2];
+  T dv[3] = {T(0), T(0), T(0)};
+  apply_row<T, O, true>(pos, N, [&](int c, T w) {
+    const long long nb = n0 + (long long)(c - pos) * stride;
+    dv[0] += w * q[nb];
+    dv[1] += w * q[fs + nb];
+    dv[2] += w * q[2 * fs + nb];
+  });
+  dv[0] *= inv_h;
+  dv[1] *= inv_h;
+  dv[2] *= inv_h;
+  const T a0[3] = {mx[n0], mx[fs + n0], mx[2 * fs + n0]};
+  add_strain(a0, dv, e);
+}
+
+// Penalties of every face the node lies on (positions pos, sizes N), in the order
+// q = 0, q = 1, r = 0, r = 1, s = 0, s = 1.  a[xi] is a^xi at the node, qc its state.
+template <typename T>
+__device__ __forceinline__ void add_face_penalties(const int pos[3], const int N[3], const T a[3][3],
+                                                   const T qc[9], T irhoJ, T lamJ, T muJ, const int bc_kind[6],
+                                                   const T bc_gamma[6], const T inv_h0[3], T rv[3], T e[6]) {
+#pragma unroll
+  for (int xi = 0; xi < 3; ++xi) {
+    if (pos[xi] == 0)
+      add_penalty<T>(0, bc_kind[2 * xi], bc_gamma[2 * xi], inv_h0[xi], qc, qc + 3, a[xi], irhoJ, lamJ, muJ, rv, e);
+    if (pos[xi] == N[xi] - 1)
+      add_penalty<T>(1, bc_kind[2 * xi + 1], bc_gamma[2 * xi + 1], inv_h0[xi], qc, qc + 3, a[xi], irhoJ, lamJ,
+                     muJ, rv, e);
+  }
+}
+
 // Raw operator (P~^-1 dQ/dt: velocity rows rv, stress rows e, penalties included) of the
 // state q at one node with in-field offset n0 and axis positions pos, using every row of
 // D+ and D- (interior stencil or closure).  qc receives the node's own 9 values.
@@ -238,51 +295,19 @@ __device__ __forceinline__ void raw_operator_at(const T* __restrict__ q, const T
 #pragma unroll
   for (int c = 0; c < 6; ++c) e[c] = T(0);
 #pragma unroll
-  for (int xi = 0; xi < 3; ++xi) {
-    const T* __restrict__ mx = met + (long long)(3 * xi) * fs;
-    T f[3] = {T(0), T(0), T(0)};
-    apply_row<T, O, false>(pos[xi], N[xi], [&](int c, T w) {
-      const long long nb = n0 + (long long)(c - pos[xi]) * stride[xi];
-      const T a[3] = {mx[nb], mx[fs + nb], mx[2 * fs + nb]};
-      T s[6];
-#pragma unroll
-      for (int m = 0; m < 6; ++m) s[m] = q[(3 + m) * fs + nb];
-      T F[3];
-      flux(a, s, F);
-      f[0] += w * F[0];
-      f[1] += w * F[1];
-      f[2] += w * F[2];
-    });
-    rv[0] += inv_h[xi] * f[0];
-    rv[1] += inv_h[xi] * f[1];
-    rv[2] += inv_h[xi] * f[2];
-    T dv[3] = {T(0), T(0), T(0)};
-    apply_row<T, O, true>(pos[xi], N[xi], [&](int c, T w) {
-      const long long nb = n0 + (long long)(c - pos[xi]) * stride[xi];
-      dv[0] += w * q[nb];
-      dv[1] += w * q[fs + nb];
-      dv[2] += w * q[2 * fs + nb];
-    });
-    dv[0] *= inv_h[xi];
-    dv[1] *= inv_h[xi];
-    dv[2] *= inv_h[xi];
-    const T a0[3] = {mx[n0], mx[fs + n0], mx[2 * fs + n0]};
-    add_strain(a0, dv, e);
-  }
+  for (int xi = 0; xi < 3; ++xi)
+    axis_operator_global<T, O>(q, met, fs, n0, xi, pos[xi], N[xi], stride[xi], inv_h[xi], rv, e);
 #pragma unroll
   for (int f = 0; f < 9; ++f) qc[f] = q[f * fs + n0];
-  const T irhoJ = mat[n0], lamJ = mat[fs + n0], muJ = mat[2 * fs + n0];
+  const bool face = pos[0] == 0 || pos[0] == N[0] - 1 || pos[1] == 0 || pos[1] == N[1] - 1 || pos[2] == 0 ||
+                    pos[2] == N[2] - 1;
+  if (face) {
+    T a[3][3];
 #pragma unroll
-  for (int xi = 0; xi < 3; ++xi) {
-    const bool lo = pos[xi] == 0, hi = pos[xi] == N[xi] - 1;
-    if (!(lo || hi)) continue;
-    const T* __restrict__ mx = met + (long long)(3 * xi) * fs;
-    const T a0[3] = {mx[n0], mx[fs + n0], mx[2 * fs + n0]};
-    if (lo)
-      add_penalty<T>(0, bc_kind[2 * xi], bc_gamma[2 * xi], inv_h0[xi], qc, qc + 3, a0, irhoJ, lamJ, muJ, rv, e);
-    if (hi)
-      add_penalty<T>(1, bc_kind[2 * xi + 1], bc_gamma[2 * xi + 1], inv_h0[xi], qc, qc + 3, a0, irhoJ, lamJ, muJ,
-                     rv, e);
+    for (int xi = 0; xi < 3; ++xi)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) a[xi][c] = met[(3 * xi + c) * fs + n0];
+    add_face_penalties(pos, N, a, qc, mat[n0], mat[fs + n0], mat[2 * fs + n0], bc_kind, bc_gamma, inv_h0, rv, e);
   }
 }
 

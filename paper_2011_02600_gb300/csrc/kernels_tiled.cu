@@ -1,0 +1,455 @@
+// Tiled stage kernel over the whole grid.
+//
+// Work layout: a block owns a TX x TY tile of the (q, r) plane and marches along
+// s through a chunk of planes.  Tiles start at multiples of TX and TY except the
+// last along each axis, which is moved back so that it ends at the grid's edge
+// (its start rounded up to a multiple of 4 along q, so that every tile load starts
+// on a 16-byte boundary); the nodes it shares with the tile before it belong to it.
+// Every closure row of D+ and D- along q and r then finds all of its taps in the
+// tile that owns the node.
+//   * Plane data arrive by TMA, one plane ahead, into a two-stage shared-memory
+//     ring: the 9 state fields with a halo of HX nodes on q and r, a_q with a q
+//     halo, a_r with an r halo, a_s and the coefficients on the tile.  One
+//     elected thread issues the copies; an mbarrier per stage counts the bytes.
+//   * Each plane, the fluxes F_q = sigma a_q and F_r = sigma a_r are formed on the
+//     tile and its halo into a double-buffered flux tile; one block barrier per
+//     plane publishes them and frees the stage the next copy will overwrite.
+//   * q and r derivatives read the flux and velocity tiles (interior stencil, or
+//     the closure row of a node within b of the face).  s derivatives use
+//     per-thread register queues of F_s = sigma a_s (planes k-q..k+r) and v
+//     (planes k-r..k+q), fed by direct loads of the lead planes.
+//   * The b closure planes at each end of s all combine the same cw planes: a block
+//     whose chunk reaches them first streams those planes once per thread and
+//     forms the closure-row sums of every closure plane together, into a scratch
+//     buffer that the same thread reads back when it gets to the plane.
+//   * Nodes on a face add the face's penalty (free surface or characteristic SAT).
+// The stage update (2N-storage Runge-Kutta) is fused in the epilogue.
+#include "common.cuh"
+#include "launch.h"
+#include "tma.cuh"
+
+namespace sbp {
+
+constexpr int TX = 32;
+constexpr int TY = 8;
+constexpr int HX = 4;              // halo in the tile loads (>= q of every order)
+constexpr int BXH = TX + 2 * HX;   // 40
+constexpr int BYH = TY + 2 * HX;   // 16
+constexpr unsigned kWaitLimit = 1u << 24;  // polls (with 64 ns sleeps) before giving up: about a second
+
+// Tile `t` of `nt` along an axis of n nodes, tile width w: origin of its loads and the
+// owned node range [own0, own1).  The last tile starts at n - w rounded up to `align`
+// (never below 0); the one before it gives up the nodes from there on.
+struct TileAxis {
+  int origin, own0, own1;
+};
+__device__ __forceinline__ TileAxis tile_axis(int t, int nt, int n, int w, int align) {
+  int last = n - w > 0 ? n - w : 0;
+  last = (last + align - 1) / align * align;
+  TileAxis a;
+  a.origin = t == nt - 1 ? last : t * w;
+  a.own0 = a.origin;
+  a.own1 = t == nt - 1 ? n : (t == nt - 2 ? last : (t + 1) * w);
+  return a;
+}
+
+// Closure-row sums of the b planes at one end of s (HI: the s = 1 end) for the node
+// column col: for closure row r (plane r, or ns-1-r at the high end) and c = 0..2,
+//   scratch[(e*b + r)*6 + c]     = sum_p D-[r][p] F_s,c(plane p)
+//   scratch[(e*b + r)*6 + 3 + c] = sum_p D+[r][p] v_c(plane p)
+// over the cw planes p nearest the face (unit spacing; rows of the high end by
+// D+[N-1-i][N-1-j] = -D-[i][j]).  Each scratch row is a plane-sized array.
+template <typename T, int O, bool HI>
+__device__ __forceinline__ void s_closure_sums(const T* __restrict__ q, const T* __restrict__ met,
+                                               const Dims& d, int col, T* __restrict__ scratch) {
+  using C = OpCoef<O>;
+  constexpr int BC = C::b;
+  const long long fs = d.fs;
+  T am[BC][3], ap[BC][3];
+#pragma unroll
+  for (int r = 0; r < BC; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) am[r][c] = ap[r][c] = T(0);
+#pragma unroll
+  for (int p = 0; p < C::cw; ++p) {
+    const long long off = (long long)(HI ? d.ns - 1 - p : p) * d.plane + col;
+    T v[3], sg[6], a[3], F[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = __ldg(q + c * fs + off);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sg[c] = __ldg(q + (3 + c) * fs + off);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a[c] = __ldg(met + (6 + c) * fs + off);
+    flux(a, sg, F);
+#pragma unroll
+    for (int r = 0; r < BC; ++r) {
+      const T wm = HI ? -Tab<T, O>::p(r, p) : Tab<T, O>::m(r, p);
+      const T wp = HI ? -Tab<T, O>::m(r, p) : Tab<T, O>::p(r, p);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        am[r][c] += wm * F[c];
+        ap[r][c] += wp * v[c];
+      }
+    }
+  }
+  T* out = scratch + (long long)(HI ? BC : 0) * 6 * d.plane + col;
+#pragma unroll
+  for (int r = 0; r < BC; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      out[(long long)(r * 6 + c) * d.plane] = am[r][c];
+      out[(long long)(r * 6 + 3 + c) * d.plane] = ap[r][c];
+    }
+}
+
+template <typename T>
+struct Stage {
+  T state[9][BYH][BXH];
+  T aq[3][TY][BXH];
+  T ar[3][BYH][TX];
+  T as[3][TY][TX];
+  T mat[3][TY][TX];
+};
+
+template <typename T>
+struct FluxTiles {
+  T fq[3][TY][BXH];
+  T fr[3][BYH][TX];
+};
+
+template <typename T>
+struct TiledShared {
+  Stage<T> st[2];
+  FluxTiles<T> f[2];
+  unsigned long long bar[2];
+};
+
+template <typename T>
+constexpr int tiled_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
+
+template <typename T>
+__device__ __forceinline__ void issue_plane(TiledShared<T>& S, int stage, const TmaSet& tm, int i0, int j0,
+                                            int k, int member) {
+  unsigned long long* bar = &S.bar[stage];
+  mbar_expect_tx(bar, (unsigned)sizeof(Stage<T>));
+  Stage<T>& st = S.st[stage];
+  tma_load_4d(&st.state[0][0][0], &tm.state, i0 - HX, j0 - HX, k, 9 * member, bar);
+  tma_load_4d(&st.aq[0][0][0], &tm.met_q, i0 - HX, j0, k, 0, bar);
+  tma_load_4d(&st.ar[0][0][0], &tm.met_r, i0, j0 - HX, k, 3, bar);
+  tma_load_4d(&st.as[0][0][0], &tm.met_s, i0, j0, k, 6, bar);
+  tma_load_4d(&st.mat[0][0][0], &tm.mat, i0, j0, k, 0, bar);
+}
+
+template <typename T, int O>
+__global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
+    stage_tiled_kernel(StageArgs<T> A, int chunk, const __grid_constant__ TmaSet tm) {
+  using C = OpCoef<O>;
+  constexpr int R = C::r;    // D+ reaches -R..+Q, D- reaches -Q..+R
+  constexpr int Q = C::q;
+  constexpr int NV = R + Q + 1;
+  constexpr int BC = C::b;   // closure rows at each end of an axis
+  constexpr int CW = C::cw;  // columns of a closure row
+  static_assert(CW <= TY + R && CW <= TX + R && BC <= TY, "closure rows must fit the first tile");
+  static_assert(Q <= HX && R <= HX, "halo too small");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  TiledShared<T>& S = *reinterpret_cast<TiledShared<T>*>(smem_raw);
+
+  const Dims d = A.d;
+  const long long fs = d.fs;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * TX + tx;
+  const TileAxis ax = tile_axis(blockIdx.x, gridDim.x, d.nq, TX, 4);
+  const TileAxis ay = tile_axis(blockIdx.y, gridDim.y, d.nr, TY, 1);
+  const int i0 = ax.origin, j0 = ay.origin;
+  const int i = i0 + tx, j = j0 + ty;
+  // blockIdx.z = chunk + nchunks * member (a batch of independent states)
+  const int nchunks = gridDim.z / A.nb;
+  const int member = blockIdx.z / nchunks;
+  const int kb = (blockIdx.z % nchunks) * chunk;
+  const int ke = min(d.ns, kb + chunk);
+  const bool active = i >= ax.own0 && i < ax.own1 && j >= ay.own0 && j < ay.own1;
+  const bool q_close = i < BC || i > d.nq - 1 - BC;
+  const bool r_close = j < BC || j > d.nr - 1 - BC;
+  const bool qr_face = i == 0 || i == d.nq - 1 || j == 0 || j == d.nr - 1;
+  const T ihq = A.inv_h[0], ihr = A.inv_h[1], ihs = A.inv_h[2];
+  const long long boff = (long long)member * A.bstride;
+  const T* __restrict__ q = A.q + boff;
+  T* __restrict__ qout = A.qout + boff;
+  T* __restrict__ dqm = A.dq + (A.mode == kModeRhs ? 0 : boff);
+  T* __restrict__ scl = A.sclose + (long long)member * A.sc_bstride;
+  const T* __restrict__ met = A.met;
+  const int col = j * d.ldq + i;
+
+  if (tid == 0) {
+    mbar_init(&S.bar[0], 1);
+    mbar_init(&S.bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (tid == 0) issue_plane(S, 0, tm, i0, j0, kb, member);
+  // closure-row sums of the s closure planes this chunk reaches (while the first copy flies)
+  if (active && kb < BC) s_closure_sums<T, O, false>(q, met, d, col, scl);
+  if (active && ke > d.ns - BC) s_closure_sums<T, O, true>(q, met, d, col, scl);
+
+  auto ld = [&](const T* p, long long off) -> T { return active ? __ldg(p + off) : T(0); };
+  // plane kk of field offset fo at this thread's column; zero outside the grid
+  auto ldk = [&](const T* p, long long fo, int kk) -> T {
+    return active && kk >= 0 && kk < d.ns ? __ldg(p + fo + (long long)kk * d.plane + col) : T(0);
+  };
+  T vq[NV][3];  // v at planes k-R .. k+Q
+  T fq[NV][3];  // F_s at planes k-Q .. k+R
+#pragma unroll
+  for (int m = 0; m < NV - 1; ++m) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vq[m][c] = ldk(q, c * fs, kb - R + m);
+  }
+#pragma unroll
+  for (int m = 0; m < NV - 1; ++m) {
+    T s[6], a[3];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s[c] = ldk(q, (3 + c) * fs, kb - Q + m);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a[c] = ldk(met, (6 + c) * fs, kb - Q + m);
+    flux(a, s, fq[m]);
+  }
+
+  // lead values (v at k+Q, sigma and a_s at k+R) staged one plane ahead
+  T lv[3], ls[6], la[3];
+  auto load_lead = [&](int k) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) lv[c] = ldk(q, c * fs, k + Q);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) ls[c] = ldk(q, (3 + c) * fs, k + R);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) la[c] = ldk(met, (6 + c) * fs, k + R);
+  };
+  load_lead(kb);
+
+  for (int it = 0, k = kb; k < ke; ++it, ++k) {
+    const int sidx = it & 1;
+    const unsigned phase = (it >> 1) & 1;
+    const long long pk = (long long)k * d.plane;
+    // push this plane's lead values (loaded during the previous plane), then fetch the next ones
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vq[NV - 1][c] = lv[c];
+    flux(la, ls, fq[NV - 1]);
+    if (k + 1 < ke) load_lead(k + 1);
+    const long long off = pk + col;
+    T dqi[9];
+    if (A.mode == kModeStage) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) dqi[c] = ld(dqm, c * fs + off);
+    }
+
+    if (!mbar_wait_bounded(&S.bar[sidx], phase, kWaitLimit)) {
+      // The copy never completed (the only one in flight is the one waited for): record
+      // it and leave; the host sees SBP_STATUS_TIMEOUT.
+      if (tid == 0) atomicOr(A.status, 8u);
+      return;
+    }
+    const Stage<T>& st = S.st[sidx];
+    FluxTiles<T>& F = S.f[sidx];
+    // fluxes on the tile and its halo: F_q at columns -Q..TX-1+R, F_r at rows -Q..TY-1+R
+    for (int t = tid; t < TY * (Q + R + TX); t += TX * TY) {
+      const int row = t / (Q + R + TX);
+      const int cc = HX - Q + t % (Q + R + TX);
+      const T a[3] = {st.aq[0][row][cc], st.aq[1][row][cc], st.aq[2][row][cc]};
+      T s[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) s[c] = st.state[3 + c][HX + row][cc];
+      T Fv[3];
+      flux(a, s, Fv);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F.fq[c][row][cc] = Fv[c];
+    }
+    for (int t = tid; t < TX * (Q + R + TY); t += TX * TY) {
+      const int cl = t % TX;
+      const int rr = HX - Q + t / TX;
+      const T a[3] = {st.ar[0][rr][cl], st.ar[1][rr][cl], st.ar[2][rr][cl]};
+      T s[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) s[c] = st.state[3 + c][rr][HX + cl];
+      T Fv[3];
+      flux(a, s, Fv);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) F.fr[c][rr][cl] = Fv[c];
+    }
+    __syncthreads();
+    if (tid == 0 && k + 1 < ke) {
+      fence_proxy_async_smem();
+      issue_plane(S, sidx ^ 1, tm, i0, j0, k + 1, member);
+    }
+
+    T rv[3] = {T(0), T(0), T(0)};
+    T e[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    T dv[3];
+    // q
+    if (!q_close) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T sf = T(0), sv = T(0);
+#pragma unroll
+        for (int jj = -Q; jj <= R; ++jj) sf += T(-C::alpha(-jj)) * F.fq[c][ty][HX + tx + jj];
+#pragma unroll
+        for (int jj = -R; jj <= Q; ++jj) sv += T(C::alpha(jj)) * st.state[c][HX + ty][HX + tx + jj];
+        rv[c] += ihq * sf;
+        dv[c] = ihq * sv;
+      }
+      const T a[3] = {st.aq[0][ty][HX + tx], st.aq[1][ty][HX + tx], st.aq[2][ty][HX + tx]};
+      add_strain(a, dv, e);
+    } else if (active) {
+      // closure row of a node within b of a q face: all its taps lie in this tile
+      const bool lo = i < BC;
+      const int row = lo ? i : d.nq - 1 - i;
+      T sf[3] = {T(0), T(0), T(0)}, sv[3] = {T(0), T(0), T(0)};
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        const int cc = HX + (lo ? c : d.nq - 1 - c) - i0;
+        const T wm = lo ? Tab<T, O>::m(row, c) : -Tab<T, O>::p(row, c);
+        const T wp = lo ? Tab<T, O>::p(row, c) : -Tab<T, O>::m(row, c);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          sf[m] += wm * F.fq[m][ty][cc];
+          sv[m] += wp * st.state[m][HX + ty][cc];
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        rv[m] += ihq * sf[m];
+        dv[m] = ihq * sv[m];
+      }
+      const T a[3] = {st.aq[0][ty][HX + tx], st.aq[1][ty][HX + tx], st.aq[2][ty][HX + tx]};
+      add_strain(a, dv, e);
+    }
+    // r
+    if (!r_close) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T sf = T(0), sv = T(0);
+#pragma unroll
+        for (int jj = -Q; jj <= R; ++jj) sf += T(-C::alpha(-jj)) * F.fr[c][HX + ty + jj][tx];
+#pragma unroll
+        for (int jj = -R; jj <= Q; ++jj) sv += T(C::alpha(jj)) * st.state[c][HX + ty + jj][HX + tx];
+        rv[c] += ihr * sf;
+        dv[c] = ihr * sv;
+      }
+      const T a[3] = {st.ar[0][HX + ty][tx], st.ar[1][HX + ty][tx], st.ar[2][HX + ty][tx]};
+      add_strain(a, dv, e);
+    } else if (active) {
+      // closure row of a node within b of an r face (whole warps: the row is uniform)
+      const bool lo = j < BC;
+      const int row = lo ? j : d.nr - 1 - j;
+      T sf[3] = {T(0), T(0), T(0)}, sv[3] = {T(0), T(0), T(0)};
+#pragma unroll
+      for (int c = 0; c < CW; ++c) {
+        const int rr = HX + (lo ? c : d.nr - 1 - c) - j0;
+        const T wm = lo ? Tab<T, O>::m(row, c) : -Tab<T, O>::p(row, c);
+        const T wp = lo ? Tab<T, O>::p(row, c) : -Tab<T, O>::m(row, c);
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          sf[m] += wm * F.fr[m][rr][tx];
+          sv[m] += wp * st.state[m][rr][HX + tx];
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        rv[m] += ihr * sf[m];
+        dv[m] = ihr * sv[m];
+      }
+      const T a[3] = {st.ar[0][HX + ty][tx], st.ar[1][HX + ty][tx], st.ar[2][HX + ty][tx]};
+      add_strain(a, dv, e);
+    }
+    // s
+    if (k >= BC && k <= d.ns - 1 - BC) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T sf = T(0), sv = T(0);
+#pragma unroll
+        for (int jj = -Q; jj <= R; ++jj) sf += T(-C::alpha(-jj)) * fq[Q + jj][c];
+#pragma unroll
+        for (int jj = -R; jj <= Q; ++jj) sv += T(C::alpha(jj)) * vq[R + jj][c];
+        rv[c] += ihs * sf;
+        dv[c] = ihs * sv;
+      }
+      const T a[3] = {st.as[0][ty][tx], st.as[1][ty][tx], st.as[2][ty][tx]};
+      add_strain(a, dv, e);
+    } else if (active) {
+      // closure plane: the sums formed before the march
+      const T* src = scl + (long long)((k < BC ? k : BC + d.ns - 1 - k) * 6) * d.plane + col;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        rv[m] += ihs * src[m * d.plane];
+        dv[m] = ihs * src[(3 + m) * d.plane];
+      }
+      const T a[3] = {st.as[0][ty][tx], st.as[1][ty][tx], st.as[2][ty][tx]};
+      add_strain(a, dv, e);
+    }
+
+    if (active) {
+      T qc[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) qc[c] = st.state[c][HX + ty][HX + tx];
+      if (qr_face || k == 0 || k == d.ns - 1) {
+        const int pos[3] = {i, j, k};
+        const int N[3] = {d.nq, d.nr, d.ns};
+        const T a[3][3] = {{st.aq[0][ty][HX + tx], st.aq[1][ty][HX + tx], st.aq[2][ty][HX + tx]},
+                           {st.ar[0][HX + ty][tx], st.ar[1][HX + ty][tx], st.ar[2][HX + ty][tx]},
+                           {st.as[0][ty][tx], st.as[1][ty][tx], st.as[2][ty][tx]}};
+        add_face_penalties(pos, N, a, qc, st.mat[0][ty][tx], st.mat[1][ty][tx], st.mat[2][ty][tx], A.bc_kind,
+                           A.bc_gamma, A.inv_h0, rv, e);
+      }
+      T dd[9];
+      apply_P(rv, e, st.mat[0][ty][tx], st.mat[1][ty][tx], st.mat[2][ty][tx], dd);
+      if (A.mode == kModeRhs) {
+#pragma unroll
+        for (int f = 0; f < 9; ++f) qout[f * fs + off] = dd[f];
+      } else {
+#pragma unroll
+        for (int f = 0; f < 9; ++f) {
+          T dn = A.dt * dd[f];
+          if (A.mode == kModeStage) dn += A.rk_a * dqi[f];
+          dqm[f * fs + off] = dn;
+          qout[f * fs + off] = qc[f] + A.rk_b * dn;
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < NV - 1; ++m)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        vq[m][c] = vq[m + 1][c];
+        fq[m][c] = fq[m + 1][c];
+      }
+  }
+}
+
+template <typename T, int O>
+cudaError_t launch_tiled_order(const StageArgs<T>& A, const TmaSet& tm, cudaStream_t st) {
+  const int ni = A.d.nq, nj = A.d.nr, nk = A.d.ns;
+  const int nchunks = (nk + 95) / 96;
+  const int chunk = (nk + nchunks - 1) / nchunks;
+  dim3 grid((ni + TX - 1) / TX, (nj + TY - 1) / TY, ((nk + chunk - 1) / chunk) * A.nb);
+  if (grid.z > 65535 || grid.y > 65535) return cudaErrorInvalidConfiguration;
+  dim3 block(TX, TY);
+  const size_t smem = sizeof(TiledShared<T>);
+  cudaError_t e = cudaFuncSetAttribute(stage_tiled_kernel<T, O>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  stage_tiled_kernel<T, O><<<grid, block, smem, st>>>(A, chunk, tm);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_stage_tiled(const StageArgs<T>& A, int order, const TmaSet& tm, cudaStream_t st) {
+  if (!A.sclose) return cudaErrorInvalidValue;
+  switch (order) {
+    case 2: return launch_tiled_order<T, 2>(A, tm, st);
+    case 4: return launch_tiled_order<T, 4>(A, tm, st);
+    case 6: return launch_tiled_order<T, 6>(A, tm, st);
+    default: return cudaErrorNotSupported;
+  }
+}
+template cudaError_t launch_stage_tiled<float>(const StageArgs<float>&, int, const TmaSet&, cudaStream_t);
+template cudaError_t launch_stage_tiled<double>(const StageArgs<double>&, int, const TmaSet&, cudaStream_t);
+
+}  // namespace sbp

@@ -40,11 +40,10 @@ cudaError_t launch_misfit(const T* q, const Dims& d, const int32_t* off, int n, 
 template <typename T>
 cudaError_t launch_stage_general(const StageArgs<T>& A, int order, const BoxList& L, cudaStream_t st);
 
-// Tiled interior kernel over `box` (q-start a multiple of 4), tile data by TMA through
-// the tensor maps in `tm` (returns cudaErrorNotSupported when the box is empty).
+// Tiled stage kernel over the whole grid, tile data by TMA through the tensor maps in
+// `tm`; A.sclose must hold 2 b 6 planes per state.
 template <typename T>
-cudaError_t launch_stage_interior(const StageArgs<T>& A, int order, const Box& box, const TmaSet& tm,
-                                  cudaStream_t st);
+cudaError_t launch_stage_tiled(const StageArgs<T>& A, int order, const TmaSet& tm, cudaStream_t st);
 
 cudaError_t launch_metrics(const double* xyz, double* jmet, const Dims& d, int order, unsigned* status,
                            cudaStream_t st);

@@ -138,11 +138,14 @@ def test_fused_stage_parity_fp64(order, stage):
     assert _relerr(s.state().cpu().numpy(), q_new) < 1e-12
 
 
-@pytest.mark.parametrize("order,nodes", [(6, (101, 45, 40)), (4, (70, 33, 30)), (2, (67, 20, 13))])
+@pytest.mark.parametrize("order,nodes", [(6, (101, 45, 40)), (4, (70, 33, 30)), (2, (67, 20, 13)),
+                                         (6, (16, 16, 16)), (4, (11, 11, 11)), (2, (6, 6, 6)),
+                                         (6, (65, 24, 17)), (4, (36, 12, 97)), (6, (37, 16, 200))])
 @pytest.mark.parametrize("prec", [32, 64])
-def test_tiled_interior_matches_general_kernel(order, nodes, prec):
-    """The tiled interior kernel (several tiles, ragged last tile, several s chunks) and the
-    general kernel compute the same right-hand side; also checked against the oracle."""
+def test_tiled_matches_general_kernel(order, nodes, prec):
+    """The tiled kernel (several tiles, ragged last tiles, closure rows split across tiles,
+    minimum sizes, several s chunks) and the general kernel compute the same right-hand
+    side over every node; also checked against the oracle."""
     X, mat, J, a, sch = _problem(nodes, order)
     s = _solver(nodes, order, prec, MIXED, X, mat)
     Q = np.stack(smooth_state(nodes, 9, *_idx(nodes))) if prec == 32 else random_state(nodes, 9)
