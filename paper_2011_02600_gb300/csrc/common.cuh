@@ -157,23 +157,26 @@ __device__ __forceinline__ void add_penalty(int side, int kind, T gamma, T inv_h
     return;
   }
   const T an = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-  const T n[3] = {a[0] / an, a[1] / an, a[2] / an};
+  const T ian = T(1) / an;
+  const T n[3] = {a[0] * ian, a[1] * ian, a[2] * ian};
   T Tr[3];
   flux(n, s, Tr);
   const T Zp = sqrt((lamJ + T(2) * muJ) / irhoJ);
   const T Zs = sqrt(muJ / irhoJ);
+  const T iZp = T(1) / Zp, iZs = T(1) / Zs;
   const T vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
   const T Tn = Tr[0] * n[0] + Tr[1] * n[1] + Tr[2] * n[2];
   const T sgT = side == 0 ? T(-1) : T(1);
   const T cv = T(0.5) * (T(1) - gamma);
   const T cT = T(0.5) * (T(1) + gamma) * sgT;
   const T Gn = cv * Zp * vn + cT * Tn;
+  const T Gnp = Gn * iZp;
   T G[3], Gt[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const T gt = cv * Zs * (v[c] - vn * n[c]) + cT * (Tr[c] - Tn * n[c]);
     G[c] = Gn * n[c] + gt;
-    Gt[c] = Gn / Zp * n[c] + gt / Zs;
+    Gt[c] = Gnp * n[c] + gt * iZs;
   }
   const T f = an * inv_h0;
   rv[0] -= f * G[0];

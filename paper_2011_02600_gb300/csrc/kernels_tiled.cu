@@ -117,10 +117,23 @@ struct FluxTiles {
   T fr[3][BYH][TX];
 };
 
+constexpr int kMaxCW = 10;  // widest closure row (order 6)
+
+// Per-thread q rows of a tile that owns closure nodes: the smem column of tap 0 for
+// D- (of the flux tile) and D+ (of the state tile) and the weights of kMaxCW taps.
+template <typename T>
+struct QRows {
+  T wm[kMaxCW][TX];
+  T wp[kMaxCW][TX];
+  int bm[TX];
+  int bp[TX];
+};
+
 template <typename T>
 struct TiledShared {
   Stage<T> st[2];
   FluxTiles<T> f[2];
+  QRows<T> qrows;
   unsigned long long bar[2];
 };
 
@@ -138,6 +151,57 @@ __device__ __forceinline__ void issue_plane(TiledShared<T>& S, int stage, const 
   tma_load_4d(&st.ar[0][0][0], &tm.met_r, i0, j0 - HX, k, 3, bar);
   tma_load_4d(&st.as[0][0][0], &tm.met_s, i0, j0, k, 6, bar);
   tma_load_4d(&st.mat[0][0][0], &tm.mat, i0, j0, k, 0, bar);
+}
+
+// Rows of D- and D+ along q for thread column tx of a tile with origin i0, as cw taps
+// starting at a shared-memory column: the closure row (the cw nodes nearest the face)
+// for a node within b of a q face, the interior stencil otherwise, zero weights for a
+// column the tile does not own ([own0, own1)).  Every tap lies in the computed flux
+// columns [HX-Q, HX+TX+R) and state columns [0, BXH).
+template <typename T, int O>
+__device__ __forceinline__ void fill_q_rows(QRows<T>& Qr, int tx, int i0, int own0, int own1, int nq) {
+  using C = OpCoef<O>;
+  constexpr int BC = C::b, CW = C::cw, Q = C::q, R = C::r;
+  const int i = i0 + tx;
+  const bool owned = i >= own0 && i < own1;
+  int bm, bp;
+  T wm[CW], wp[CW];
+  if (owned && i < BC) {
+    bm = bp = HX - i0;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+      wm[c] = Tab<T, O>::m(i, c);
+      wp[c] = Tab<T, O>::p(i, c);
+    }
+  } else if (owned && i > nq - 1 - BC) {
+    // tap t is node nq-cw+t, i.e. column cw-1-t of the mirrored closure row ii
+    const int ii = nq - 1 - i;
+    bm = bp = HX + nq - CW - i0;
+#pragma unroll
+    for (int t = 0; t < CW; ++t) {
+      wm[t] = -Tab<T, O>::p(ii, CW - 1 - t);
+      wp[t] = -Tab<T, O>::m(ii, CW - 1 - t);
+    }
+  } else {
+    // interior stencil, placed so that all cw taps stay inside the computed columns
+    const int dm = HX + tx - Q, dp = HX + tx - R;
+    bm = min(dm, HX + TX + R - CW);
+    bp = min(dp, BXH - CW);
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+      const int jm = bm + c - dm - Q;   // offset of this tap from the node for D-
+      const int jp = bp + c - dp - R;   // and for D+
+      wm[c] = owned && jm >= -Q && jm <= R ? T(-C::alpha(-jm)) : T(0);
+      wp[c] = owned && jp >= -R && jp <= Q ? T(C::alpha(jp)) : T(0);
+    }
+  }
+  Qr.bm[tx] = bm;
+  Qr.bp[tx] = bp;
+#pragma unroll
+  for (int c = 0; c < kMaxCW; ++c) {
+    Qr.wm[c][tx] = c < CW ? wm[c] : T(0);
+    Qr.wp[c][tx] = c < CW ? wp[c] : T(0);
+  }
 }
 
 template <typename T, int O>
@@ -168,7 +232,8 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
   const int kb = (blockIdx.z % nchunks) * chunk;
   const int ke = min(d.ns, kb + chunk);
   const bool active = i >= ax.own0 && i < ax.own1 && j >= ay.own0 && j < ay.own1;
-  const bool q_close = i < BC || i > d.nq - 1 - BC;
+  // a tile owning nodes within b of a q face takes its q rows from a per-thread table
+  const bool q_edge = ax.own0 < BC || ax.own1 > d.nq - BC;
   const bool r_close = j < BC || j > d.nr - 1 - BC;
   const bool qr_face = i == 0 || i == d.nq - 1 || j == 0 || j == d.nr - 1;
   const T ihq = A.inv_h[0], ihr = A.inv_h[1], ihs = A.inv_h[2];
@@ -185,6 +250,7 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
     mbar_init(&S.bar[1], 1);
     fence_mbar_init();
   }
+  if (q_edge && ty == 0) fill_q_rows<T, O>(S.qrows, tx, i0, ax.own0, ax.own1, d.nq);  // read after the first plane's barrier
   __syncthreads();
   if (tid == 0) issue_plane(S, 0, tm, i0, j0, kb, member);
   // closure-row sums of the s closure planes this chunk reaches (while the first copy flies)
@@ -233,7 +299,6 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
 #pragma unroll
     for (int c = 0; c < 3; ++c) vq[NV - 1][c] = lv[c];
     flux(la, ls, fq[NV - 1]);
-    if (k + 1 < ke) load_lead(k + 1);
     const long long off = pk + col;
     T dqi[9];
     if (A.mode == kModeStage) {
@@ -284,7 +349,7 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
     T e[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     T dv[3];
     // q
-    if (!q_close) {
+    if (!q_edge) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         T sf = T(0), sv = T(0);
@@ -295,22 +360,16 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
         rv[c] += ihq * sf;
         dv[c] = ihq * sv;
       }
-      const T a[3] = {st.aq[0][ty][HX + tx], st.aq[1][ty][HX + tx], st.aq[2][ty][HX + tx]};
-      add_strain(a, dv, e);
-    } else if (active) {
-      // closure row of a node within b of a q face: all its taps lie in this tile
-      const bool lo = i < BC;
-      const int row = lo ? i : d.nq - 1 - i;
+    } else {
+      const int bm = S.qrows.bm[tx], bp = S.qrows.bp[tx];
       T sf[3] = {T(0), T(0), T(0)}, sv[3] = {T(0), T(0), T(0)};
 #pragma unroll
       for (int c = 0; c < CW; ++c) {
-        const int cc = HX + (lo ? c : d.nq - 1 - c) - i0;
-        const T wm = lo ? Tab<T, O>::m(row, c) : -Tab<T, O>::p(row, c);
-        const T wp = lo ? Tab<T, O>::p(row, c) : -Tab<T, O>::m(row, c);
+        const T wm = S.qrows.wm[c][tx], wp = S.qrows.wp[c][tx];
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-          sf[m] += wm * F.fq[m][ty][cc];
-          sv[m] += wp * st.state[m][HX + ty][cc];
+          sf[m] += wm * F.fq[m][ty][bm + c];
+          sv[m] += wp * st.state[m][HX + ty][bp + c];
         }
       }
 #pragma unroll
@@ -318,6 +377,8 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
         rv[m] += ihq * sf[m];
         dv[m] = ihq * sv[m];
       }
+    }
+    {
       const T a[3] = {st.aq[0][ty][HX + tx], st.aq[1][ty][HX + tx], st.aq[2][ty][HX + tx]};
       add_strain(a, dv, e);
     }
@@ -384,6 +445,8 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
       const T a[3] = {st.as[0][ty][tx], st.as[1][ty][tx], st.as[2][ty][tx]};
       add_strain(a, dv, e);
     }
+    // lead values of the next plane (in flight during the epilogue and the next barrier)
+    if (k + 1 < ke) load_lead(k + 1);
 
     if (active) {
       T qc[9];
