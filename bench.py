@@ -8,6 +8,11 @@ stage kernel per stage).  Metric: million node-stage updates per second,
 nodes * 5 * steps / time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+    python bench.py --workload adjoint129_o4 [--adj-steps N]
+
+The second form times one misfit gradient of the adjoint workload (129 x 129 x 97, order 4,
+FP32 forward with FP64 misfit, 1500 steps, sqrt(N) checkpoints): forward run, checkpoint
+recomputation and adjoint stages, with the adjoint stage kernels' roofline.
 
 One JSON line on rank 0.  With --gpus N > 1 (torchrun) every rank runs an
 independent replica of the workload on its own GPU ("replicas only": the
@@ -33,6 +38,10 @@ UNIT = "Mnode-stage/s"
 WORKLOAD = "topo1025_o6_fp32"
 BYTES_PER_NODE_STAGE = 192        # 48 FP32 values per node per stage (algorithmic)
 BYTES_PER_NODE_STAGE0 = 156       # first stage: A_0 = 0, the RK register is not read
+NOMINAL_HBM_GBS = 7900.0          # HBM3e nominal, for the second fraction
+FLOP_PER_NODE_STAGE = 420         # order 6: 18 one-axis derivatives x 7 taps x 2, flux 45, strain 54,
+                                  # Hooke 12, Runge-Kutta 36, scaling 20
+FP64_PEAK_TFLOPS = 1.25           # GB300 FP64 nominal (the FP64 path is bound by it, not by HBM)
 
 
 def _peaks():
@@ -154,6 +163,72 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+ADJ_BYTES_PER_NODE_STAGE = 500   # adjoint prep 156 B + adjoint stage 264 B (FP32) + 80 B (FP64 rho, lambda,
+                                  # mu, J read, gradient read and written), FP32 state
+
+
+def run_adjoint(args, local):
+    """One misfit gradient of the adjoint workload, timed on the device."""
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_02600_gb300 import _lib as L
+    from paper_2011_02600_gb300.adjoint import workload_problem
+    from workloads.configs import config_by_name
+    cfg = config_by_name("adjoint129_o4")
+    nsteps = args.adj_steps or cfg.steps
+    p, _, _ = workload_problem(cfg, 32, nsteps=nsteps)
+    s = p.s
+    nq, nr, ns = cfg.nodes
+    nodes = nq * nr * ns
+    p.forward()                       # warm-up
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    L.sbp_kernel_timing(s.h, True)
+    L.sbp_kernel_times(s.h)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    phi = p.forward()
+    ev[1].record(stream)
+    g = p.gradient()
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    kms, kn = L.sbp_kernel_times(s.h)
+    L.sbp_kernel_timing(s.h, False)
+    clk = clocks.stop()
+    t_fwd, t_grad = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    adj_avg = kms[2] / max(1, kn[2])
+    stage_avg = kms[0] / max(1, kn[0])
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = ADJ_BYTES_PER_NODE_STAGE * nodes / (adj_avg / 1e3) / 1e9
+    value = nodes * 5 * nsteps / ((t_fwd + t_grad) / 1e3) / 1e6
+    line = {
+        "metric": "adjoint gradient throughput", "value": value, "unit": "Mnode-stage/s",
+        "n_gpus": 1, "steps": nsteps, "warmup": 1, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "adjoint129_o4", "nodes": list(cfg.nodes), "order": cfg.order,
+                   "checkpoint_every": p.C, "receivers": len(p.receivers),
+                   "what": "node-stages of the forward problem per second of forward run + gradient"},
+        "forward_ms": t_fwd, "gradient_ms": t_grad, "misfit": phi,
+        "gradient_norm": float(g.double().norm()),
+        "roofline": {"bound": "hbm", "kernel": "adjoint stage (prep + stage)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "algorithmic_bytes_per_launch": ADJ_BYTES_PER_NODE_STAGE * nodes,
+                     "avg_launch_ms": adj_avg, "launches": kn[2],
+                     "peak_source": "measured" if peaks else "fallback"},
+        "stage_kernel": {"avg_launch_ms": stage_avg, "launches": kn[0],
+                         "achieved_gbs": 184.8 * nodes / (stage_avg / 1e3) / 1e9},
+        "kernel_ms": {"tiled": kms[0], "general": kms[1], "adjoint": kms[2], "launches": kn},
+        "clocks": clk, "gpu_launches": int(kn[0] + kn[1] + 2 * kn[2]),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -164,6 +239,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nodes", default=None,
                     help="nq,nr,ns: a smaller instance of the workload (same generators; for profiling)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "adjoint129_o4"])
+    ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--adj-steps", type=int, default=None, help="steps of the adjoint workload (default: its 1500)")
     args = ap.parse_args()
 
     rank = int(os.environ.get("RANK", "0"))
@@ -176,6 +254,12 @@ def main():
         dist.init_process_group(backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
+    if args.workload == "adjoint129_o4":
+        if rank == 0:
+            run_adjoint(args, local)
         if dist:
             dist.destroy_process_group()
         return
@@ -196,7 +280,8 @@ def main():
     if args.nodes:
         import dataclasses
         cfg = dataclasses.replace(cfg, nodes=tuple(int(x) for x in args.nodes.split(",")))
-    s, info = build_solver(cfg, precision=32, device=f"cuda:{local}")
+    s, info = build_solver(cfg, precision=args.precision, device=f"cuda:{local}")
+    elem = args.precision // 8
     nq, nr, ns = cfg.nodes
     nodes = nq * nr * ns
     dt = info["dt"]
@@ -251,7 +336,7 @@ def main():
     else:
         kind, launches, kms_tot, knodes = "general", kn[1], kms[1], nodes
     # per launch: stage 0 reads no RK register; average over the 5 stages of a step
-    avg_bytes = knodes * (BYTES_PER_NODE_STAGE * 4 + BYTES_PER_NODE_STAGE0) / 5.0
+    avg_bytes = knodes * (BYTES_PER_NODE_STAGE * 4 + BYTES_PER_NODE_STAGE0) / 5.0 * (elem / 4)
     avg_ms = kms_tot / max(1, launches)
     achieved = avg_bytes / (avg_ms / 1e3) / 1e9
     peaks = _peaks()
@@ -268,12 +353,27 @@ def main():
             per_node = (float(kv["dram_bytes_per_node_stage0"]) + 4 * float(kv["dram_bytes_per_node_stage1to4"])) / 5
             prof_traffic = per_node * knodes
 
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": prof_traffic if elem == 4 else None, "kernel": kind,
+            "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms,
+            "launches": launches, "peak_source": "measured" if peaks else "fallback",
+            "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
+    if elem == 8:
+        # FP64 is bound by the FP64 pipe, not by HBM
+        tflops = FLOP_PER_NODE_STAGE * knodes / (avg_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kind,
+                "algorithmic_flop_per_launch": FLOP_PER_NODE_STAGE * knodes, "avg_launch_ms": avg_ms,
+                "launches": launches, "peak_source": "nominal FP64 rate",
+                "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak}
+
     # end to end: state in from pinned host memory, one step, state and energy out, per step
     e2e = None
     try:
-        nbytes = 9 * s.fs * 4
-        host_in = torch.empty(9 * s.fs, dtype=torch.float32, pin_memory=True)
-        host_out = torch.empty(9 * s.fs, dtype=torch.float32, pin_memory=True)
+        nbytes = 9 * s.fs * elem
+        tdt = torch.float32 if elem == 4 else torch.float64
+        host_in = torch.empty(9 * s.fs, dtype=tdt, pin_memory=True)
+        host_out = torch.empty(9 * s.fs, dtype=tdt, pin_memory=True)
         host_in.copy_(s.qbuf[s.current].cpu())
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         torch.cuda.synchronize()
@@ -287,7 +387,7 @@ def main():
         e_ms = ev[0].elapsed_time(ev[1]) / args.e2e_steps
         e2e = {"value": nodes * 5 / (e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": e_ms,
-               "what": "per step: the 9-field FP32 state copied in from pinned host memory, one RK step "
+               "what": "per step: the 9-field state copied in from pinned host memory, one RK step "
                        "through the C ABI, the state copied back to pinned host memory"}
         del host_in, host_out
     except Exception as ex:  # pinned memory can be unavailable
@@ -305,16 +405,13 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if elem == 4 else "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD if not args.nodes else WORKLOAD + " (reduced: profiling only)",
                    "nodes": list(cfg.nodes), "order": cfg.order,
                    "extent_m": list(cfg.extent), "stages_per_step": 5, "dt_s": dt,
                    "l2": "inputs larger than L2 (39 fields x 1.74 GB resident)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": prof_traffic, "kernel": kind,
-                     "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms,
-                     "launches": launches, "peak_source": "measured" if peaks else "fallback"},
+        "roofline": roof,
         "kernel_ms": {"tiled": kms[0], "general": kms[1], "launches": kn},
         "cpu_baseline": cpu,
         "clocks": clk,

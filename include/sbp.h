@@ -152,7 +152,9 @@ int sbp_set_kernel_path(SbpGrid* grid, int32_t path);
 /* Per-kernel timing: when enabled, each stage-kernel launch is bracketed by
  * CUDA events recorded on the launching stream.  sbp_kernel_times waits for
  * the recorded events, returns the summed milliseconds and launch counts per
- * kernel kind (index 0: tiled kernel, 1: general kernel) since the previous call, and clears them. */
+ * kernel kind (arrays of 3: index 0 the tiled stage kernel, 1 the general
+ * stage kernel, 2 one adjoint stage, its two kernels together) since the
+ * previous call, and clears them. */
 int sbp_kernel_timing(SbpGrid* grid, int32_t enable);
 int sbp_kernel_times(SbpGrid* grid, double* ms, int64_t* launches);
 
@@ -210,6 +212,14 @@ int sbp_adjoint_stage(SbpGrid* grid, int32_t stage, double dt, const void* u_sta
  * Needs sbp_set_receivers. */
 int sbp_misfit(SbpGrid* grid, const void* q, const double* data, double weight, double* acc, void* ubar,
                void* stream);
+
+/* Failure-detection self-test (no counterpart in the paper): launches one
+ * bounded wait on a shared-memory mbarrier that nothing completes, the wait
+ * the tiled stage kernel uses for its tile copies.  After `polls` polls
+ * (1..2^20, about 64 ns apart) it gives up and sets SBP_STATUS_TIMEOUT in the
+ * status word; the context stays usable.  SBP_ERR_ARG for polls outside
+ * that range. */
+int sbp_selftest_wait_timeout(SbpGrid* grid, uint32_t polls, void* stream);
 
 /* Copy the device status word into *bits and clear it (synchronises). */
 int sbp_status(SbpGrid* grid, uint32_t* bits, void* stream);

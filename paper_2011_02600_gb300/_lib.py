@@ -20,7 +20,7 @@ EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sb
             "sbp_rk_coefficients", "sbp_energy_noalloc", "sbp_rhs_adjoint", "sbp_adjoint_stage",
             "sbp_misfit", "sbp_set_batch", "sbp_set_sources", "sbp_nn_gemm", "sbp_nn_im2col", "sbp_nn_col2im",
             "sbp_nn_upsample2", "sbp_nn_relu_backward", "sbp_nn_bias_grad", "sbp_nn_mse", "sbp_nn_adam",
-            "sbp_nn_mlp_to_conv", "sbp_nn_cast_bf16", "sbp_nn_moment_combine", "sbp_last_error")
+            "sbp_nn_mlp_to_conv", "sbp_nn_cast_bf16", "sbp_nn_moment_combine", "sbp_selftest_wait_timeout", "sbp_last_error")
 
 
 class SbpError(RuntimeError):
@@ -93,6 +93,7 @@ def lib(path=None):
         "sbp_nn_mlp_to_conv": [P, P, i32, i32, i32, i32, P],
         "sbp_nn_cast_bf16": [P, P, i64, P],
         "sbp_nn_moment_combine": [P, P, P, P, P, i32, i32, i32, i32, P],
+        "sbp_selftest_wait_timeout": [P, ctypes.c_uint32, P],
         "sbp_set_sources": [P, i32, ctypes.POINTER(SbpSource), P, P],
     }
     for name, args in sig.items():
@@ -181,8 +182,8 @@ def sbp_kernel_timing(h, enable):
 
 
 def sbp_kernel_times(h):
-    """([ms_tiled, ms_general], [launches_tiled, launches_general]) since the previous call."""
-    ms, n = (ctypes.c_double * 2)(), (ctypes.c_int64 * 2)()
+    """([ms_tiled, ms_general, ms_adjoint], [launches ...]) since the previous call."""
+    ms, n = (ctypes.c_double * 3)(), (ctypes.c_int64 * 3)()
     _check(lib().sbp_kernel_times(h, ms, n))
     return list(ms), list(n)
 
@@ -318,3 +319,7 @@ def sbp_nn_cast_bf16(x, y, n, stream):
 
 def sbp_nn_moment_combine(G, m, y, dy, dG, n_out, B, T, backward, stream):
     _check(lib().sbp_nn_moment_combine(_ptr(G), _ptr(m), _ptr(y), _ptr(dy), _ptr(dG), n_out, B, T, backward, stream))
+
+
+def sbp_selftest_wait_timeout(h, polls, stream):
+    _check(lib().sbp_selftest_wait_timeout(h, polls, stream))

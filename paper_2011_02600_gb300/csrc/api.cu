@@ -107,7 +107,7 @@ struct SbpGrid {
   // tensor maps of the tiled stage kernel, per state buffer (q0, q1)
   bool tma_ok[2] = {false, false};
   sbp::TmaSet tma[2];
-  // optional per-kernel CUDA-event timing of the stage kernels (kind 0 = tiled, 1 = general)
+  // optional per-kernel CUDA-event timing (kind 0 = tiled stage, 1 = general stage, 2 = adjoint stage)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
@@ -343,8 +343,11 @@ int adjoint_impl(SbpGrid* g, int mode, int stage, double dt, const void* u, void
     A.inv_h[x] = S.inv_h[x];
     A.inv_h0[x] = S.inv_h0[x];
   }
+  TimedLaunch ta(g, 2, st);
   cudaError_t e = sbp::launch_adjoint<T>(A, g->desc.order, st);
-  return e == cudaSuccess ? SBP_OK : cuda_fail(e, "adjoint");
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint");
+  ta.done();
+  return SBP_OK;
 }
 
 }  // namespace
@@ -539,8 +542,10 @@ int sbp_kernel_timing(SbpGrid* g, int32_t enable) {
 
 int sbp_kernel_times(SbpGrid* g, double* ms, int64_t* launches) {
   if (!g || !ms || !launches) return fail(SBP_ERR_ARG, "null argument");
-  ms[0] = ms[1] = 0.0;
-  launches[0] = launches[1] = 0;
+  for (int k = 0; k < 3; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
   for (auto& p : g->ev_pending) {
     cudaError_t e = cudaEventSynchronize(p.second.second);
     float t = 0.f;
@@ -730,6 +735,13 @@ int sbp_misfit(SbpGrid* g, const void* q, const double* data, double weight, dou
                                : sbp::launch_misfit<double>((const double*)q, g->dims, g->rec_off, g->rec_n, data,
                                                              weight, acc, (double*)ubar, (cudaStream_t)stream);
   return e == cudaSuccess ? SBP_OK : cuda_fail(e, "misfit");
+}
+
+int sbp_selftest_wait_timeout(SbpGrid* g, uint32_t polls, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (polls == 0 || polls > (1u << 20)) return fail(SBP_ERR_ARG, "polls must lie in 1..2^20");
+  cudaError_t e = sbp::launch_wait_selftest(polls, g->status, (cudaStream_t)stream);
+  return e == cudaSuccess ? SBP_OK : cuda_fail(e, "wait self-test");
 }
 
 int sbp_status(SbpGrid* g, uint32_t* bits, void* stream) {

@@ -111,8 +111,8 @@ template cudaError_t launch_material<double>(const double*, const double*, doubl
 // Energy (Eq. physical_energy_discrete with P~): 1/2 sum H J (rho |v|^2 + sigma^T S sigma),
 // written with the stored coefficients: J rho = 1/(1/(rho J)), and
 // J sigma^T S sigma = [sum s_ii^2 + 2 sum s_ij^2 - l/(3 l + 2 m) tr^2] / (2 m)
-// with l = lambda/J, m = mu/J.  Accumulated in FP64; warp shuffles, then a
-// fixed-order block reduction.
+// with l = lambda/J, m = mu/J.  Accumulated in FP64 (per row, per thread, then warp
+// shuffles and a fixed-order block reduction), so the result is deterministic.
 constexpr int kEnergyBlocks = 1184;  // 152 SMs x 8
 constexpr int kEnergyThreads = 256;
 int energy_blocks() { return kEnergyBlocks; }
@@ -123,42 +123,54 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Energy density of one node over a single division: with l = lambda/J, m = mu/J,
+// r = 1/(rho J) and A = sum s_ii^2 + 2 sum s_ij^2,
+//   rho J |v|^2 + J sigma^T S sigma = |v|^2 / r + (A (3 l + 2 m) - l tr^2) / ((3 l + 2 m) 2 m)
+//                                  = (|v|^2 D + r (A (3 l + 2 m) - l tr^2)) / (r D),  D = (3 l + 2 m) 2 m.
+// Evaluated in the state's precision (FP32 terms are summed in FP64).
+template <typename T>
+__device__ __forceinline__ T energy_density(const T v[3], const T s[6], T r, T l, T m) {
+  const T v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const T tr = s[0] + s[1] + s[2];
+  const T A = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + T(2) * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
+  const T c = T(3) * l + T(2) * m;
+  const T D = c * T(2) * m;
+  return (v2 * D + r * (A * c - l * tr * tr)) / (r * D);
+}
+
+// One warp per (r, s) row of nodes (q contiguous, coalesced); rows strided over the grid.
 template <typename T, int O>
 __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const T* __restrict__ q, const T* __restrict__ mat,
                                                                 Dims d, double* __restrict__ partial,
                                                                 unsigned* status) {
-  const long long total = (long long)d.nq * d.nr * d.ns;
+  const int warps = kEnergyThreads / 32;
+  const int lane = threadIdx.x & 31;
+  const int rows = d.nr * d.ns;
   const double hq = 1.0 / (d.nq - 1), hr = 1.0 / (d.nr - 1), hs = 1.0 / (d.ns - 1);
+  const long long fs = d.fs;
   double acc = 0.0;
   bool bad = false;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % d.nq);
-    const long long rest = t / d.nq;
-    const int j = (int)(rest % d.nr);
-    const int k = (int)(rest / d.nr);
-    const long long n0 = (long long)k * d.plane + (long long)j * d.ldq + i;
-    const double H = hq * norm_weight<O>(i, d.nq) * hr * norm_weight<O>(j, d.nr) * hs * norm_weight<O>(k, d.ns);
-    double v2 = 0.0;
+  for (int row = blockIdx.x * warps + (threadIdx.x >> 5); row < rows; row += gridDim.x * warps) {
+    const int j = row % d.nr, k = row / d.nr;
+    const double wjk = hr * norm_weight<O>(j, d.nr) * hs * norm_weight<O>(k, d.ns);
+    const long long base = (long long)k * d.plane + (long long)j * d.ldq;
+    double racc = 0.0;
+    for (int i = lane; i < d.nq; i += 32) {
+      const long long n0 = base + i;
+      T v[3], sg[6];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double v = (double)q[c * d.fs + n0];
-      v2 += v * v;
+      for (int c = 0; c < 3; ++c) v[c] = q[c * fs + n0];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) sg[c] = q[(3 + c) * fs + n0];
+      const T dens = energy_density<T>(v, sg, mat[n0], mat[fs + n0], mat[2 * fs + n0]);
+      bad |= !isfinite(dens);
+      racc += hq * norm_weight<O>(i, d.nq) * (double)dens;
     }
-    double s[6];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) s[c] = (double)q[(3 + c) * d.fs + n0];
-    const double irhoJ = (double)mat[n0], l = (double)mat[d.fs + n0], m = (double)mat[2 * d.fs + n0];
-    const double tr = s[0] + s[1] + s[2];
-    const double sSs = (s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + 2.0 * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]) -
-                        l / (3.0 * l + 2.0 * m) * tr * tr) / (2.0 * m);
-    const double dens = v2 / irhoJ + sSs;
-    bad |= !isfinite(dens);
-    acc += H * dens;
+    acc += wjk * racc;
   }
   __shared__ double red[kEnergyThreads / 32];
   acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  if (lane == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x < 32) {
     double v = threadIdx.x < kEnergyThreads / 32 ? red[threadIdx.x] : 0.0;

@@ -486,10 +486,52 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
   }
 }
 
+// Self-test of the bounded wait used by the tiled kernel: one thread initialises an mbarrier
+// that expects one arrival, nothing arrives, and the wait gives up after `polls` polls and
+// records SBP_STATUS_TIMEOUT in the status word, exactly as the stage kernel does when a tile
+// copy never lands.  The barrier lives in shared memory; nothing is left in flight.
+__global__ void wait_selftest_kernel(unsigned polls, unsigned* status) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  fence_mbar_init();
+  if (!mbar_wait_bounded(&bar, 0, polls)) atomicOr(status, 8u);
+}
+
+cudaError_t launch_wait_selftest(unsigned polls, unsigned* status, cudaStream_t st) {
+  wait_selftest_kernel<<<1, 32, 0, st>>>(polls, status);
+  return cudaGetLastError();
+}
+
+// Planes a chunk spends filling its s queues before the first output plane.
+template <int O>
+constexpr int NVQ() { return OpCoef<O>::r + OpCoef<O>::q; }
+
 template <typename T, int O>
 cudaError_t launch_tiled_order(const StageArgs<T>& A, const TmaSet& tm, cudaStream_t st) {
   const int ni = A.d.nq, nj = A.d.nr, nk = A.d.ns;
-  const int nchunks = (nk + 95) / 96;
+  // s chunks: at most 96 planes; when that leaves SM slots idle (few tiles), more chunks
+  // (at least 16 planes each), the count that minimises waves x (chunk + queue warm-up)
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 148;
+  const long long tiles = (long long)((ni + TX - 1) / TX) * ((nj + TY - 1) / TY) * A.nb;
+  const long long slots = (long long)sms * tiled_min_blocks<T>();
+  int nchunks = (nk + 95) / 96;
+  if (tiles * nchunks < slots) {
+    const int base = nchunks;
+    long long best = -1;
+    for (int nc = base; nc <= base + 8; ++nc) {
+      const int ch = (nk + nc - 1) / nc;
+      if (nc > base && ch < 16) break;
+      const long long waves = (tiles * ((nk + ch - 1) / ch) + slots - 1) / slots;
+      const long long cost = waves * (ch + NVQ<O>());
+      if (best < 0 || cost < best) {
+        best = cost;
+        nchunks = nc;
+      }
+    }
+  }
   const int chunk = (nk + nchunks - 1) / nchunks;
   dim3 grid((ni + TX - 1) / TX, (nj + TY - 1) / TY, ((nk + chunk - 1) / chunk) * A.nb);
   if (grid.z > 65535 || grid.y > 65535) return cudaErrorInvalidConfiguration;

@@ -45,6 +45,9 @@ cudaError_t launch_stage_general(const StageArgs<T>& A, int order, const BoxList
 template <typename T>
 cudaError_t launch_stage_tiled(const StageArgs<T>& A, int order, const TmaSet& tm, cudaStream_t st);
 
+// One bounded mbarrier wait that nothing completes (sets status bit 8 after `polls` polls).
+cudaError_t launch_wait_selftest(unsigned polls, unsigned* status, cudaStream_t st);
+
 cudaError_t launch_metrics(const double* xyz, double* jmet, const Dims& d, int order, unsigned* status,
                            cudaStream_t st);
 
