@@ -107,6 +107,8 @@ struct SbpGrid {
   // tensor maps of the tiled stage kernel, per state buffer (q0, q1)
   bool tma_ok[2] = {false, false};
   sbp::TmaSet tma[2];
+  // tensor maps of other inputs of the tiled kernel (the adjoint's yhat and stage states), by pointer
+  std::vector<std::pair<const void*, sbp::TmaSet>> tma_cache;
   // optional per-kernel CUDA-event timing (kind 0 = tiled stage, 1 = general stage, 2 = adjoint stage)
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -159,6 +161,7 @@ sbp::StageArgs<T> make_args(const SbpGrid* g, const void* q, void* qout, int mod
   for (int x = 0; x < 3; ++x) {
     A.inv_h[x] = (T)(N[x] - 1);
     A.inv_h0[x] = (T)((double)(N[x] - 1) / w0);
+    A.h[x] = (T)(1.0 / (N[x] - 1));
   }
   return A;
 }
@@ -221,6 +224,23 @@ int encode_maps(const SbpGrid* g, const void* q, int nb, sbp::TmaSet* out) {
   if (!rc) rc = one(&out->met_s, g->met, 9, 32, 8, 3);
   if (!rc) rc = one(&out->mat, g->mat, 3, 32, 8, 3);
   return rc;
+}
+
+// Tensor maps of an unbatched input buffer of the tiled kernel, encoded once per pointer.
+int cached_maps(SbpGrid* g, const void* p, const sbp::TmaSet** out) {
+  for (auto& c : g->tma_cache)
+    if (c.first == p) {
+      *out = &c.second;
+      return SBP_OK;
+    }
+  if (g->tma_cache.size() >= 16) g->tma_cache.clear();
+  g->tma_cache.emplace_back(p, sbp::TmaSet{});
+  if (int rc = encode_maps(g, p, 1, &g->tma_cache.back().second)) {
+    g->tma_cache.pop_back();
+    return rc;
+  }
+  *out = &g->tma_cache.back().second;
+  return SBP_OK;
 }
 
 template <typename T>
@@ -344,8 +364,34 @@ int adjoint_impl(SbpGrid* g, int mode, int stage, double dt, const void* u, void
     A.inv_h0[x] = S.inv_h0[x];
   }
   TimedLaunch ta(g, 2, st);
-  cudaError_t e = sbp::launch_adjoint<T>(A, g->desc.order, st);
-  if (e != cudaSuccess) return cuda_fail(e, "adjoint");
+  if (!g->use_tiled) {
+    cudaError_t e = sbp::launch_adjoint<T>(A, g->desc.order, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint");
+  } else {
+    // prep (Wb_k, yhat), then the tiled gradient pass on U_k and the tiled L^T pass on yhat
+    cudaError_t e = sbp::launch_adjoint_prep<T>(A, g->desc.order, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint prep");
+    sbp::StageArgs<T> S2 = make_args<T>(g, nullptr, nullptr, mode == 1 ? sbp::kModeStage : sbp::kModeRhs,
+                                        mode == 1 ? kRkA[stage] : 0.0, 0.0, dt, 1);
+    S2.ubar_next = A.ubar_next;
+    S2.ubar_out = A.ubar_out;
+    S2.wbar = A.wbar;
+    S2.yhat = A.yhat;
+    S2.rlmj = rlmj;
+    S2.grad = grad;
+    if (grad && u) {
+      const sbp::TmaSet* tu = nullptr;
+      if (int rc = cached_maps(g, u, &tu)) return rc;
+      S2.q = (const T*)u;
+      e = sbp::launch_adjoint_tiled<T>(S2, g->desc.order, 2, *tu, st);
+      if (e != cudaSuccess) return cuda_fail(e, "adjoint gradient (tiled)");
+    }
+    const sbp::TmaSet* ty = nullptr;
+    if (int rc = cached_maps(g, scratch, &ty)) return rc;
+    S2.q = (const T*)scratch;
+    e = sbp::launch_adjoint_tiled<T>(S2, g->desc.order, 1, *ty, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint (tiled)");
+  }
   ta.done();
   return SBP_OK;
 }
@@ -449,6 +495,7 @@ int sbp_bind(SbpGrid* g, void* q0, void* q1, void* dq, void* met, void* mat) {
   g->mat = mat;
   g->cur = 0;
   g->tma_ok[0] = g->tma_ok[1] = false;
+  g->tma_cache.clear();
   if (!g->partial) {
     cudaError_t e = cudaMalloc(&g->partial, sizeof(double) * sbp::energy_blocks());
     if (e == cudaSuccess) e = cudaMalloc(&g->eout, sizeof(double));

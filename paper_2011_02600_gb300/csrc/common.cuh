@@ -43,11 +43,19 @@ struct StageArgs {
   T bc_gamma[6];
   T inv_h[3];       // N_xi - 1 (reference spacing 1/(N_xi - 1))
   T inv_h0[3];      // 1 / H_xi[0] = (N_xi - 1) / w_0
+  T h[3];           // reference spacing 1 / (N_xi - 1)
   unsigned* status; // device status word (bit 8: a tile copy timed out)
   int nb;           // independent states processed together (shared metrics and coefficients)
   long long bstride;  // elements between consecutive states (9 fields)
   T* sclose;          // tiled kernel scratch: s-closure sums, 2 b 6 planes per state
   long long sc_bstride;  // elements between consecutive states' scratch
+  // adjoint passes of the tiled kernel (q is then yhat = H^-1 P~ Wb_k, or U_k)
+  const T* ubar_next;   // Ub_{k+1} (null: zero)
+  T* ubar_out;          // Ub_k, or L^T w (mode kModeRhs)
+  T* wbar;              // Wb_k, replaced by A_k Wb_k
+  const T* yhat;        // H^-1 P~ Wb_k (the gradient pass reads it at faces)
+  const double* rlmj;   // rho, lambda, mu, J (FP64)
+  double* grad;         // gradient accumulators (FP64, 3 fields)
 };
 
 // Closure rows of D+ and D- (unit spacing), one private copy per translation unit.
@@ -112,6 +120,23 @@ template <int O>
 __host__ __device__ __forceinline__ double norm_weight(int pos, int N) {
   const int e = pos < N - 1 - pos ? pos : N - 1 - pos;
   return OpCoef<O>::w(e);
+}
+
+// Norm weight and its reciprocal in precision T, each a compile-time constant (no
+// conversion or division at run time).
+template <typename T, int O>
+__device__ __forceinline__ T norm_weight_t(int pos, int N) {
+  const int e = pos < N - 1 - pos ? pos : N - 1 - pos;
+  constexpr T w0 = T(OpCoef<O>::w(0)), w1 = T(OpCoef<O>::w(1)), w2 = T(OpCoef<O>::w(2)), w3 = T(OpCoef<O>::w(3)),
+              w4 = T(OpCoef<O>::w(4)), w5 = T(OpCoef<O>::w(5));
+  return e == 0 ? w0 : e == 1 ? w1 : e == 2 ? w2 : e == 3 ? w3 : e == 4 ? w4 : e == 5 ? w5 : T(1);
+}
+template <typename T, int O>
+__device__ __forceinline__ T norm_weight_inv_t(int pos, int N) {
+  const int e = pos < N - 1 - pos ? pos : N - 1 - pos;
+  constexpr T r0 = T(1.0 / OpCoef<O>::w(0)), r1 = T(1.0 / OpCoef<O>::w(1)), r2 = T(1.0 / OpCoef<O>::w(2)),
+              r3 = T(1.0 / OpCoef<O>::w(3)), r4 = T(1.0 / OpCoef<O>::w(4)), r5 = T(1.0 / OpCoef<O>::w(5));
+  return e == 0 ? r0 : e == 1 ? r1 : e == 2 ? r2 : e == 3 ? r3 : e == 4 ? r4 : e == 5 ? r5 : T(1);
 }
 
 // Flux rows of Eq. split_form with e_xi = a: F = sigma a.

@@ -24,6 +24,7 @@
 //     buffer that the same thread reads back when it gets to the plane.
 //   * Nodes on a face add the face's penalty (free surface or characteristic SAT).
 // The stage update (2N-storage Runge-Kutta) is fused in the epilogue.
+#include "adjoint_terms.cuh"
 #include "common.cuh"
 #include "launch.h"
 #include "tma.cuh"
@@ -204,7 +205,10 @@ __device__ __forceinline__ void fill_q_rows(QRows<T>& Qr, int tx, int i0, int ow
   }
 }
 
-template <typename T, int O>
+// KIND 0: the forward stage.  KIND 1: the adjoint's L^T pass on q = yhat (-H times the
+// forward rows, face terms of the transposes; Ub and Wb updated).  KIND 2: the material
+// gradient pass on q = U_k (forward rows and penalties contracted with Wb_k).
+template <typename T, int O, int KIND>
 __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
     stage_tiled_kernel(StageArgs<T> A, int chunk, const __grid_constant__ TmaSet tm) {
   using C = OpCoef<O>;
@@ -300,10 +304,27 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
     for (int c = 0; c < 3; ++c) vq[NV - 1][c] = lv[c];
     flux(la, ls, fq[NV - 1]);
     const long long off = pk + col;
-    T dqi[9];
-    if (A.mode == kModeStage) {
+    // the epilogue's own inputs at this node, fetched before the tile wait so that their
+    // latency overlaps the plane's derivatives: the RK register (forward stage), Ub_{k+1} and
+    // Wb_k (L^T pass), Wb_k, rho and J (gradient pass)
+    T dqi[9], pre[9];
+    double rj[2];
+    if (KIND == 0 && A.mode == kModeStage) {
 #pragma unroll
       for (int c = 0; c < 9; ++c) dqi[c] = ld(dqm, c * fs + off);
+    }
+    if (KIND == 1 && A.mode != kModeRhs) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        dqi[c] = A.ubar_next ? ld(A.ubar_next, c * fs + off) : T(0);
+        pre[c] = ld(A.wbar, c * fs + off);
+      }
+    }
+    if (KIND == 2) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) pre[c] = ld(A.wbar, c * fs + off);
+      rj[0] = active ? __ldg(A.rlmj + off) : 0.0;
+      rj[1] = active ? __ldg(A.rlmj + 3 * fs + off) : 0.0;
     }
 
     if (!mbar_wait_bounded(&S.bar[sidx], phase, kWaitLimit)) {
@@ -448,7 +469,7 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
     // lead values of the next plane (in flight during the epilogue and the next barrier)
     if (k + 1 < ke) load_lead(k + 1);
 
-    if (active) {
+    if (active && KIND == 0) {
       T qc[9];
 #pragma unroll
       for (int c = 0; c < 9; ++c) qc[c] = st.state[c][HX + ty][HX + tx];
@@ -474,6 +495,67 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
           dqm[f * fs + off] = dn;
           qout[f * fs + off] = qc[f] + A.rk_b * dn;
         }
+      }
+    } else if (active) {
+      T qc[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) qc[c] = st.state[c][HX + ty][HX + tx];
+      const bool face = qr_face || k == 0 || k == d.ns - 1;
+      const int pos[3] = {i, j, k};
+      const int N[3] = {d.nq, d.nr, d.ns};
+      const T irhoJ = st.mat[0][ty][tx], lamJ = st.mat[1][ty][tx], muJ = st.mat[2][ty][tx];
+      T a[3][3];
+      if (face) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          a[0][c] = st.aq[c][ty][HX + tx];
+          a[1][c] = st.ar[c][HX + ty][tx];
+          a[2][c] = st.as[c][ty][tx];
+        }
+      }
+      if (KIND == 2 && face)
+        add_face_penalties(pos, N, a, qc, irhoJ, lamJ, muJ, A.bc_kind, A.bc_gamma, A.inv_h0, rv, e);
+      if (KIND == 1) {
+        // L^T Wb_k = -H (forward rows on yhat) + face terms, y = H yhat = P~ Wb_k at the node
+        const T H = norm_weight_t<T, O>(i, d.nq) * A.h[0] * norm_weight_t<T, O>(j, d.nr) * A.h[1] *
+                    norm_weight_t<T, O>(k, d.ns) * A.h[2];
+        T vb[3], sb[6];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) vb[c] = -H * rv[c];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) sb[c] = -H * e[c];
+        if (face) {
+          T y[9];
+#pragma unroll
+          for (int f = 0; f < 9; ++f) y[f] = H * qc[f];
+          adjoint_face_terms(pos, N, a, y, irhoJ, lamJ, muJ, A.bc_kind, A.bc_gamma, A.inv_h0, vb, sb);
+        }
+        const T m9[9] = {vb[0], vb[1], vb[2], sb[0], sb[1], sb[2], sb[3], sb[4], sb[5]};
+        if (A.mode == kModeRhs) {
+#pragma unroll
+          for (int f = 0; f < 9; ++f) A.ubar_out[f * fs + off] = m9[f];
+        } else {
+#pragma unroll
+          for (int f = 0; f < 9; ++f) {
+            A.ubar_out[f * fs + off] = dqi[f] + A.dt * m9[f];
+            A.wbar[f * fs + off] = A.rk_a * pre[f];
+          }
+        }
+      } else {
+        // dt Wb_k . d(P~ M U_k)/d(rho, lambda, mu) at the node
+        T y[9];
+        if (face) {
+          const T H = norm_weight_t<T, O>(i, d.nq) * A.h[0] * norm_weight_t<T, O>(j, d.nr) * A.h[1] *
+                      norm_weight_t<T, O>(k, d.ns) * A.h[2];
+#pragma unroll
+          for (int f = 0; f < 9; ++f) y[f] = H * A.yhat[f * fs + off];
+        }
+        double g[3];
+        gradient_terms(rv, e, qc, pre, y, pos, N, a, irhoJ, lamJ, muJ, rj[0], rj[1], A.bc_kind, A.bc_gamma,
+                       A.inv_h0, (double)A.dt, g);
+        // one writer per node and launch: a reduction that needs no read-back
+#pragma unroll
+        for (int c = 0; c < 3; ++c) atomicAdd(A.grad + c * fs + off, g[c]);
       }
     }
 #pragma unroll
@@ -507,7 +589,7 @@ cudaError_t launch_wait_selftest(unsigned polls, unsigned* status, cudaStream_t 
 template <int O>
 constexpr int NVQ() { return OpCoef<O>::r + OpCoef<O>::q; }
 
-template <typename T, int O>
+template <typename T, int O, int KIND>
 cudaError_t launch_tiled_order(const StageArgs<T>& A, const TmaSet& tm, cudaStream_t st) {
   const int ni = A.d.nq, nj = A.d.nr, nk = A.d.ns;
   // s chunks: at most 96 planes; when that leaves SM slots idle (few tiles), more chunks
@@ -537,24 +619,46 @@ cudaError_t launch_tiled_order(const StageArgs<T>& A, const TmaSet& tm, cudaStre
   if (grid.z > 65535 || grid.y > 65535) return cudaErrorInvalidConfiguration;
   dim3 block(TX, TY);
   const size_t smem = sizeof(TiledShared<T>);
-  cudaError_t e = cudaFuncSetAttribute(stage_tiled_kernel<T, O>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(stage_tiled_kernel<T, O, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  stage_tiled_kernel<T, O><<<grid, block, smem, st>>>(A, chunk, tm);
+  stage_tiled_kernel<T, O, KIND><<<grid, block, smem, st>>>(A, chunk, tm);
   return cudaGetLastError();
+}
+
+template <typename T, int KIND>
+cudaError_t launch_kind(const StageArgs<T>& A, int order, const TmaSet& tm, cudaStream_t st) {
+  if (!A.sclose) return cudaErrorInvalidValue;
+  switch (order) {
+    case 2: return launch_tiled_order<T, 2, KIND>(A, tm, st);
+    case 4: return launch_tiled_order<T, 4, KIND>(A, tm, st);
+    case 6: return launch_tiled_order<T, 6, KIND>(A, tm, st);
+    default: return cudaErrorNotSupported;
+  }
 }
 
 template <typename T>
 cudaError_t launch_stage_tiled(const StageArgs<T>& A, int order, const TmaSet& tm, cudaStream_t st) {
-  if (!A.sclose) return cudaErrorInvalidValue;
-  switch (order) {
-    case 2: return launch_tiled_order<T, 2>(A, tm, st);
-    case 4: return launch_tiled_order<T, 4>(A, tm, st);
-    case 6: return launch_tiled_order<T, 6>(A, tm, st);
-    default: return cudaErrorNotSupported;
-  }
+  return launch_kind<T, 0>(A, order, tm, st);
 }
+
+template <typename T>
+cudaError_t launch_adjoint_tiled(const StageArgs<T>& A, int order, int pass, const TmaSet& tm, cudaStream_t st) {
+  if (A.nb != 1) return cudaErrorInvalidValue;
+  if (pass == 1) {
+    if (!A.ubar_out || (A.mode != kModeRhs && !A.wbar)) return cudaErrorInvalidValue;
+    return launch_kind<T, 1>(A, order, tm, st);
+  }
+  if (pass == 2) {
+    if (!A.wbar || !A.yhat || !A.rlmj || !A.grad) return cudaErrorInvalidValue;
+    return launch_kind<T, 2>(A, order, tm, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
 template cudaError_t launch_stage_tiled<float>(const StageArgs<float>&, int, const TmaSet&, cudaStream_t);
 template cudaError_t launch_stage_tiled<double>(const StageArgs<double>&, int, const TmaSet&, cudaStream_t);
+template cudaError_t launch_adjoint_tiled<float>(const StageArgs<float>&, int, int, const TmaSet&, cudaStream_t);
+template cudaError_t launch_adjoint_tiled<double>(const StageArgs<double>&, int, int, const TmaSet&, cudaStream_t);
 
 }  // namespace sbp

@@ -30,8 +30,12 @@ struct AdjArgs {
   T inv_h0[3];
 };
 
+// General adjoint stage: the prep kernel (Wb_k, yhat) and the one-thread-per-node L^T and
+// gradient kernel; launch_adjoint_prep alone runs the first of the two.
 template <typename T>
 cudaError_t launch_adjoint(const AdjArgs<T>& A, int order, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adjoint_prep(const AdjArgs<T>& A, int order, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_misfit(const T* q, const Dims& d, const int32_t* off, int n, const double* data, double w,
@@ -44,6 +48,12 @@ cudaError_t launch_stage_general(const StageArgs<T>& A, int order, const BoxList
 // `tm`; A.sclose must hold 2 b 6 planes per state.
 template <typename T>
 cudaError_t launch_stage_tiled(const StageArgs<T>& A, int order, const TmaSet& tm, cudaStream_t st);
+
+// The tiled kernel's adjoint passes (after launch_adjoint_prep): pass 2, the material
+// gradient on q = U_k (tensor maps of U_k), then pass 1, L^T on q = yhat (maps of yhat),
+// which replaces Wb_k by A_k Wb_k.  Unbatched grids only.
+template <typename T>
+cudaError_t launch_adjoint_tiled(const StageArgs<T>& A, int order, int pass, const TmaSet& tm, cudaStream_t st);
 
 // One bounded mbarrier wait that nothing completes (sets status bit 8 after `polls` polls).
 cudaError_t launch_wait_selftest(unsigned polls, unsigned* status, cudaStream_t st);

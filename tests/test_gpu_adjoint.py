@@ -186,3 +186,37 @@ def test_autograd_function():
     g = p2.gradient()
     for f in range(3):
         assert torch.equal(gr[f], g[f])
+
+
+@pytest.mark.parametrize("order,nodes", [(2, (40, 20, 13)), (4, (70, 19, 30)), (6, (45, 30, 40)), (4, (11, 11, 11)),
+                                         (6, (16, 17, 16))])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_tiled_adjoint_matches_general_path(order, nodes, prec):
+    """The tiled kernel's adjoint passes (L^T on yhat, the gradient on U_k: several tiles,
+    ragged and minimum sizes) against the general one-thread-per-node adjoint kernels: L^T y,
+    and a whole misfit gradient (forward run, checkpoints, adjoint stages)."""
+    ext = (1000.0, 1100.0, 900.0)
+    X = node_coordinates(make_map("curvy", ext), nodes)
+    mat = make_medium("smooth_gradient", Lz=900.0)(*X)
+    s = _solver(nodes, order, prec, MIXED, X, mat)
+    y = random_state(nodes, 61, 1.0e-6, 1.0)
+    LT = []
+    for path in (0, 1):
+        s.set_kernel_path(path)
+        LT.append(_gpu_LT(s, y))
+    tol = 1e-12 if prec == 64 else 2e-5
+    scale = np.abs(LT[1]).max(axis=(1, 2, 3), keepdims=True)
+    assert np.abs(LT[0] - LT[1]).max() < tol * scale.max()
+    assert (np.abs(LT[0] - LT[1]) / scale).max() < tol
+    c = _misfit_case(nsteps=6, order=order, nodes=nodes)
+    c["bc"] = MIXED
+    grads = []
+    for path in (0, 1):
+        p = _gpu_problem(c, prec)
+        p.s.set_kernel_path(path)
+        _set(p, c["mat"])
+        p.forward()
+        grads.append(p.gradient().double().cpu().numpy())
+    for f in range(3):
+        sc = np.abs(grads[1][f]).max()
+        assert np.abs(grads[0][f] - grads[1][f]).max() < (1e-11 if prec == 64 else 1e-4) * sc, f
