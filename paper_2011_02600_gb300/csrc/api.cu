@@ -214,7 +214,7 @@ int encode_maps(const SbpGrid* g, const void* q, int nb, sbp::TmaSet* out) {
     const cuuint32_t box[4] = {bx, by, 1, bf};
     const cuuint32_t es[4] = {1, 1, 1, 1};
     CUresult r = enc(m, dt, 4, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? SBP_OK : fail(SBP_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   };

@@ -54,6 +54,28 @@ __device__ __forceinline__ TileAxis tile_axis(int t, int nt, int n, int w, int a
   return a;
 }
 
+// Launch order of the tiles of one s chunk: groups of kSwizzle tile columns (q), in each
+// group q fastest, then r.  Blocks start in about launch order, so the tiles that share a
+// halo row (r neighbours, kSwizzle launches apart) and a halo column (q neighbours, next to
+// each other) run close together in time and the second reads the halo from L2; in plain
+// row order r neighbours start a whole row of tiles apart, and on wide grids the halo has
+// left L2 by then.
+constexpr int kSwizzle = 8;
+__device__ __forceinline__ void swizzle_tiles(int lin, int nbx, int nby, int& bx, int& by) {
+  const int full = nbx / kSwizzle;                 // complete groups
+  const int group = lin / (kSwizzle * nby);
+  if (group < full) {
+    const int rem = lin - group * kSwizzle * nby;
+    by = rem / kSwizzle;
+    bx = group * kSwizzle + rem % kSwizzle;
+  } else {
+    const int gw = nbx - full * kSwizzle;          // width of the last, narrower group
+    const int rem = lin - full * kSwizzle * nby;
+    by = rem / gw;
+    bx = full * kSwizzle + rem % gw;
+  }
+}
+
 // Closure-row sums of the b planes at one end of s (HI: the s = 1 end) for the node
 // column col: for closure row r (plane r, or ns-1-r at the high end) and c = 0..2,
 //   scratch[(e*b + r)*6 + c]     = sum_p D-[r][p] F_s,c(plane p)
@@ -226,8 +248,10 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
   const long long fs = d.fs;
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * TX + tx;
-  const TileAxis ax = tile_axis(blockIdx.x, gridDim.x, d.nq, TX, 4);
-  const TileAxis ay = tile_axis(blockIdx.y, gridDim.y, d.nr, TY, 1);
+  int bx, by;
+  swizzle_tiles(blockIdx.x + gridDim.x * blockIdx.y, gridDim.x, gridDim.y, bx, by);
+  const TileAxis ax = tile_axis(bx, gridDim.x, d.nq, TX, 4);
+  const TileAxis ay = tile_axis(by, gridDim.y, d.nr, TY, 1);
   const int i0 = ax.origin, j0 = ay.origin;
   const int i = i0 + tx, j = j0 + ty;
   // blockIdx.z = chunk + nchunks * member (a batch of independent states)
