@@ -105,6 +105,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x, dist, device="cpu"):
+    """The largest x over all ranks (the job's time is the slowest rank's); x itself when
+    there is no process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def oracle_step_sample(sub, stages=5):
     """Time the FP64 oracle on a sub-block (the top `sub` nodes of the workload's grid, same map,
     medium and spacing): `stages` Runge-Kutta stages.  Returns (node-stages, seconds)."""
@@ -321,10 +332,7 @@ def main():
     kms, kn = L.sbp_kernel_times(h)
     L.sbp_kernel_timing(h, False)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     energy = s.energy()
     bits = s.status()
     ms_per_step = ms / args.steps
