@@ -9,10 +9,12 @@ nodes * 5 * steps / time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
     python bench.py --workload adjoint129_o4 [--adj-steps N]
+    python bench.py --workload surrogate97_o4
 
 The second form times one misfit gradient of the adjoint workload (129 x 129 x 97, order 4,
 FP32 forward with FP64 misfit, 1500 steps, sqrt(N) checkpoints): forward run, checkpoint
-recomputation and adjoint stages, with the adjoint stage kernels' roofline.
+recomputation and adjoint stages, with the adjoint stage kernels' roofline.  The third times the
+surrogate network's training iterations at full size and its largest GEMM against the BF16 peak.
 
 One JSON line on rank 0.  With --gpus N > 1 (torchrun) every rank runs an
 independent replica of the workload on its own GPU ("replicas only": the
@@ -240,6 +242,84 @@ def run_adjoint(args, local):
     print(json.dumps(line), flush=True)
 
 
+def run_surrogate_kernels(args, local):
+    """The surrogate network's kernels at the surrogate workload's full size (3 inputs ->
+    6 x 192 trace sets x 1024 samples, hidden 512, 128 channels): training iterations
+    (forward, backward, Adam; batch 32) and the largest GEMM alone, against the BF16 peak."""
+    import torch
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2011_02600_gb300 import _lib as L
+    from paper_2011_02600_gb300 import surrogate as S
+    from paper_2011_02600_gb300.solver import _stream
+    B = 32
+    net = S.SurrogateNet(n_in=3, hidden=512, C=128, T0=32, n_up=5, n_out=192, seed=0)
+    flops = [0]
+    gemm = S.SurrogateNet._gemm
+
+    def counting(M, N, K, *a, **k):
+        flops[0] += 2 * M * N * K
+        return gemm(M, N, K, *a, **k)
+    net._gemm = counting
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.rand(3, B, generator=g).mul(2).sub(1).to(torch.bfloat16).cuda()
+    m = torch.randn(6, B, generator=g).cuda()
+    tgt = torch.randn(net.n_out, B * net.T, generator=g).cuda()
+
+    def it():
+        y = net.forward(x, m, keep=True)
+        _, dy = S.mse(y, tgt)
+        net.backward(dy)
+        net.adam(1e-4)
+    for _ in range(args.warmup):
+        it()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    flops[0] = 0
+    n_it = max(3, args.steps)
+    ev[0].record(stream)
+    for _ in range(n_it):
+        it()
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    it_ms = ev[0].elapsed_time(ev[1]) / n_it
+    it_flops = flops[0] / n_it
+    # the largest GEMM alone: output layer forward, M = 6 x 192, N = B x 1024, K = 128 x 5
+    M, N, K = net.n_last, B * net.T, net.C * 5
+    A_ = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
+    B_ = torch.randn(K, N, generator=g).to(torch.bfloat16).cuda()
+    C_ = torch.empty(M, N, device="cuda")
+    for _ in range(3):
+        L.sbp_nn_gemm(M, N, K, A_, K, 0, B_, N, 0, C_, N, 0, None, 0, 0.0, _stream())
+    torch.cuda.synchronize()
+    reps = 20
+    ev[0].record(stream)
+    for _ in range(reps):
+        L.sbp_nn_gemm(M, N, K, A_, K, 0, B_, N, 0, C_, N, 0, None, 0, 0.0, _stream())
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    g_ms = ev[0].elapsed_time(ev[1]) / reps
+    tflops = 2.0 * M * N * K / (g_ms / 1e3) / 1e12
+    peaks = _peaks()
+    peak = peaks["bf16_tflops"] if peaks else 1900.0
+    line = {
+        "metric": "surrogate training iterations per second", "value": 1e3 / it_ms, "unit": "it/s",
+        "n_gpus": 1, "steps": n_it, "warmup": args.warmup, "higher_is_better": True, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": "surrogate97_o4 network", "batch": B, "samples": net.T, "outputs": net.n_out,
+                   "hidden": net.hidden, "channels": net.C, "params": net.n_params()},
+        "ms_per_iteration": it_ms, "gemm_tflop_per_iteration": it_flops / 1e12,
+        "gemm_tflops_in_iterations": it_flops / (it_ms / 1e3) / 1e12,
+        "roofline": {"bound": "tensor", "kernel": "gemm_bf16_pipe_kernel (cp.async, ldmatrix, mma.sync m16n8k16)",
+                     "shape": [M, N, K], "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                     "frac": tflops / peak, "avg_launch_ms": g_ms,
+                     "peak_source": "measured (cuBLAS bf16 burst)" if peaks else "fallback"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -250,7 +330,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nodes", default=None,
                     help="nq,nr,ns: a smaller instance of the workload (same generators; for profiling)")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "adjoint129_o4"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "adjoint129_o4", "surrogate97_o4"])
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
     ap.add_argument("--adj-steps", type=int, default=None, help="steps of the adjoint workload (default: its 1500)")
     args = ap.parse_args()
@@ -265,6 +345,12 @@ def main():
         dist.init_process_group(backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
+    if args.workload == "surrogate97_o4":
+        if rank == 0:
+            run_surrogate_kernels(args, local)
         if dist:
             dist.destroy_process_group()
         return

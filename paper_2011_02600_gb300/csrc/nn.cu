@@ -9,6 +9,7 @@
 // tiles are staged in shared memory as A[m][k] and B^T[n][k] and fed to
 // mma.sync.m16n8k16 (BF16 in, FP32 accumulate) through ldmatrix.
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <stdint.h>
 
 #include "sbp.h"
@@ -130,6 +131,177 @@ __global__ void __launch_bounds__(256) gemm_bf16_kernel(int M, int N, int K, con
           float v = acc[mi][nj][h * 2 + q] + bv;
           const long long idx = (long long)gm * ldc + gn;
           if (c_bf16) {
+            if (relu) v = fmaxf(v, 0.f);
+            ((__nv_bfloat16*)C)[idx] = __float2bfloat16(v);
+          } else {
+            if (beta != 0.f) v += beta * ((float*)C)[idx];
+            if (relu) v = fmaxf(v, 0.f);
+            ((float*)C)[idx] = v;
+          }
+        }
+      }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pipelined GEMM for operands whose leading dimensions are multiples of 8 (16-byte rows):
+// each operand tile is copied with 16-byte cp.async vectors along the operand's contiguous
+// dimension into a three-stage shared-memory ring, keeping that orientation: "K-major" tiles
+// [row][k] when k is contiguous (A stored M x K, or B stored N x K) and "MN-major" tiles
+// [k][row] otherwise; ldmatrix (K-major) or ldmatrix.trans (MN-major) produces the same
+// mma.sync fragments either way.  Vectors past M, N or K are zero-filled by the copy.
+// Split-K (blockIdx.z over K ranges) adds partial tiles atomically into an FP32 output that
+// the host zeroed; it is used only without accumulation, ReLU or BF16 output.
+constexpr int PBM = 128, PBN = 128, PBK = 64, PSTAGES = 3;
+constexpr int KM_LD = PBK + 8;  // K-major tile row stride (bf16 elements)
+constexpr int MN_LD = PBM + 8;  // MN-major tile row stride
+constexpr int PTILE = PBM * KM_LD > PBK * MN_LD ? PBM * KM_LD : PBK * MN_LD;
+constexpr int PSMEM = PSTAGES * 2 * PTILE * 2;  // bytes
+
+__device__ __forceinline__ void ldsm_x4_t(unsigned& r0, unsigned& r1, unsigned& r2, unsigned& r3, const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(s_addr(p)));
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s_addr(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Copy the 128 x PBK tile of an operand whose rows (m or n) start at r0 and k at k0 into t.
+//   kmajor: stored [R][ld] with k contiguous -> t[row][k];  else stored [K][ld] -> t[k][row].
+__device__ __forceinline__ void load_tile(__nv_bfloat16* t, const __nv_bfloat16* __restrict__ X, long long ld,
+                                          bool kmajor, int R, int K, int r0, int k0, int tid) {
+  constexpr int VR = PBK / 8;  // 16-byte vectors per K-major row
+#pragma unroll
+  for (int i = 0; i < PBM * PBK / 8 / 256; ++i) {
+    const int v = tid + i * 256;
+    int r, k, valid;
+    const __nv_bfloat16* src;
+    __nv_bfloat16* dst;
+    if (kmajor) {
+      r = v / VR;
+      k = (v % VR) * 8;
+      const int gr = r0 + r, gk = k0 + k;
+      valid = gr < R ? max(0, min(8, K - gk)) : 0;
+      src = valid ? X + (long long)gr * ld + gk : X;
+      dst = t + r * KM_LD + k;
+    } else {
+      k = v >> 4;
+      r = (v & 15) * 8;
+      const int gr = r0 + r, gk = k0 + k;
+      valid = gk < K ? max(0, min(8, R - gr)) : 0;
+      src = valid ? X + (long long)gk * ld + gr : X;
+      dst = t + k * MN_LD + r;
+    }
+    cp_async16(dst, src, valid * 2);
+  }
+}
+
+__global__ void __launch_bounds__(256) gemm_bf16_pipe_kernel(int M, int N, int K, int k_per,
+                                                             const __nv_bfloat16* __restrict__ A, long long lda,
+                                                             int ta, const __nv_bfloat16* __restrict__ B,
+                                                             long long ldb, int tb, void* C, long long ldc,
+                                                             int c_bf16, const float* __restrict__ bias, int relu,
+                                                             float beta) {
+  extern __shared__ __align__(16) unsigned char nn_smem[];
+  __nv_bfloat16* sm = reinterpret_cast<__nv_bfloat16*>(nn_smem);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = (warp >> 2) * 64;  // 2 x 4 warps: 64 (m) x 32 (n) each
+  const int wn = (warp & 3) * 32;
+  const int m0 = blockIdx.y * PBM, n0 = blockIdx.x * PBN;
+  const int kb = blockIdx.z * k_per, ke = min(K, kb + k_per);
+  const bool akm = !ta, bkm = tb;  // K-major tiles
+  const int nt = (ke - kb + PBK - 1) / PBK;
+  float acc[4][4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+  auto As = [&](int st) { return sm + (2 * st) * PTILE; };
+  auto Bs = [&](int st) { return sm + (2 * st + 1) * PTILE; };
+#pragma unroll
+  for (int st = 0; st < PSTAGES - 1; ++st) {
+    if (st < nt) {
+      load_tile(As(st), A, lda, akm, M, ke, m0, kb + st * PBK, tid);
+      load_tile(Bs(st), B, ldb, bkm, N, ke, n0, kb + st * PBK, tid);
+    }
+    cp_async_commit();
+  }
+  for (int t = 0; t < nt; ++t) {
+    cp_async_wait1();
+    __syncthreads();
+    {
+      const int tn = t + PSTAGES - 1;
+      if (tn < nt) {
+        load_tile(As(tn % PSTAGES), A, lda, akm, M, ke, m0, kb + tn * PBK, tid);
+        load_tile(Bs(tn % PSTAGES), B, ldb, bkm, N, ke, n0, kb + tn * PBK, tid);
+      }
+      cp_async_commit();
+    }
+    const __nv_bfloat16* as = As(t % PSTAGES);
+    const __nv_bfloat16* bs = Bs(t % PSTAGES);
+#pragma unroll
+    for (int kk = 0; kk < PBK; kk += 16) {
+      unsigned af[4][4];
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi) {
+        if (akm) {
+          ldsm_x4(af[mi][0], af[mi][1], af[mi][2], af[mi][3],
+                  as + (wm + mi * 16 + (lane & 15)) * KM_LD + kk + (lane >> 4) * 8);
+        } else {
+          const int q = lane >> 3, r = lane & 7;
+          ldsm_x4_t(af[mi][0], af[mi][1], af[mi][2], af[mi][3],
+                    as + (kk + (q >> 1) * 8 + r) * MN_LD + wm + mi * 16 + (q & 1) * 8);
+        }
+      }
+      unsigned bf[4][2];
+#pragma unroll
+      for (int nj = 0; nj < 4; nj += 2) {
+        unsigned r0, r1, r2, r3;
+        if (bkm) {
+          const int r = wn + nj * 8 + (lane & 7) + ((lane >> 4) << 3);
+          const int c = kk + ((lane >> 3) & 1) * 8;
+          ldsm_x4(r0, r1, r2, r3, bs + r * KM_LD + c);
+        } else {
+          const int q = lane >> 3, r = lane & 7;
+          ldsm_x4_t(r0, r1, r2, r3, bs + (kk + (q & 1) * 8 + r) * MN_LD + wn + nj * 8 + (q >> 1) * 8);
+        }
+        bf[nj][0] = r0;
+        bf[nj][1] = r1;
+        bf[nj + 1][0] = r2;
+        bf[nj + 1][1] = r3;
+      }
+#pragma unroll
+      for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+        for (int nj = 0; nj < 4; ++nj) mma_bf16(acc[mi][nj], af[mi], bf[nj][0], bf[nj][1]);
+    }
+  }
+  cp_async_wait1();
+  const bool split = gridDim.z > 1;
+#pragma unroll
+  for (int mi = 0; mi < 4; ++mi)
+#pragma unroll
+    for (int nj = 0; nj < 4; ++nj)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int gm = m0 + wm + mi * 16 + (lane >> 2) + h * 8;
+        if (gm >= M) continue;
+        const float bv = (bias && blockIdx.z == 0) ? bias[gm] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int gn = n0 + wn + nj * 8 + (lane & 3) * 2 + q;
+          if (gn >= N) continue;
+          float v = acc[mi][nj][h * 2 + q] + bv;
+          const long long idx = (long long)gm * ldc + gn;
+          if (split) {
+            atomicAdd((float*)C + idx, v);
+          } else if (c_bf16) {
             if (relu) v = fmaxf(v, 0.f);
             ((__nv_bfloat16*)C)[idx] = __float2bfloat16(v);
           } else {
@@ -334,11 +506,43 @@ int sbp_nn_gemm(int32_t M, int32_t N, int32_t K, const void* A, int64_t lda, int
   if (!A || !B || !C) return nn_bad("null GEMM operand");
   if (lda < (transA ? M : K) || ldb < (transB ? K : N) || ldc < N) return nn_bad("leading dimension too small");
   if (c_bf16 && beta != 0.f) return nn_bad("accumulation (beta) needs an FP32 output");
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+  const cudaStream_t st = (cudaStream_t)stream;
+  const bool aligned = lda % 8 == 0 && ldb % 8 == 0 && (uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0;
+  if (!aligned) {
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    if (grid.y > 65535) return nn_bad("M too large");
+    gemm_bf16_kernel<<<grid, 256, 0, st>>>(M, N, K, (const __nv_bfloat16*)A, lda, transA, (const __nv_bfloat16*)B,
+                                           ldb, transB, C, ldc, c_bf16, bias, relu, beta);
+    return nn_status(cudaGetLastError());
+  }
+  dim3 grid((N + PBN - 1) / PBN, (M + PBM - 1) / PBM, 1);
   if (grid.y > 65535) return nn_bad("M too large");
-  gemm_bf16_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(M, N, K, (const __nv_bfloat16*)A, lda, transA,
-                                                            (const __nv_bfloat16*)B, ldb, transB, C, ldc, c_bf16, bias,
-                                                            relu, beta);
+  // split K when the output tiles alone would leave most SMs idle (FP32 output, plain sum)
+  int k_per = K;
+  const long long tiles = (long long)grid.x * grid.y;
+  if (!c_bf16 && !relu && beta == 0.f && tiles < 2 * 148 && K >= 8 * PBK) {
+    long long splits = (2 * 148 + tiles - 1) / tiles;
+    splits = std::min<long long>(splits, K / (4 * PBK));
+    if (splits > 1) {
+      k_per = (int)(((K + splits - 1) / splits + PBK - 1) / PBK * PBK);
+      grid.z = (unsigned)((K + k_per - 1) / k_per);
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  if (grid.z > 1) {
+    e = ldc == N ? cudaMemsetAsync(C, 0, sizeof(float) * (size_t)M * N, st)
+                 : cudaMemset2DAsync(C, sizeof(float) * (size_t)ldc, 0, sizeof(float) * (size_t)N, (size_t)M, st);
+    if (e != cudaSuccess) return nn_status(e);
+  }
+  static bool attr = false;
+  if (!attr) {
+    e = cudaFuncSetAttribute(gemm_bf16_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PSMEM);
+    if (e != cudaSuccess) return nn_status(e);
+    attr = true;
+  }
+  gemm_bf16_pipe_kernel<<<grid, 256, PSMEM, st>>>(M, N, K, k_per, (const __nv_bfloat16*)A, lda, transA,
+                                                  (const __nv_bfloat16*)B, ldb, transB, C, ldc, c_bf16, bias, relu,
+                                                  beta);
   return nn_status(cudaGetLastError());
 }
 

@@ -31,9 +31,12 @@ def _bf(x):
     return torch.as_tensor(x, dtype=torch.float32).to(torch.bfloat16)
 
 
-@pytest.mark.parametrize("M,N,K", [(37, 61, 19), (128, 256, 320), (300, 70, 33), (192, 1024, 320), (7, 5, 300)])
+@pytest.mark.parametrize("M,N,K", [(37, 61, 19), (128, 256, 320), (300, 70, 33), (192, 1024, 320), (7, 5, 300),
+                                   (136, 200, 96), (40, 64, 1000), (264, 136, 64), (128, 640, 32768)])
 @pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
 def test_gemm_tensor_cores_vs_numpy(M, N, K, ta, tb):
+    """Both GEMM kernels: the scalar-staged one (a leading dimension not a multiple of 8) and
+    the pipelined one (ragged M, N, K edges; split K for the 128 x 640 x 32768 FP32 case)."""
     from paper_2011_02600_gb300 import _lib as L
     from paper_2011_02600_gb300.solver import _stream
     rng = np.random.default_rng(M * 7 + N * 3 + K + ta * 5 + tb)
@@ -48,11 +51,13 @@ def test_gemm_tensor_cores_vs_numpy(M, N, K, ta, tb):
     C = torch.empty(M, N, device="cuda")
     L.sbp_nn_gemm(M, N, K, Ad, lda, ta, Bd, ldb, tb, C, N, 0, bd, 0, 0.0, _stream())
     got = C.cpu().numpy()
-    assert np.abs(got - ref).max() < 1e-5 * np.abs(ref).max()
+    # FP32 accumulation: the rounding error of a K-term sum of random-sign terms grows like sqrt(K)
+    tol = 1e-5 * max(1.0, (K / 1024) ** 0.5)
+    assert np.abs(got - ref).max() < tol * np.abs(ref).max()
     # accumulate (beta = 1) and ReLU
     L.sbp_nn_gemm(M, N, K, Ad, lda, ta, Bd, ldb, tb, C, N, 0, bd, 1, 1.0, _stream())
     want = np.maximum(2 * ref, 0)
-    assert np.abs(C.cpu().numpy() - want).max() < 1e-5 * np.abs(want).max()
+    assert np.abs(C.cpu().numpy() - want).max() < tol * np.abs(want).max()
     # BF16 output with ReLU
     Cb = torch.empty(M, N, device="cuda", dtype=torch.bfloat16)
     L.sbp_nn_gemm(M, N, K, Ad, lda, ta, Bd, ldb, tb, Cb, N, 1, bd, 1, 0.0, _stream())
