@@ -520,12 +520,14 @@ def main():
 
 
 def _kernel_digest():
+    """Digest of the sources the stage kernel is built from (its translation unit, the
+    headers it includes and the host code that encodes its tensor maps and launch shape)."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2011_02600_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in ("kernels_tiled.cu", "common.cuh", "tma.cuh", "adjoint_terms.cuh", "sbp_coeffs.h", "launch.h",
+              "api.cu"):
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 

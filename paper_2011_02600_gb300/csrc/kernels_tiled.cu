@@ -23,7 +23,11 @@
 //     forms the closure-row sums of every closure plane together, into a scratch
 //     buffer that the same thread reads back when it gets to the plane.
 //   * Nodes on a face add the face's penalty (free surface or characteristic SAT).
-// The stage update (2N-storage Runge-Kutta) is fused in the epilogue.
+// The stage update (2N-storage Runge-Kutta) is fused in the epilogue.  Tiles of one s
+// chunk launch in groups of tile columns (swizzle_tiles) so that tiles sharing halos run
+// together and read them from L2.  The same kernel, templated on a pass kind, also runs
+// the two stencil passes of the discrete adjoint (L^T on yhat, the material gradient on
+// U_k) with their own epilogues.
 #include "adjoint_terms.cuh"
 #include "common.cuh"
 #include "launch.h"
