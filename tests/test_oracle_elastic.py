@@ -358,3 +358,63 @@ def test_pointwise_oracle_matches_whole_array(order):
     for node in [(0, 0, 0), (18, 16, 19), (5, 7, 19), (9, 8, 10), (3, 0, 12), (18, 3, 0)]:
         got = po.rhs_at(node, fs)
         assert np.abs(got - R[:, node[2], node[1], node[0]]).max() < 1e-13 * np.abs(R).max()
+
+
+@pytest.mark.parametrize("order,sizes", [(2, (17, 33, 65)), (4, (17, 33, 65)), (6, (33, 65))])
+def test_free_stream_residual_converges_at_design_order(order, sizes):
+    """A constant state has zero continuous right-hand side (the metric identity
+    sum_xi d/dxi (J grad xi) = 0, Sec. 2.2).  The discrete residual (metrics by D_c, flux by
+    D-, velocity by D+; no penalties) is not zero on a curved grid, but in the interior it
+    falls at the interior order of the operators (free-stream preservation is not enforced)."""
+    errs = []
+    for n in sizes:
+        nodes = (n, n, n)
+        x, y, z = node_coordinates(make_map("curvy", (1.0, 1.2, 0.9)), nodes)
+        J, a = metrics(x, y, z, order)
+        sch = Scheme(order, nodes)
+        Q = np.zeros((9,) + x.shape)
+        Q[:3] = np.array([0.3, -0.2, 0.5])[:, None, None, None]
+        Q[3:] = np.array([1.0, 0.7, -0.4, 0.3, 0.2, -0.5])[:, None, None, None]
+        ones = np.ones_like(x)
+        rv, e = rhs_raw(Q, sch, a, (ones, ones, ones), [("free",)] * 6, with_sat=False)
+        c = (slice(None),) + (slice(n // 4, 3 * n // 4 + 1),) * 3
+        errs.append(max(np.abs(np.array(rv)[c]).max(), np.abs(np.array(e)[c]).max()))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert min(rates) > order - 0.3, rates
+
+
+@pytest.mark.parametrize("geometry,order", [("identity", 4), ("curvy", 4), ("curvy", 6)])
+def test_cfl_half_step_lies_inside_the_runge_kutta_stability_limit(geometry, order):
+    """dt rho(L) for the dt rule at CFL 0.5 (dt = CFL h_min / c_p,max): the spectral radius of
+    the full operator (penalties included) by power iteration in the discrete energy norm,
+    in which L is skew-adjoint plus a dissipative part, must stay below 3.34, where the
+    scheme's stability region (|R(iy)| <= 1, R the stability polynomial) leaves the
+    imaginary axis.  Grid spacing and medium of the 33^3 cube workload."""
+    from workloads.timestep import stable_dt
+    n, h = 20, 1000.0 / 32
+    nodes = (n, n, n)
+    X = node_coordinates(make_map(geometry, (h * (n - 1),) * 3), nodes)
+    mat = make_medium("homogeneous")(*X)
+    J, a = metrics(*X, order)
+    sch = Scheme(order, nodes)
+    dt = stable_dt(*X, *mat, 0.5)
+    bc = [("char", 0.0)] * 5 + [("free",)]
+    rng = np.random.default_rng(0)
+    Q = rng.normal(size=(9,) + X[0].shape)
+    Q[3:] *= 1e7
+    Q /= math.sqrt(energy(Q, sch, J, mat))
+    lam = 0.0
+    for _ in range(250):
+        Y = rhs(Q, sch, J, a, mat, bc)
+        lam = math.sqrt(energy(Y, sch, J, mat))
+        Q = Y / lam
+    assert 1.0 < lam * dt < 3.34, lam * dt
+    # the limit itself, from the scheme's Butcher tableau: R(z) = 1 + z b^T (I - z A)^-1 1 has
+    # |R(iy)| <= 1 up to y = 3.34 and exceeds 1 beyond
+    At, bt, _ = rk.butcher_tableau()
+    At = np.array(At, dtype=float)
+    bt = np.array(bt, dtype=float)
+
+    def R(z):
+        return 1.0 + z * bt @ np.linalg.solve(np.eye(len(bt)) - z * At, np.ones(len(bt)))
+    assert abs(R(3.30j)) <= 1.0 and abs(R(3.40j)) > 1.0
