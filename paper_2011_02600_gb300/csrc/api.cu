@@ -14,6 +14,8 @@
 #include "launch.h"
 #include "sbp.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -116,6 +118,12 @@ struct SbpGrid {
 };
 
 namespace {
+
+// NVTX range around a C-ABI call (shows in nsys/ncu timelines; free when no tool listens).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 // Elements of the tiled kernel's s-closure scratch per state: 2 ends x b rows x 6 planes.
 long long sclose_elems(const SbpGrid* g) { return 2LL * closure_b(g->desc.order) * 6 * g->dims.plane; }
@@ -539,6 +547,7 @@ int sbp_rhs(SbpGrid* g, const void* q, void* out, void* stream) {
 }
 
 int sbp_rk_stage(SbpGrid* g, int32_t stage, double dt, void* stream) {
+  NvtxRange nvtx_range("sbp_rk_stage");
   if (int rc = check_ready(g)) return rc;
   if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
   if (stage < 0 || stage > 4) return fail(SBP_ERR_ARG, "stage must be 0..4");
@@ -548,6 +557,7 @@ int sbp_rk_stage(SbpGrid* g, int32_t stage, double dt, void* stream) {
 }
 
 int sbp_step_n(SbpGrid* g, int32_t n, double dt, void* stream) {
+  NvtxRange nvtx_range("sbp_step_n");
   if (int rc = check_ready(g)) return rc;
   if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
   if (n < 0) return fail(SBP_ERR_ARG, "negative step count");

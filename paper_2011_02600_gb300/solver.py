@@ -132,8 +132,47 @@ class ElasticSolver:
     def rk_stage(self, k, dt):
         L.sbp_rk_stage(self.h, k, dt, _stream())
 
-    def step(self, n, dt):
-        L.sbp_step_n(self.h, n, dt, _stream())
+    def step(self, n, dt, check_every=0):
+        """n Runge-Kutta steps of size dt.  With check_every = m > 0 the discrete energy is
+        formed every m steps and a non-finite state raises SbpError (SBP_ERR_NONFINITE, code 4)
+        before further steps run (the check covers the first batch member)."""
+        if check_every <= 0:
+            L.sbp_step_n(self.h, n, dt, _stream())
+            return
+        done = 0
+        while done < n:
+            k = min(int(check_every), n - done)
+            L.sbp_step_n(self.h, k, dt, _stream())
+            done += k
+            self.energy()
+
+    def save_state(self, path):
+        """Write the state, the Runge-Kutta register, the time and the step counter to path
+        (between steps; see checkpoint.py for the format)."""
+        from . import checkpoint
+        t, step = L.sbp_get_time(self.h)
+        header = dict(nodes=list(self.nodes), order=self.order, precision=self.precision, batch=self.batch,
+                      ldq=self.ldq, fs=self.fs, time=t, step=step)
+        data = checkpoint.pack(header, [self.qbuf[self.current].cpu().numpy(), self.dq.cpu().numpy()])
+        with open(path, "wb") as f:
+            f.write(data)
+
+    def load_state(self, path):
+        """Resume from a file written by save_state on a grid of the same shape, order,
+        precision, batch and layout (checkpoint.CheckpointError otherwise)."""
+        from . import checkpoint
+        with open(path, "rb") as f:
+            header, (q, dq) = checkpoint.unpack(f.read())
+        want = dict(nodes=list(self.nodes), order=self.order, precision=self.precision, batch=self.batch,
+                    ldq=self.ldq, fs=self.fs)
+        for k, v in want.items():
+            if header.get(k) != v:
+                raise checkpoint.CheckpointError(f"checkpoint {k} {header.get(k)} does not match the grid's {v}")
+        if q.size != self.qbuf[0].numel() or dq.size != self.dq.numel():
+            raise checkpoint.CheckpointError("checkpoint array sizes do not match the grid")
+        self.qbuf[self.current].copy_(torch.from_numpy(q))
+        self.dq.copy_(torch.from_numpy(dq))
+        L.sbp_set_time(self.h, float(header["time"]), int(header["step"]))
 
     def energy(self):
         return L.sbp_energy(self.h, _stream())

@@ -85,3 +85,37 @@ def test_invalid_material_is_reported():
     with pytest.raises(L.SbpError) as ex:
         _grid(nodes, mat=mat)
     assert ex.value.code == 6
+
+
+def test_checkpoint_resume_is_bit_identical_fp64(tmp_path):
+    """save_state between steps and load_state into a fresh grid continue the run bit for bit
+    (FP64), time and step counter included; a grid of another shape is refused."""
+    from paper_2011_02600_gb300.checkpoint import CheckpointError
+    a = _grid(precision=64)
+    b = _grid(precision=64)
+    dt = 1e-4
+    a.step(12, dt)
+    b.step(5, dt)
+    path = str(tmp_path / "run.ckpt")
+    b.save_state(path)
+    c = _grid(precision=64)
+    c.set_state(torch.zeros_like(c.state()))
+    c.load_state(path)
+    c.step(7, dt)
+    assert torch.equal(a.state(), c.state())
+    assert torch.equal(a.view(a.dq, 9), c.view(c.dq, 9))
+    from paper_2011_02600_gb300 import _lib as L
+    assert L.sbp_get_time(a.h) == L.sbp_get_time(c.h)
+    other = _grid(nodes=(21, 18, 17), precision=64)
+    with pytest.raises(CheckpointError):
+        other.load_state(path)
+
+
+def test_periodic_check_stops_a_nonfinite_run():
+    from paper_2011_02600_gb300 import _lib as L
+    s = _grid()
+    s.step(3, 1e-4, check_every=2)           # finite: passes
+    s.state()[2, 4, 5, 6] = float("inf")
+    with pytest.raises(L.SbpError) as ex:
+        s.step(10, 1e-4, check_every=4)
+    assert ex.value.code == 4
