@@ -1,8 +1,8 @@
 // General stage kernel: one thread per node of a list of boxes; every row of
-// D+ and D- (interior stencil or closure), the penalties of every face the
-// node lies on, and the fused Runge-Kutta stage.  It serves the boundary
-// slabs (closure rows, edges, corners, penalties) and any grid too small for
-// the tiled interior kernel.
+// D+ and D- (interior stencil or closure) read from global memory, the penalties
+// of every face the node lies on, and the fused Runge-Kutta stage.  It computes
+// the same scheme as the tiled kernel and serves to cross-check it
+// (sbp_set_kernel_path(1)).
 #include "common.cuh"
 #include "launch.h"
 
