@@ -534,12 +534,9 @@ int sbp_nn_gemm(int32_t M, int32_t N, int32_t K, const void* A, int64_t lda, int
                  : cudaMemset2DAsync(C, sizeof(float) * (size_t)ldc, 0, sizeof(float) * (size_t)N, (size_t)M, st);
     if (e != cudaSuccess) return nn_status(e);
   }
-  static bool attr = false;
-  if (!attr) {
-    e = cudaFuncSetAttribute(gemm_bf16_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PSMEM);
-    if (e != cudaSuccess) return nn_status(e);
-    attr = true;
-  }
+  // per launch: the attribute belongs to the current device
+  e = cudaFuncSetAttribute(gemm_bf16_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PSMEM);
+  if (e != cudaSuccess) return nn_status(e);
   gemm_bf16_pipe_kernel<<<grid, 256, PSMEM, st>>>(M, N, K, k_per, (const __nv_bfloat16*)A, lda, transA,
                                                   (const __nv_bfloat16*)B, ldb, transB, C, ldc, c_bf16, bias, relu,
                                                   beta);
