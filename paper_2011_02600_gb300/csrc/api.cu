@@ -692,19 +692,23 @@ int sbp_set_sources(SbpGrid* g, int32_t n, const SbpSource* srcs, const double* 
     int start[3];
     double phi[3][8];
     for (int a = 0; a < 3; ++a) delta_1d(src->ref[a], N[a], mo, &start[a], phi[a]);
+    double Jrow[8];
     for (int kk = 0, c = 0; kk < n1; ++kk)
-      for (int jj = 0; jj < n1; ++jj)
+      for (int jj = 0; jj < n1; ++jj) {
+        // the Jacobian along this q row of the source's stencil box, one copy per row
+        const long long row = (long long)(start[2] + kk) * g->dims.plane + (long long)(start[1] + jj) * g->dims.ldq +
+                              start[0];
+        if (e == cudaSuccess) e = cudaMemcpy(Jrow, jmet + row, sizeof(double) * n1, cudaMemcpyDeviceToHost);
         for (int ii = 0; ii < n1; ++ii, ++c) {
-          const long long node = (long long)(start[2] + kk) * g->dims.plane + (long long)(start[1] + jj) * g->dims.ldq +
-                                 start[0] + ii;
-          double J = 0.0;
-          if (e == cudaSuccess) e = cudaMemcpy(&J, jmet + node, sizeof(double), cudaMemcpyDeviceToHost);
+          const long long node = row + ii;
+          const double J = Jrow[ii];
           const double H = wgt(0, start[0] + ii) * wgt(1, start[1] + jj) * wgt(2, start[2] + kk);
           const double delta = phi[0][ii] * phi[1][jj] * phi[2][kk] / (J * H);
           const size_t idx = (size_t)m * per + c;
           off[idx] = (long long)m * 9 * g->dims.fs + node;
           for (int q = 0; q < 6; ++q) w[idx * 6 + q] = -src->moment[q] * delta;
         }
+      }
   }
   if (e != cudaSuccess) return cuda_fail(e, "source Jacobian readback");
   cudaFree(g->src_off);
