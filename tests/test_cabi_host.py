@@ -95,3 +95,17 @@ def test_generated_coefficients_match_oracle():
         assert alpha == {j: Fraction(a) for j, a in op.interior_stencil(order).items()}
     text = open(os.path.join(ROOT, "paper_2011_02600_gb300", "csrc", "sbp_coeffs.h")).read()
     assert text == opgen.render()
+
+
+def test_network_entry_points_reject_bad_arguments(lib):
+    """The layer kernels' entry points check sizes, leading dimensions and pointers on the host
+    (SBP_ERR_ARG) before any launch; fake aligned addresses suffice since nothing runs."""
+    a, b, c = 4096, 8192, 16384
+    _expect(1, L.sbp_nn_gemm, 0, 8, 8, a, 8, 0, b, 8, 0, c, 8, 0, None, 0, 0.0, None)     # M = 0
+    _expect(1, L.sbp_nn_gemm, 8, 8, 8, None, 8, 0, b, 8, 0, c, 8, 0, None, 0, 0.0, None)  # null A
+    _expect(1, L.sbp_nn_gemm, 8, 8, 16, a, 8, 0, b, 8, 0, c, 8, 0, None, 0, 0.0, None)   # lda < K
+    _expect(1, L.sbp_nn_gemm, 8, 16, 8, a, 8, 0, b, 8, 0, c, 16, 0, None, 0, 0.0, None)  # ldb < N
+    _expect(1, L.sbp_nn_gemm, 8, 8, 8, a, 8, 0, b, 8, 0, c, 8, 1, None, 0, 1.0, None)    # beta with BF16 C
+    _expect(1, L.sbp_nn_im2col, a, b, 0, 2, 8, 5, 2, None)
+    _expect(1, L.sbp_nn_moment_combine, None, None, None, None, None, 4, 2, 8, 0, None)
+    _expect(1, L.sbp_nn_moment_combine, a, b, None, None, None, 4, 2, 8, 0, None)        # no output
