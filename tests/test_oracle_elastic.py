@@ -418,3 +418,43 @@ def test_cfl_half_step_lies_inside_the_runge_kutta_stability_limit(geometry, ord
     def R(z):
         return 1.0 + z * bt @ np.linalg.solve(np.eye(len(bt)) - z * At, np.ones(len(bt)))
     assert abs(R(3.30j)) <= 1.0 and abs(R(3.40j)) > 1.0
+
+
+def test_receivers_record_the_plane_wave_at_their_nodes_after_each_step():
+    """The oracle's receivers: traces[n][r][c] is velocity component c at node (i, j, k) of
+    receiver r after step n + 1.  On an exact plane wave (P wave along (1, 2, 2)/3, so the
+    field varies along every axis) interior receivers must reproduce the exact solution at
+    their own node and time to the discretization error; a transposed node index or a
+    one-step shift in time misses it by far more."""
+    from oracle.solver import OracleSolver
+    order, n = 4, 24
+    nodes = (n + 1, n + 1, n + 1)
+    X = node_coordinates(make_map("curvy", (1.0, 1.0, 1.0), eps=0.05), nodes)
+    rho, lam, mu = 1.0, 2.0, 1.0
+    mat = tuple(np.full(X[0].shape, v) for v in (rho, lam, mu))
+    dvec = np.array([1.0, 2.0, 2.0]) / 3.0
+    wl = 0.8
+
+    def exact(t):
+        v, s = _plane_wave("P", X, t, rho, lam, mu, dvec, dvec, wl)
+        return np.stack(v + s)
+    orc = OracleSolver(order, *X, mat, [("char", 0.0)] * 6)
+    orc.Q[:] = exact(0.0)
+    rec = [(8, 12, 15), (15, 9, 11), (12, 16, 8)]
+    orc.receivers = rec
+    c = math.sqrt((lam + 2 * mu) / rho)
+    dt = 0.25 / n / c
+    nsteps = 6
+    orc.step(dt, nsteps)
+    got = np.array(orc.traces)                          # [step][receiver][component]
+    want = np.array([[[exact((s + 1) * dt)[cc][k, j, i] for cc in range(3)] for (i, j, k) in rec]
+                     for s in range(nsteps)])
+    scale = np.abs(want).max()
+    err = np.abs(got - want).max() / scale
+    assert err < 5e-3, err
+    shifted = np.array([[[exact(s * dt)[cc][k, j, i] for cc in range(3)] for (i, j, k) in rec]
+                        for s in range(nsteps)])
+    transposed = np.array([[[exact((s + 1) * dt)[cc][i, j, k] for cc in range(3)] for (i, j, k) in rec]
+                           for s in range(nsteps)])
+    assert np.abs(got - shifted).max() / scale > 10 * err
+    assert np.abs(got - transposed).max() / scale > 10 * err
