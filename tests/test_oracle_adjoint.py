@@ -5,6 +5,7 @@ from oracle.adjoint import assemble_operator, complex_step, misfit
 from oracle.elastic import Scheme
 from oracle.metrics import metrics
 from workloads.geometry import make_map, node_coordinates
+from workloads.media import make_medium
 
 
 def _setup(order=2, nodes=(7, 6, 6)):
@@ -61,3 +62,27 @@ def test_assembled_operator_is_skew_in_the_energy_inner_product():
         Pinv[np.ix_(idx, idx)] = S
     A = Pinv @ Lm
     assert np.abs(A + A.T).max() < 1e-11 * np.abs(A).max()
+
+
+def test_misfit_quadrature_closed_forms():
+    """Phi = sum_n 1/2 dt sum_r |v(x_r, t_{n+1}) - d_{r,n}|^2: with a zero state (no source)
+    it is 1/2 dt times the data's squared sum; with the solver's own traces as data it is 0."""
+    from oracle.solver import OracleSolver
+    from workloads.fields import random_state
+    nodes, order = (9, 8, 7), 2
+    X = node_coordinates(make_map("curvy", (1000.0, 1100.0, 900.0)), nodes)
+    mat = make_medium("smooth_gradient", Lz=900.0)(*X)
+    bc = [("char", 0.0)] * 5 + [("free",)]
+    rec = [(2, 3, 6), (5, 4, 3)]
+    dt, nsteps = 1e-3, 5
+    rng = np.random.default_rng(3)
+    data = rng.normal(size=(nsteps, len(rec), 3))
+    phi0 = misfit(order, X, mat, bc, rec, data, dt, nsteps)
+    assert abs(phi0 - 0.5 * dt * float(np.sum(data ** 2))) < 1e-14 * phi0
+    Q0 = random_state(nodes, 5, 1.0, 1.0e6)
+    orc = OracleSolver(order, *X, mat, bc)
+    orc.Q[:] = Q0
+    orc.receivers = rec
+    orc.step(dt, nsteps)
+    own = np.array(orc.traces)
+    assert misfit(order, X, mat, bc, rec, own, dt, nsteps, Q0=Q0) < 1e-24 * float(np.sum(own ** 2))
