@@ -208,8 +208,9 @@ int sbp_adjoint_stage(SbpGrid* grid, int32_t stage, double dt, const void* u_sta
 /* Receiver misfit of the state q (9 fields): for each receiver r and velocity
  * component c, diff = v_c - data[3r + c] (data: FP64 device, 3 per receiver);
  * acc[3r + c] += weight diff^2 / 2 (FP64 device, may be NULL) and, if ubar is
- * not NULL, ubar_c += weight diff at the receiver node (the adjoint source).
- * Needs sbp_set_receivers. */
+ * not NULL, ubar_c += weight diff at the receiver node (the adjoint source;
+ * receivers that share a node add their sources atomically, so the order of
+ * those additions is unspecified).  Needs sbp_set_receivers. */
 int sbp_misfit(SbpGrid* grid, const void* q, const double* data, double weight, double* acc, void* ubar,
                void* stream);
 

@@ -158,8 +158,6 @@ sbp::StageArgs<T> make_args(const SbpGrid* g, const void* q, void* qout, int mod
   A.sclose = (T*)g->sclose;
   A.sc_bstride = sclose_elems(g);
   const int N[3] = {g->desc.nq, g->desc.nr, g->desc.ns};
-  const int b = closure_b(g->desc.order);
-  (void)b;
   for (int f = 0; f < 6; ++f) {
     A.bc_kind[f] = g->desc.bc_kind[f];
     A.bc_gamma[f] = (T)g->desc.bc_gamma[f];
@@ -206,7 +204,7 @@ struct TimedLaunch {
   }
 };
 
-// Tensor maps for the tiled kernel's tile loads (see kernels_interior.cu): the state
+// Tensor maps for the tiled kernel's tile loads (kernels_tiled.cu): the state
 // (box 40 x 16 x 1 x 9), the metric vectors a_q (40 x 8 x 1 x 3), a_r (32 x 16 x 1 x 3),
 // a_s (32 x 8 x 1 x 3) and the coefficients (32 x 8 x 1 x 3).  Out-of-range elements
 // are filled with zeros.
@@ -740,11 +738,8 @@ int sbp_set_batch(SbpGrid* g, int32_t nb) {
 
 int sbp_set_receivers(SbpGrid* g, int32_t n, const int32_t* ijk, void* traces, int32_t n_t) {
   if (int rc = check_ready(g)) return rc;
-  cudaFree(g->rec_off);
-  g->rec_off = nullptr;
-  g->rec_n = 0;
-  if (n == 0) return SBP_OK;
-  if (n < 0 || !ijk || !traces || n_t <= 0) return fail(SBP_ERR_ARG, "bad receiver arguments");
+  if (n < 0 || (n > 0 && (!ijk || !traces || n_t <= 0))) return fail(SBP_ERR_ARG, "bad receiver arguments");
+  // validate every receiver before the current ones are dropped
   std::vector<int32_t> off(n);
   for (int r = 0; r < n; ++r) {
     const int i = ijk[3 * r], j = ijk[3 * r + 1], k = ijk[3 * r + 2];
@@ -752,6 +747,10 @@ int sbp_set_receivers(SbpGrid* g, int32_t n, const int32_t* ijk, void* traces, i
       return fail(SBP_ERR_ARG, "receiver %d outside the grid", r);
     off[r] = (int32_t)((long long)k * g->dims.plane + (long long)j * g->dims.ldq + i);
   }
+  cudaFree(g->rec_off);
+  g->rec_off = nullptr;
+  g->rec_n = 0;
+  if (n == 0) return SBP_OK;
   cudaError_t e = cudaMalloc(&g->rec_off, sizeof(int32_t) * n);
   if (e == cudaSuccess) e = cudaMemcpy(g->rec_off, off.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_fail(e, "receiver buffers");

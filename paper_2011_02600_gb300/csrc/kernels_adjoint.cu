@@ -171,7 +171,8 @@ cudaError_t launch_adjoint(const AdjArgs<T>& A, int order, cudaStream_t st) {
 }
 
 // Receivers: misfit 1/2 w (v - d)^2 accumulated per receiver component in FP64, and the
-// adjoint source w (v - d) added to ubar (if given) at the receiver node.
+// adjoint source w (v - d) added to ubar (if given) at the receiver node.  The add is atomic:
+// receivers that share a node each contribute their own source.
 template <typename T>
 __global__ void misfit_kernel(const T* __restrict__ q, Dims d, const int32_t* __restrict__ off, int n,
                               const double* __restrict__ data, double w, double* __restrict__ acc, T* ubar) {
@@ -181,7 +182,7 @@ __global__ void misfit_kernel(const T* __restrict__ q, Dims d, const int32_t* __
   const long long idx = (long long)c * d.fs + off[r];
   const double diff = (double)q[idx] - data[t];
   if (acc) acc[t] += 0.5 * w * diff * diff;
-  if (ubar) ubar[idx] = (T)((double)ubar[idx] + w * diff);
+  if (ubar) atomicAdd(&ubar[idx], (T)(w * diff));
 }
 
 template <typename T>
