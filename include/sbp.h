@@ -162,7 +162,7 @@ int sbp_kernel_times(SbpGrid* grid, double* ms, int64_t* launches);
 int sbp_current(const SbpGrid* grid, int32_t* which);
 
 /* Set / get the simulation time and the step counter (receivers record at
- * column step). */
+ * column step).  SBP_ERR_ARG for a negative step or a non-finite time. */
 int sbp_set_time(SbpGrid* grid, double t, int64_t step);
 int sbp_get_time(const SbpGrid* grid, double* t, int64_t* step);
 

@@ -623,6 +623,8 @@ int sbp_current(const SbpGrid* g, int32_t* which) {
 
 int sbp_set_time(SbpGrid* g, double t, int64_t step) {
   if (!g) return fail(SBP_ERR_ARG, "null grid");
+  if (step < 0) return fail(SBP_ERR_ARG, "negative step counter");
+  if (!isfinite(t)) return fail(SBP_ERR_ARG, "time must be finite");
   g->t = t;
   g->step = step;
   return SBP_OK;

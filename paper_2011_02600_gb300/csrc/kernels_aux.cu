@@ -259,7 +259,7 @@ __global__ void receivers_kernel(const T* __restrict__ q, Dims d, const int32_t*
 template <typename T>
 cudaError_t launch_receivers(const T* q, const Dims& d, const int32_t* off, int n, int nb, long long bstride,
                              T* traces, int n_t, long long step, cudaStream_t st) {
-  if (n == 0 || step >= n_t) return cudaSuccess;
+  if (n == 0 || step < 0 || step >= n_t) return cudaSuccess;
   receivers_kernel<T><<<(nb * n * 3 + 127) / 128, 128, 0, st>>>(q, d, off, n, nb, bstride, traces, n_t, step);
   return cudaGetLastError();
 }

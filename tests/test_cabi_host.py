@@ -69,6 +69,10 @@ def test_calls_out_of_sequence_are_rejected(lib):
     _expect(1, L.sbp_bind, h, 0, 256, 512, 768, 1024)          # null
     _expect(1, L.sbp_bind, h, 256, 256, 512, 768, 1024)        # aliasing
     _expect(1, L.sbp_bind, h, 260, 512, 768, 1024, 1280)       # misaligned
+    _expect(1, L.sbp_set_time, h, 0.0, -1)                       # receivers would write before column 0
+    _expect(1, L.sbp_set_time, h, float("nan"), 0)
+    L.sbp_set_time(h, 2.5, 7)
+    assert L.sbp_get_time(h) == (2.5, 7)
     L.sbp_destroy(h)
 
 
