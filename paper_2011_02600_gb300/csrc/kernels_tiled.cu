@@ -624,7 +624,7 @@ cudaError_t launch_tiled_order(const StageArgs<T>& A, const TmaSet& tm, cudaStre
   // (at least 16 planes each), the count that minimises waves x (chunk + queue warm-up)
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    sms = 148;
+    sms = 152;  // GB300
   const long long tiles = (long long)((ni + TX - 1) / TX) * ((nj + TY - 1) / TY) * A.nb;
   const long long slots = (long long)sms * tiled_min_blocks<T>();
   int nchunks = (nk + 95) / 96;

@@ -493,6 +493,14 @@ int nn_bad(const char* msg) {
   sbp::set_last_error(msg);
   return SBP_ERR_ARG;
 }
+// SM count of the current device (152 on GB300, also the value taken if the query fails).
+int device_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      n <= 0)
+    return 152;
+  return n;
+}
 }  // namespace
 
 using namespace sbp_nn;
@@ -517,11 +525,13 @@ int sbp_nn_gemm(int32_t M, int32_t N, int32_t K, const void* A, int64_t lda, int
   }
   dim3 grid((N + PBN - 1) / PBN, (M + PBM - 1) / PBM, 1);
   if (grid.y > 65535) return nn_bad("M too large");
-  // split K when the output tiles alone would leave most SMs idle (FP32 output, plain sum)
+  // split K when the output tiles alone would leave most SMs idle (FP32 output, plain sum);
+  // the target is two resident CTAs per SM
   int k_per = K;
   const long long tiles = (long long)grid.x * grid.y;
-  if (!c_bf16 && !relu && beta == 0.f && tiles < 2 * 148 && K >= 8 * PBK) {
-    long long splits = (2 * 148 + tiles - 1) / tiles;
+  const long long slots = 2LL * device_sms();
+  if (!c_bf16 && !relu && beta == 0.f && tiles < slots && K >= 8 * PBK) {
+    long long splits = (slots + tiles - 1) / tiles;
     splits = std::min<long long>(splits, K / (4 * PBK));
     if (splits > 1) {
       k_per = (int)(((K + splits - 1) / splits + PBK - 1) / PBK * PBK);
