@@ -195,7 +195,8 @@ def run_adjoint(args, local):
     s = p.s
     nq, nr, ns = cfg.nodes
     nodes = nq * nr * ns
-    p.forward()                       # warm-up
+    p.forward()                       # warm-up: one untimed forward run and gradient
+    p.gradient()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(local)
@@ -222,10 +223,12 @@ def run_adjoint(args, local):
     value = nodes * 5 * nsteps / ((t_fwd + t_grad) / 1e3) / 1e6
     line = {
         "metric": "adjoint gradient throughput", "value": value, "unit": "Mnode-stage/s",
-        "n_gpus": 1, "steps": nsteps, "warmup": 1, "higher_is_better": True, "dtype": "f32",
+        "n_gpus": 1, "steps": nsteps, "warmup": nsteps, "ms_per_step": (t_fwd + t_grad) / nsteps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "adjoint129_o4", "nodes": list(cfg.nodes), "order": cfg.order,
                    "checkpoint_every": p.C, "receivers": len(p.receivers),
+                   "warmup": "one untimed forward run and gradient over the same steps",
                    "what": "node-stages of the forward problem per second of forward run + gradient"},
         "forward_ms": t_fwd, "gradient_ms": t_grad, "misfit": phi,
         "gradient_norm": float(g.double().norm()),
@@ -279,11 +282,15 @@ def run_surrogate_kernels(args, local):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     flops[0] = 0
     n_it = max(3, args.steps)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
     ev[0].record(stream)
     for _ in range(n_it):
         it()
     ev[1].record(stream)
     torch.cuda.synchronize()
+    clk = clocks.stop()
     it_ms = ev[0].elapsed_time(ev[1]) / n_it
     it_flops = flops[0] / n_it
     # the largest GEMM alone: output layer forward, M = 6 x 192, N = B x 1024, K = 128 x 5
@@ -306,7 +313,8 @@ def run_surrogate_kernels(args, local):
     peak = peaks["bf16_tflops"] if peaks else 1900.0
     line = {
         "metric": "surrogate training iterations per second", "value": 1e3 / it_ms, "unit": "it/s",
-        "n_gpus": 1, "steps": n_it, "warmup": args.warmup, "higher_is_better": True, "dtype": "bf16",
+        "n_gpus": 1, "steps": n_it, "warmup": args.warmup, "ms_per_step": it_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "clocks": clk,
         "data": "synthetic",
         "config": {"workload": "surrogate97_o4 network", "batch": B, "samples": net.T, "outputs": net.n_out,
                    "hidden": net.hidden, "channels": net.C, "params": net.n_params()},
