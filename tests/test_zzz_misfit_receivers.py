@@ -83,3 +83,22 @@ def test_rejected_receiver_list_keeps_the_current_receivers():
     torch.cuda.synchronize()
     _, acc_want = _expected(s.view(q, 9).double().cpu().numpy(), data.cpu().numpy(), 1.0)
     assert np.allclose(acc.cpu().numpy(), acc_want, rtol=1e-12, atol=0.0)
+
+
+def test_zero_steps_and_a_zero_state():
+    """Degenerate calls: zero steps leave state, time and step counter as they are; the zero
+    state is a fixed point of the scheme without a source (L is linear)."""
+    from paper_2011_02600_gb300 import _lib as L
+    s, _, _ = _case(64)
+    Q = random_state(NODES, 8, 1.0, 1.0e6)
+    s.set_state(torch.from_numpy(Q))
+    s.set_time(0.5, 3)
+    s.step(0, 1.0e-4)
+    torch.cuda.synchronize()
+    assert np.array_equal(s.state().cpu().numpy(), Q)
+    assert L.sbp_get_time(s.h) == (0.5, 3)
+    s.set_state(torch.zeros((9,) + Q.shape[1:], dtype=torch.float64))
+    s.step(2, 1.0e-4)
+    torch.cuda.synchronize()
+    assert not s.state().cpu().numpy().any()
+    assert L.sbp_get_time(s.h)[1] == 5
