@@ -340,21 +340,19 @@ def test_plane_wave_convergence_with_free_surfaces(order, kind, lo):
     assert rate > lo, (e1, e2, rate)
 
 
-def _interior_truncation(order, n, kind, mapname):
+def _interior_truncation(order, n, kind, mapname, ext=1.0, medium=(1.0, 2.0, 1.0), wl=0.8):
     """max |dQ/dt_h(Q) - dQ/dt| / max |dQ/dt| for the exact plane wave of _plane_wave at t = 0,
     over the nodes at least b + max(r, q) from every face: there every row is the interior
     stencil of Table 1 applied to metrics formed by interior rows (the closure rows, their
     stencil reach and the penalised face nodes are left out)."""
     nodes = (n + 1, n + 1, n + 1)
-    fmap = make_map("curvy", (1.0, 1.0, 1.0), eps=0.05) if mapname == "curvy" else \
-        make_map("identity", (1.0, 1.0, 1.0))
+    fmap = make_map("curvy", (ext,) * 3, eps=0.05) if mapname == "curvy" else make_map("identity", (ext,) * 3)
     X = node_coordinates(fmap, nodes)
     J, a = metrics(*X, order)
-    rho, lam, mu = 1.0, 2.0, 1.0
+    rho, lam, mu = medium
     mat = tuple(np.full(J.shape, v) for v in (rho, lam, mu))
     dvec = np.array([1.0, 2.0, 2.0]) / 3.0
     pol = dvec if kind == "P" else np.array([2.0, -1.0, 0.0]) / math.sqrt(5.0)
-    wl = 0.8
     v, s = _plane_wave(kind, X, 0.0, rho, lam, mu, dvec, pol, wl)
     # time derivative in closed form: d/dt F'(d.x - c t) = -c F''(d.x - c t), F'' = -k^2 sin
     c = math.sqrt((lam + 2 * mu) / rho) if kind == "P" else math.sqrt(mu / rho)
@@ -380,6 +378,20 @@ def test_interior_truncation_error_at_design_order(order, kind):
     e1 = _interior_truncation(order, 24, kind, "identity")
     e2 = _interior_truncation(order, 48, kind, "identity")
     assert math.log2(e1 / e2) > order - 0.1, (e1, e2)
+
+
+@pytest.mark.parametrize("kind", ["P", "S"])
+def test_interior_truncation_homogeneous_medium_in_physical_units(kind):
+    """The first workload's homogeneous medium (rho = 2700 kg/m^3, vp = 6000 m/s, vs = 3464 m/s)
+    on a 1 km cube with an 800 m wavelength: the same relative truncation errors and rate as the
+    unit problem, so no step of the scheme depends on the units (order 6)."""
+    rho, vp, vs = 2700.0, 6000.0, 3464.0
+    med = (rho, rho * (vp * vp - 2 * vs * vs), rho * vs * vs)
+    e1 = _interior_truncation(6, 24, kind, "identity", 1000.0, med, 800.0)
+    e2 = _interior_truncation(6, 48, kind, "identity", 1000.0, med, 800.0)
+    assert math.log2(e1 / e2) > 5.9, (e1, e2)
+    u1 = _interior_truncation(6, 24, kind, "identity", 1.0, med, 0.8)
+    assert abs(e1 - u1) < 1e-6 * u1, (e1, u1)
 
 
 @pytest.mark.parametrize("order,lo", [(4, 3.6), (6, 5.0)])
