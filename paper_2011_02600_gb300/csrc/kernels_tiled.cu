@@ -31,54 +31,12 @@
 #include "adjoint_terms.cuh"
 #include "common.cuh"
 #include "launch.h"
+#include "tile_map.cuh"
 #include "tma.cuh"
 
 namespace sbp {
 
-constexpr int TX = 32;
-constexpr int TY = 8;
-constexpr int HX = 4;              // halo in the tile loads (>= q of every order)
-constexpr int BXH = TX + 2 * HX;   // 40
-constexpr int BYH = TY + 2 * HX;   // 16
 constexpr unsigned kWaitLimit = 1u << 24;  // polls (with 64 ns sleeps) before giving up: about a second
-
-// Tile `t` of `nt` along an axis of n nodes, tile width w: origin of its loads and the
-// owned node range [own0, own1).  The last tile starts at n - w rounded up to `align`
-// (never below 0); the one before it gives up the nodes from there on.
-struct TileAxis {
-  int origin, own0, own1;
-};
-__device__ __forceinline__ TileAxis tile_axis(int t, int nt, int n, int w, int align) {
-  int last = n - w > 0 ? n - w : 0;
-  last = (last + align - 1) / align * align;
-  TileAxis a;
-  a.origin = t == nt - 1 ? last : t * w;
-  a.own0 = a.origin;
-  a.own1 = t == nt - 1 ? n : (t == nt - 2 ? last : (t + 1) * w);
-  return a;
-}
-
-// Launch order of the tiles of one s chunk: groups of kSwizzle tile columns (q), in each
-// group q fastest, then r.  Blocks start in about launch order, so the tiles that share a
-// halo row (r neighbours, kSwizzle launches apart) and a halo column (q neighbours, next to
-// each other) run close together in time and the second reads the halo from L2; in plain
-// row order r neighbours start a whole row of tiles apart, and on wide grids the halo has
-// left L2 by then.
-constexpr int kSwizzle = 8;
-__device__ __forceinline__ void swizzle_tiles(int lin, int nbx, int nby, int& bx, int& by) {
-  const int full = nbx / kSwizzle;                 // complete groups
-  const int group = lin / (kSwizzle * nby);
-  if (group < full) {
-    const int rem = lin - group * kSwizzle * nby;
-    by = rem / kSwizzle;
-    bx = group * kSwizzle + rem % kSwizzle;
-  } else {
-    const int gw = nbx - full * kSwizzle;          // width of the last, narrower group
-    const int rem = lin - full * kSwizzle * nby;
-    by = rem / gw;
-    bx = full * kSwizzle + rem % gw;
-  }
-}
 
 // Closure-row sums of the b planes at one end of s (HI: the s = 1 end) for the node
 // column col: for closure row r (plane r, or ns-1-r at the high end) and c = 0..2,
@@ -144,18 +102,6 @@ struct FluxTiles {
   T fr[3][BYH][TX];
 };
 
-constexpr int kMaxCW = 10;  // widest closure row (order 6)
-
-// Per-thread q rows of a tile that owns closure nodes: the smem column of tap 0 for
-// D- (of the flux tile) and D+ (of the state tile) and the weights of kMaxCW taps.
-template <typename T>
-struct QRows {
-  T wm[kMaxCW][TX];
-  T wp[kMaxCW][TX];
-  int bm[TX];
-  int bp[TX];
-};
-
 template <typename T>
 struct TiledShared {
   Stage<T> st[2];
@@ -178,57 +124,6 @@ __device__ __forceinline__ void issue_plane(TiledShared<T>& S, int stage, const 
   tma_load_4d(&st.ar[0][0][0], &tm.met_r, i0, j0 - HX, k, 3, bar);
   tma_load_4d(&st.as[0][0][0], &tm.met_s, i0, j0, k, 6, bar);
   tma_load_4d(&st.mat[0][0][0], &tm.mat, i0, j0, k, 0, bar);
-}
-
-// Rows of D- and D+ along q for thread column tx of a tile with origin i0, as cw taps
-// starting at a shared-memory column: the closure row (the cw nodes nearest the face)
-// for a node within b of a q face, the interior stencil otherwise, zero weights for a
-// column the tile does not own ([own0, own1)).  Every tap lies in the computed flux
-// columns [HX-Q, HX+TX+R) and state columns [0, BXH).
-template <typename T, int O>
-__device__ __forceinline__ void fill_q_rows(QRows<T>& Qr, int tx, int i0, int own0, int own1, int nq) {
-  using C = OpCoef<O>;
-  constexpr int BC = C::b, CW = C::cw, Q = C::q, R = C::r;
-  const int i = i0 + tx;
-  const bool owned = i >= own0 && i < own1;
-  int bm, bp;
-  T wm[CW], wp[CW];
-  if (owned && i < BC) {
-    bm = bp = HX - i0;
-#pragma unroll
-    for (int c = 0; c < CW; ++c) {
-      wm[c] = Tab<T, O>::m(i, c);
-      wp[c] = Tab<T, O>::p(i, c);
-    }
-  } else if (owned && i > nq - 1 - BC) {
-    // tap t is node nq-cw+t, i.e. column cw-1-t of the mirrored closure row ii
-    const int ii = nq - 1 - i;
-    bm = bp = HX + nq - CW - i0;
-#pragma unroll
-    for (int t = 0; t < CW; ++t) {
-      wm[t] = -Tab<T, O>::p(ii, CW - 1 - t);
-      wp[t] = -Tab<T, O>::m(ii, CW - 1 - t);
-    }
-  } else {
-    // interior stencil, placed so that all cw taps stay inside the computed columns
-    const int dm = HX + tx - Q, dp = HX + tx - R;
-    bm = min(dm, HX + TX + R - CW);
-    bp = min(dp, BXH - CW);
-#pragma unroll
-    for (int c = 0; c < CW; ++c) {
-      const int jm = bm + c - dm - Q;   // offset of this tap from the node for D-
-      const int jp = bp + c - dp - R;   // and for D+
-      wm[c] = owned && jm >= -Q && jm <= R ? T(-C::alpha(-jm)) : T(0);
-      wp[c] = owned && jp >= -R && jp <= Q ? T(C::alpha(jp)) : T(0);
-    }
-  }
-  Qr.bm[tx] = bm;
-  Qr.bp[tx] = bp;
-#pragma unroll
-  for (int c = 0; c < kMaxCW; ++c) {
-    Qr.wm[c][tx] = c < CW ? wm[c] : T(0);
-    Qr.wp[c][tx] = c < CW ? wp[c] : T(0);
-  }
 }
 
 // KIND 0: the forward stage.  KIND 1: the adjoint's L^T pass on q = yhat (-H times the

@@ -1,0 +1,195 @@
+// CPU check of the tiled stage kernel's index arithmetic (paper_2011_02600_gb300/csrc/tile_map.cuh,
+// compiled here as host C++) for every grid size in a range, for orders 2, 4 and 6:
+//   * the tiles along q (width TX, origins on 4-node boundaries) and r (width TY) own disjoint
+//     node ranges that cover the axis, and every q origin keeps the tile loads on a 16-byte
+//     boundary;
+//   * the per-thread q rows (fill_q_rows): every tap of every thread lies in the flux columns the
+//     kernel computes and in the loaded state columns, threads that own no node carry zero
+//     weights, and the row a thread applies equals row i of D- and of D+ (Table 1 inside, the
+//     closure tables within b of a face, the mirrored closure at the far face);
+//   * along r, every tap of every owned node's rows lies in the computed flux rows and the loaded
+//     state rows of its tile;
+//   * the tile launch order (swizzle_tiles) is a bijection onto the tiles.
+// Prints "ok" and exits 0, or lists the first failures and exits 1.
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+using std::max;
+using std::min;
+
+#include "tile_map.cuh"
+
+using namespace sbp;
+
+static long failures = 0;
+#define CHECK(cond, ...)                 \
+  do {                                   \
+    if (!(cond)) {                       \
+      if (failures++ < 20) {             \
+        fprintf(stderr, __VA_ARGS__);    \
+        fputc('\n', stderr);             \
+      }                                  \
+    }                                    \
+  } while (0)
+
+// Closure tables of D+ and D- (rows 0..b-1, columns 0..cw-1, unit spacing).
+template <int O> struct Closure;
+template <> struct Closure<2> {
+  static constexpr double P[2][4] = SBP_DP2_ROWS;
+  static constexpr double M[2][4] = SBP_DM2_ROWS;
+};
+template <> struct Closure<4> {
+  static constexpr double P[4][7] = SBP_DP4_ROWS;
+  static constexpr double M[4][7] = SBP_DM4_ROWS;
+};
+template <> struct Closure<6> {
+  static constexpr double P[6][10] = SBP_DP6_ROWS;
+  static constexpr double M[6][10] = SBP_DM6_ROWS;
+};
+
+// Row i of D+ (plus) or D- on n nodes as a dense vector: the closure rows within b of the
+// q = 0 face, at the far face D+[n-1-i][n-1-j] = -D-[i][j] and D-[n-1-i][n-1-j] = -D+[i][j],
+// and inside alpha_j at offsets -r..q for D+, beta_j = -alpha_{-j} at offsets -q..r for D-.
+template <int O>
+std::vector<double> dense_row(int i, int n, bool plus) {
+  using C = OpCoef<O>;
+  std::vector<double> row(n, 0.0);
+  if (i < C::b) {
+    for (int c = 0; c < C::cw; ++c) row[c] = plus ? Closure<O>::P[i][c] : Closure<O>::M[i][c];
+  } else if (i > n - 1 - C::b) {
+    const int ii = n - 1 - i;
+    for (int c = 0; c < C::cw; ++c) row[n - 1 - c] = plus ? -Closure<O>::M[ii][c] : -Closure<O>::P[ii][c];
+  } else if (plus) {
+    for (int j = -C::r; j <= C::q; ++j) row[i + j] = C::alpha(j);
+  } else {
+    for (int j = -C::q; j <= C::r; ++j) row[i + j] = -C::alpha(-j);
+  }
+  return row;
+}
+
+// Ownership along one axis: disjoint ranges covering [0, n), origins as required.
+void check_partition(int n, int w, int align, const char* axis) {
+  const int nt = (n + w - 1) / w;
+  int next = 0;
+  for (int t = 0; t < nt; ++t) {
+    const TileAxis a = tile_axis(t, nt, n, w, align);
+    CHECK(a.own0 == next, "%s n=%d tile %d: owns from %d, expected %d", axis, n, t, a.own0, next);
+    CHECK(a.own1 > a.own0 && a.own1 - a.own0 <= w, "%s n=%d tile %d: owns [%d, %d)", axis, n, t, a.own0, a.own1);
+    CHECK(a.origin == a.own0 && a.origin >= 0 && a.origin % align == 0, "%s n=%d tile %d: origin %d", axis, n, t,
+          a.origin);
+    next = a.own1;
+  }
+  CHECK(next == n, "%s n=%d: ownership ends at %d", axis, n, next);
+}
+
+template <typename T, int O>
+void check_q_rows(int n) {
+  using C = OpCoef<O>;
+  constexpr int CW = C::cw, Q = C::q, R = C::r;
+  const int nt = (n + TX - 1) / TX;
+  static QRows<T> Qr;
+  for (int t = 0; t < nt; ++t) {
+    const TileAxis a = tile_axis(t, nt, n, TX, 4);
+    for (int tx = 0; tx < TX; ++tx) {
+      fill_q_rows<T, O>(Qr, tx, a.origin, a.own0, a.own1, n);
+      const int bm = Qr.bm[tx], bp = Qr.bp[tx];
+      CHECK(bm >= HX - Q && bm + CW <= HX + TX + R, "q n=%d O=%d tile %d tx %d: D- taps [%d, %d) outside the flux columns",
+            n, O, t, tx, bm, bm + CW);
+      CHECK(bp >= 0 && bp + CW <= BXH, "q n=%d O=%d tile %d tx %d: D+ taps [%d, %d) outside the state columns", n, O, t, tx,
+            bp, bp + CW);
+      for (int c = CW; c < kMaxCW; ++c)
+        CHECK(Qr.wm[c][tx] == T(0) && Qr.wp[c][tx] == T(0), "q n=%d O=%d: weight beyond cw", n, O);
+      const int i = a.origin + tx;
+      const bool owned = i >= a.own0 && i < a.own1;
+      if (!owned) {
+        for (int c = 0; c < CW; ++c)
+          CHECK(Qr.wm[c][tx] == T(0) && Qr.wp[c][tx] == T(0), "q n=%d O=%d tile %d tx %d: weight on a column not owned", n,
+                O, t, tx);
+        continue;
+      }
+      for (int pass = 0; pass < 2; ++pass) {
+        const bool plus = pass == 1;
+        std::vector<double> eff(n, 0.0);
+        for (int c = 0; c < CW; ++c) {
+          const T wgt = plus ? Qr.wp[c][tx] : Qr.wm[c][tx];
+          const int node = a.origin - HX + (plus ? bp : bm) + c;   // smem column 0 is node origin - HX
+          if (wgt == T(0)) continue;
+          CHECK(node >= 0 && node < n, "q n=%d O=%d node %d: tap at node %d outside the grid", n, O, i, node);
+          if (node >= 0 && node < n) eff[node] += (double)wgt;
+        }
+        const std::vector<double> want = dense_row<O>(i, n, plus);
+        for (int c = 0; c < n; ++c)
+          CHECK(eff[c] == (double)(T)want[c], "q n=%d O=%d node %d: %s row differs at node %d (%.17g vs %.17g)", n, O, i,
+                plus ? "D+" : "D-", c, eff[c], (double)(T)want[c]);
+      }
+    }
+  }
+}
+
+template <int O>
+void check_r_taps(int n) {
+  using C = OpCoef<O>;
+  const int nt = (n + TY - 1) / TY;
+  for (int t = 0; t < nt; ++t) {
+    const TileAxis a = tile_axis(t, nt, n, TY, 1);
+    for (int j = a.own0; j < a.own1; ++j)
+      for (int pass = 0; pass < 2; ++pass) {
+        const bool plus = pass == 1;
+        const std::vector<double> row = dense_row<O>(j, n, plus);
+        for (int c = 0; c < n; ++c) {
+          if (row[c] == 0.0) continue;
+          const int s = c - a.origin + HX;   // smem row of node c
+          if (plus)
+            CHECK(s >= 0 && s < BYH, "r n=%d O=%d node %d: D+ tap at node %d outside the state rows", n, O, j, c);
+          else
+            CHECK(s >= HX - C::q && s < HX + TY + C::r, "r n=%d O=%d node %d: D- tap at node %d outside the flux rows", n,
+                  O, j, c);
+        }
+      }
+  }
+}
+
+void check_swizzle(int nbx, int nby) {
+  std::vector<char> seen((size_t)nbx * nby, 0);
+  for (int lin = 0; lin < nbx * nby; ++lin) {
+    int bx = -1, by = -1;
+    swizzle_tiles(lin, nbx, nby, bx, by);
+    const bool in = bx >= 0 && bx < nbx && by >= 0 && by < nby;
+    CHECK(in, "swizzle %d x %d: launch %d maps to (%d, %d)", nbx, nby, lin, bx, by);
+    if (in) {
+      CHECK(!seen[(size_t)by * nbx + bx], "swizzle %d x %d: tile (%d, %d) launched twice", nbx, nby, bx, by);
+      seen[(size_t)by * nbx + bx] = 1;
+    }
+  }
+}
+
+template <int O>
+void check_order(const std::vector<int>& sizes) {
+  const int nmin = 2 * OpCoef<O>::b + max(OpCoef<O>::r, OpCoef<O>::q);
+  for (int n : sizes) {
+    if (n < nmin) continue;
+    check_partition(n, TX, 4, "q");
+    check_partition(n, TY, 1, "r");
+    check_q_rows<double, O>(n);
+    check_q_rows<float, O>(n);
+    check_r_taps<O>(n);
+  }
+}
+
+int main() {
+  std::vector<int> sizes;
+  for (int n = 1; n <= 400; ++n) sizes.push_back(n);
+  for (int n : {511, 512, 513, 1023, 1024, 1025, 1026, 1029, 2049, 4097}) sizes.push_back(n);
+  check_order<2>(sizes);
+  check_order<4>(sizes);
+  check_order<6>(sizes);
+  for (int nbx = 1; nbx <= 70; ++nbx)
+    for (int nby = 1; nby <= 140; ++nby) check_swizzle(nbx, nby);
+  if (failures) {
+    fprintf(stderr, "%ld failures\n", failures);
+    return 1;
+  }
+  printf("ok\n");
+  return 0;
+}
