@@ -9,7 +9,10 @@
 //     closure tables within b of a face, the mirrored closure at the far face);
 //   * along r, every tap of every owned node's rows lies in the computed flux rows and the loaded
 //     state rows of its tile;
-//   * the tile launch order (swizzle_tiles) is a bijection onto the tiles.
+//   * the tile launch order (swizzle_tiles) is a bijection onto the tiles;
+//   * apply_row (the rows of the general, metrics and adjoint kernels) equals the dense rows, the
+//     norm weights are symmetric and integrate constants exactly, and the applied operators
+//     satisfy the SBP relation H D+ + D-^T H = B (Sec. 4.1, Eq. upw_SBP) to rounding.
 // Prints "ok" and exits 0, or lists the first failures and exits 1.
 #include <algorithm>
 #include <cstdio>
@@ -150,6 +153,64 @@ void check_r_taps(int n) {
   }
 }
 
+// apply_row (the rows the general, metrics and adjoint kernels apply) equals the dense rows.
+template <typename T, int O>
+void check_apply_row(int n) {
+  for (int pos = 0; pos < n; ++pos)
+    for (int pass = 0; pass < 2; ++pass) {
+      const bool plus = pass == 1;
+      std::vector<double> eff(n, 0.0);
+      bool inside = true;
+      auto fn = [&](int c, T w) {
+        if (c < 0 || c >= n) inside = false;
+        else eff[c] += (double)w;
+      };
+      if (plus) apply_row<T, O, true>(pos, n, fn);
+      else apply_row<T, O, false>(pos, n, fn);
+      CHECK(inside, "apply_row n=%d O=%d pos %d: tap outside the grid", n, O, pos);
+      const std::vector<double> want = dense_row<O>(pos, n, plus);
+      for (int c = 0; c < n; ++c)
+        CHECK(eff[c] == (double)(T)want[c], "apply_row n=%d O=%d pos %d: %s row differs at %d", n, O, pos,
+              plus ? "D+" : "D-", c);
+    }
+}
+
+// Norm weights: symmetric, sum n - 1 (H integrates constants exactly on unit spacing), and the
+// compile-time forms in T equal the rounded weight and its reciprocal.
+template <int O>
+void check_weights(int n) {
+  double sum = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double w = norm_weight<O>(i, n);
+    sum += w;
+    CHECK(w > 0.0 && w == norm_weight<O>(n - 1 - i, n), "weights n=%d O=%d: w[%d] = %g", n, O, i, w);
+    CHECK((norm_weight_t<float, O>(i, n) == (float)w && norm_weight_t<double, O>(i, n) == w),
+          "weights n=%d O=%d: constant form of w[%d]", n, O, i);
+    CHECK((norm_weight_inv_t<float, O>(i, n) == (float)(1.0 / w) && norm_weight_inv_t<double, O>(i, n) == 1.0 / w),
+          "weights n=%d O=%d: constant form of 1/w[%d]", n, O, i);
+  }
+  CHECK(sum > n - 1 - 1e-12 * n && sum < n - 1 + 1e-12 * n, "weights n=%d O=%d: sum %.17g", n, O, sum);
+}
+
+// The SBP relation H D+ + D-^T H = diag(-1, 0, ..., 0, 1) (Sec. 4.1, Eq. upw_SBP) for the
+// operators the kernels apply, to rounding.
+template <int O>
+void check_sbp(int n) {
+  std::vector<double> P((size_t)n * n, 0.0), M((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    apply_row<double, O, true>(i, n, [&](int c, double w) { P[(size_t)i * n + c] += w; });
+    apply_row<double, O, false>(i, n, [&](int c, double w) { M[(size_t)i * n + c] += w; });
+  }
+  double worst = 0.0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      const double v = norm_weight<O>(i, n) * P[(size_t)i * n + j] + M[(size_t)j * n + i] * norm_weight<O>(j, n);
+      const double b = i == j ? (i == 0 ? -1.0 : i == n - 1 ? 1.0 : 0.0) : 0.0;
+      worst = max(worst, v - b > 0 ? v - b : b - v);
+    }
+  CHECK(worst < 1e-13, "SBP relation n=%d O=%d: residual %g", n, O, worst);
+}
+
 void check_swizzle(int nbx, int nby) {
   std::vector<char> seen((size_t)nbx * nby, 0);
   for (int lin = 0; lin < nbx * nby; ++lin) {
@@ -174,6 +235,10 @@ void check_order(const std::vector<int>& sizes) {
     check_q_rows<double, O>(n);
     check_q_rows<float, O>(n);
     check_r_taps<O>(n);
+    check_apply_row<double, O>(n);
+    check_apply_row<float, O>(n);
+    check_weights<O>(n);
+    if (n <= 64) check_sbp<O>(n);
   }
 }
 
