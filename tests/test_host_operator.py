@@ -1,0 +1,94 @@
+"""The kernels' per-node operator on the CPU: tests/host_operator.cpp compiles raw_operator_at and
+apply_P of csrc/common.cuh (rows of D+ and D-, flux and strain forms, free-surface and
+characteristic penalties, P~) as host C++; its dQ/dt at every node of a curvilinear grid with a
+random medium and a random state is compared with the oracle's right-hand side (Eq.
+gen_hyp_transformed_discrete_SAT) in FP64.  The metric terms are inputs here (the oracle's,
+Sec. 2.2); the stored coefficients 1/(rho J), lambda/J, mu/J are formed as the library forms
+them."""
+import ctypes
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle.elastic import Scheme, rhs
+from oracle.metrics import metrics
+from workloads.fields import random_state
+from workloads.geometry import make_map, node_coordinates
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+BCS = {
+    "free": [("free",)] * 6,
+    "char": [("char", g) for g in (0.0, 0.3, -0.4, 1.0, -1.0, 0.25)],
+    "mixed": [("char", 0.0), ("free",), ("char", 0.6), ("free",), ("char", -0.2), ("free",)],
+}
+
+
+def _cuda_include():
+    for base in (os.environ.get("CUDA_HOME"), os.environ.get("CUDA_PATH"), "/usr/local/cuda"):
+        if base and os.path.exists(os.path.join(base, "include", "cuda_runtime.h")):
+            return os.path.join(base, "include")
+    nvcc = shutil.which("nvcc")
+    if nvcc:
+        inc = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "include")
+        if os.path.exists(os.path.join(inc, "cuda_runtime.h")):
+            return inc
+    return None
+
+
+@pytest.fixture(scope="module")
+def hostop(tmp_path_factory):
+    cxx = shutil.which("g++")
+    inc = _cuda_include()
+    if not cxx or not inc:
+        pytest.skip("needs g++ and the CUDA headers")
+    so = str(tmp_path_factory.mktemp("hostop") / "libhostop.so")
+    r = subprocess.run([cxx, "-std=c++17", "-O2", "-w", "-shared", "-fPIC", "-I" + inc,
+                        "-I" + os.path.join(ROOT, "paper_2011_02600_gb300", "csrc"),
+                        "-I" + os.path.join(ROOT, "include"),
+                        os.path.join(ROOT, "tests", "host_operator.cpp"), "-o", so],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    lib = ctypes.CDLL(so)
+    P = ctypes.c_void_p
+    lib.host_rhs.argtypes = [ctypes.c_int] * 4 + [P] * 6
+    lib.host_rhs.restype = ctypes.c_int
+    return lib
+
+
+def _host_rhs(lib, order, Q, J, a, mat, bc):
+    ns, nr, nq = J.shape
+    rho, lam, mu = mat
+    met = np.ascontiguousarray(np.stack([a[xi][c] for xi in range(3) for c in range(3)]))
+    coef = np.ascontiguousarray(np.stack([1.0 / (rho * J), lam / J, mu / J]))
+    q = np.ascontiguousarray(Q)
+    kind = (ctypes.c_int * 6)(*[0 if b[0] == "free" else 1 for b in bc])
+    gamma = (ctypes.c_double * 6)(*[0.0 if b[0] == "free" else b[1] for b in bc])
+    out = np.empty_like(q)
+    rc = lib.host_rhs(order, nq, nr, ns, q.ctypes.data, met.ctypes.data, coef.ctypes.data,
+                      ctypes.cast(kind, ctypes.c_void_p), ctypes.cast(gamma, ctypes.c_void_p), out.ctypes.data)
+    assert rc == 0
+    return out
+
+
+@pytest.mark.parametrize("order,nodes", [(2, (9, 7, 8)), (4, (13, 12, 14)), (6, (18, 16, 17))])
+@pytest.mark.parametrize("bcname", sorted(BCS))
+def test_kernel_operator_matches_oracle_fp64(hostop, order, nodes, bcname):
+    bc = BCS[bcname]
+    X = node_coordinates(make_map("curvy", (1000.0, 1100.0, 900.0)), nodes)
+    J, a = metrics(*X, order)
+    rng = np.random.default_rng(order * 10 + len(bcname))
+    shape = J.shape
+    rho = rng.uniform(2000.0, 3000.0, shape)
+    mu = rho * rng.uniform(1500.0, 3000.0, shape) ** 2
+    lam = rho * rng.uniform(3000.0, 6000.0, shape) ** 2 - 2 * mu
+    lam = np.maximum(lam, 0.1 * mu)
+    mat = (rho, lam, mu)
+    Q = random_state(nodes, 21 + order, 1.0, 1.0e6)
+    got = _host_rhs(hostop, order, Q, J, a, mat, bc)
+    want = rhs(Q, Scheme(order, nodes), J, a, mat, bc)
+    err = np.abs(got - want).max(axis=(1, 2, 3)) / np.abs(want).max(axis=(1, 2, 3))
+    assert err.max() < 1e-12, err
