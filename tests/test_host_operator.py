@@ -15,8 +15,9 @@ import pytest
 
 from oracle.elastic import Scheme, rhs
 from oracle.metrics import metrics
-from workloads.fields import random_state
+from workloads.fields import random_state, smooth_state
 from workloads.geometry import make_map, node_coordinates
+from workloads.media import make_medium
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -54,22 +55,26 @@ def hostop(tmp_path_factory):
     assert r.returncode == 0, r.stderr
     lib = ctypes.CDLL(so)
     P = ctypes.c_void_p
-    lib.host_rhs.argtypes = [ctypes.c_int] * 4 + [P] * 6
-    lib.host_rhs.restype = ctypes.c_int
+    for fn in (lib.host_rhs, lib.host_rhs_f32):
+        fn.argtypes = [ctypes.c_int] * 4 + [P] * 6
+        fn.restype = ctypes.c_int
     return lib
 
 
-def _host_rhs(lib, order, Q, J, a, mat, bc):
+def _host_rhs(lib, order, Q, J, a, mat, bc, dtype=np.float64):
+    """dQ/dt of the host-compiled kernel operator; FP32 arrays (state, metrics, coefficients cast
+    from FP64 as the library stores them) when dtype is float32."""
     ns, nr, nq = J.shape
     rho, lam, mu = mat
-    met = np.ascontiguousarray(np.stack([a[xi][c] for xi in range(3) for c in range(3)]))
-    coef = np.ascontiguousarray(np.stack([1.0 / (rho * J), lam / J, mu / J]))
-    q = np.ascontiguousarray(Q)
+    met = np.ascontiguousarray(np.stack([a[xi][c] for xi in range(3) for c in range(3)]).astype(dtype))
+    coef = np.ascontiguousarray(np.stack([1.0 / (rho * J), lam / J, mu / J]).astype(dtype))
+    q = np.ascontiguousarray(np.asarray(Q).astype(dtype))
     kind = (ctypes.c_int * 6)(*[0 if b[0] == "free" else 1 for b in bc])
     gamma = (ctypes.c_double * 6)(*[0.0 if b[0] == "free" else b[1] for b in bc])
     out = np.empty_like(q)
-    rc = lib.host_rhs(order, nq, nr, ns, q.ctypes.data, met.ctypes.data, coef.ctypes.data,
-                      ctypes.cast(kind, ctypes.c_void_p), ctypes.cast(gamma, ctypes.c_void_p), out.ctypes.data)
+    fn = lib.host_rhs if dtype == np.float64 else lib.host_rhs_f32
+    rc = fn(order, nq, nr, ns, q.ctypes.data, met.ctypes.data, coef.ctypes.data,
+            ctypes.cast(kind, ctypes.c_void_p), ctypes.cast(gamma, ctypes.c_void_p), out.ctypes.data)
     assert rc == 0
     return out
 
@@ -92,3 +97,20 @@ def test_kernel_operator_matches_oracle_fp64(hostop, order, nodes, bcname):
     want = rhs(Q, Scheme(order, nodes), J, a, mat, bc)
     err = np.abs(got - want).max(axis=(1, 2, 3)) / np.abs(want).max(axis=(1, 2, 3))
     assert err.max() < 1e-12, err
+
+
+@pytest.mark.parametrize("order,nodes", [(2, (9, 7, 8)), (4, (13, 12, 14)), (6, (18, 16, 17))])
+@pytest.mark.parametrize("bcname", sorted(BCS))
+def test_kernel_operator_matches_oracle_fp32(hostop, order, nodes, bcname):
+    """The FP32 instantiation (FP32 closure tables, weights and penalty arithmetic) on a smooth
+    state, within the FP32 tolerance of the GPU parity tests (5e-5 of each field's peak)."""
+    bc = BCS[bcname]
+    X = node_coordinates(make_map("curvy", (1000.0, 1100.0, 900.0)), nodes)
+    J, a = metrics(*X, order)
+    mat = make_medium("smooth_gradient", Lz=900.0)(*X)
+    K, Jj, I = np.meshgrid(np.arange(nodes[2]), np.arange(nodes[1]), np.arange(nodes[0]), indexing="ij")
+    Q = np.stack(smooth_state(nodes, 9, I, Jj, K))
+    got = _host_rhs(hostop, order, Q, J, a, mat, bc, np.float32)
+    want = rhs(Q, Scheme(order, nodes), J, a, mat, bc)
+    err = np.abs(got - want).max(axis=(1, 2, 3)) / np.abs(want).max(axis=(1, 2, 3))
+    assert err.max() < 5e-5, err
