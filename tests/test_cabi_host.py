@@ -113,3 +113,19 @@ def test_network_entry_points_reject_bad_arguments(lib):
     _expect(1, L.sbp_nn_im2col, a, b, 0, 2, 8, 5, 2, None)
     _expect(1, L.sbp_nn_moment_combine, None, None, None, None, None, 4, 2, 8, 0, None)
     _expect(1, L.sbp_nn_moment_combine, a, b, None, None, None, 4, 2, 8, 0, None)        # no output
+
+
+def test_energy_noalloc_rejects_bad_arguments_on_the_host(lib):
+    """Every check of sbp_energy_noalloc runs before its first CUDA call, so it runs without a GPU
+    (the addresses below are never dereferenced)."""
+    q, mat, nodes = 4096, 8192, (20, 20, 20)
+    ldq, fs = 32, 32 * 20 * 20
+    _expect(1, L.sbp_energy_noalloc, None, mat, nodes, ldq, fs, 6, 32, 0, None)       # null state
+    _expect(1, L.sbp_energy_noalloc, q, mat, nodes, ldq, fs, 5, 32, 0, None)          # order
+    _expect(1, L.sbp_energy_noalloc, q, mat, nodes, ldq, fs, 6, 16, 0, None)          # precision
+    _expect(1, L.sbp_energy_noalloc, q, mat, (15, 20, 20), ldq, fs, 6, 32, 0, None)   # too few nodes
+    _expect(1, L.sbp_energy_noalloc, q, mat, nodes, 19, fs, 6, 32, 0, None)           # ldq < nq
+    _expect(1, L.sbp_energy_noalloc, q, mat, nodes, ldq, fs - 1, 6, 32, 0, None)      # fields overlap
+    _expect(1, L.sbp_energy_noalloc, q, mat, nodes, ldq, 1 << 31, 6, 32, 0, None)     # field stride >= 2^31
+    _expect(1, L.sbp_energy_noalloc, q, mat, nodes, ldq, fs, 6, 32, 4097, None)       # beyond the static scratch
+    _expect(1, L.sbp_energy_noalloc, q, mat, nodes, ldq, fs, 6, 32, -1, None)
