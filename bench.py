@@ -534,7 +534,7 @@ def _kernel_digest():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2011_02600_gb300", "csrc")
     for f in ("kernels_tiled.cu", "tile_map.cuh", "common.cuh", "tma.cuh", "adjoint_terms.cuh", "sbp_coeffs.h",
-              "launch.h", "api.cu"):
+              "launch.h", "adjoint_args.h", "api.cu"):
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 

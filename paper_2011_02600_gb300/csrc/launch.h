@@ -4,31 +4,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "adjoint_args.h"
 #include "common.cuh"
 #include "tma.cuh"
 
 namespace sbp {
-
-template <typename T>
-struct AdjArgs {
-  const T* ubar_next;  // Ub_{k+1} (may be null: zero)
-  T* ubar_out;         // Ub_k (mode 1) or L^T w (mode 0); may alias ubar_next
-  const T* wbar_in;    // Wb before adding B_k Ub_{k+1} (mode 1), or w (mode 0)
-  T* wbar;             // mode 1: Wb_k written by the prep pass, A_k Wb_k written by the stage pass
-  T* yhat;             // scratch: H^-1 P~ Wb_k (9 fields)
-  const T* u;          // forward stage state U_k (mode 1 with gradient)
-  const T* met;
-  const T* mat;
-  const double* rlmj;  // rho, lambda, mu, J (FP64, 4 fields), for the gradient
-  double* grad;        // d/d(rho, lambda, mu) accumulators (FP64, 3 fields), may be null
-  Dims d;
-  T rk_a, rk_b, dt;
-  int mode;            // 0: out = L^T w; 1: adjoint stage
-  int bc_kind[6];
-  T bc_gamma[6];
-  T inv_h[3];
-  T inv_h0[3];
-};
 
 // General adjoint stage: the prep kernel (Wb_k, yhat) and the one-thread-per-node L^T and
 // gradient kernel; launch_adjoint_prep alone runs the first of the two.

@@ -6,9 +6,6 @@ gen_hyp_transformed_discrete_SAT) in FP64.  The metric terms are inputs here (th
 Sec. 2.2); the stored coefficients 1/(rho J), lambda/J, mu/J are formed as the library forms
 them."""
 import ctypes
-import os
-import shutil
-import subprocess
 
 import numpy as np
 import pytest
@@ -19,7 +16,7 @@ from workloads.fields import random_state, smooth_state
 from workloads.geometry import make_map, node_coordinates
 from workloads.media import make_medium
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+from host_build import build
 
 BCS = {
     "free": [("free",)] * 6,
@@ -28,31 +25,9 @@ BCS = {
 }
 
 
-def _cuda_include():
-    for base in (os.environ.get("CUDA_HOME"), os.environ.get("CUDA_PATH"), "/usr/local/cuda"):
-        if base and os.path.exists(os.path.join(base, "include", "cuda_runtime.h")):
-            return os.path.join(base, "include")
-    nvcc = shutil.which("nvcc")
-    if nvcc:
-        inc = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "include")
-        if os.path.exists(os.path.join(inc, "cuda_runtime.h")):
-            return inc
-    return None
-
-
 @pytest.fixture(scope="module")
 def hostop(tmp_path_factory):
-    cxx = shutil.which("g++")
-    inc = _cuda_include()
-    if not cxx or not inc:
-        pytest.skip("needs g++ and the CUDA headers")
-    so = str(tmp_path_factory.mktemp("hostop") / "libhostop.so")
-    r = subprocess.run([cxx, "-std=c++17", "-O2", "-w", "-shared", "-fPIC", "-I" + inc,
-                        "-I" + os.path.join(ROOT, "paper_2011_02600_gb300", "csrc"),
-                        "-I" + os.path.join(ROOT, "include"),
-                        os.path.join(ROOT, "tests", "host_operator.cpp"), "-o", so],
-                       capture_output=True, text=True)
-    assert r.returncode == 0, r.stderr
+    so = build("host_operator.cpp", tmp_path_factory.mktemp("hostop") / "libhostop.so", shared=True)
     lib = ctypes.CDLL(so)
     P = ctypes.c_void_p
     for fn in (lib.host_rhs, lib.host_rhs_f32):
