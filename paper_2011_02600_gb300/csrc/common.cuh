@@ -232,6 +232,21 @@ __device__ __forceinline__ void apply_P(const T rv[3], const T e[6], T irhoJ, T 
   d[8] = muJ * e[5];
 }
 
+// Energy density of one node over a single division: with l = lambda/J, m = mu/J,
+// r = 1/(rho J) and A = sum s_ii^2 + 2 sum s_ij^2,
+//   rho J |v|^2 + J sigma^T S sigma = |v|^2 / r + (A (3 l + 2 m) - l tr^2) / ((3 l + 2 m) 2 m)
+//                                  = (|v|^2 D + r (A (3 l + 2 m) - l tr^2)) / (r D),  D = (3 l + 2 m) 2 m.
+// Evaluated in the state's precision (FP32 terms are summed in FP64).
+template <typename T>
+__device__ __forceinline__ T energy_density(const T v[3], const T s[6], T r, T l, T m) {
+  const T v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+  const T tr = s[0] + s[1] + s[2];
+  const T A = s[0] * s[0] + s[1] * s[1] + s[2] * s[2] + T(2) * (s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);
+  const T c = T(3) * l + T(2) * m;
+  const T D = c * T(2) * m;
+  return (v2 * D + r * (A * c - l * tr * tr)) / (r * D);
+}
+
 // Write the stage result for one node at in-field offset off.
 template <typename T>
 __device__ __forceinline__ void stage_epilogue(const StageArgs<T>& A, long long off, const T d[9],

@@ -69,3 +69,32 @@ extern "C" int host_rhs_f32(int order, int nq, int nr, int ns, const float* q, c
                             const int* bc_kind, const double* bc_gamma, float* out) {
   return rhs_order<float>(order, nq, nr, ns, q, met, mat, bc_kind, bc_gamma, out);
 }
+
+// Discrete energy E = 1/2 sum_nodes H J (rho |v|^2 + sigma^T S sigma) from the kernels' per-node
+// energy_density (common.cuh) and norm weights, FP64, summed node by node.
+template <int O>
+static double energy_all(int nq, int nr, int ns, const double* q, const double* mat) {
+  const long long fs = (long long)nq * nr * ns;
+  double E = 0.0;
+  for (int k = 0; k < ns; ++k)
+    for (int j = 0; j < nr; ++j)
+      for (int i = 0; i < nq; ++i) {
+        const long long n0 = ((long long)k * nr + j) * nq + i;
+        double v[3], s[6];
+        for (int c = 0; c < 3; ++c) v[c] = q[c * fs + n0];
+        for (int c = 0; c < 6; ++c) s[c] = q[(3 + c) * fs + n0];
+        const double H = norm_weight<O>(i, nq) / (nq - 1) * norm_weight<O>(j, nr) / (nr - 1) * norm_weight<O>(k, ns) /
+                         (ns - 1);
+        E += H * energy_density<double>(v, s, mat[n0], mat[fs + n0], mat[2 * fs + n0]);
+      }
+  return 0.5 * E;
+}
+
+extern "C" int host_energy(int order, int nq, int nr, int ns, const double* q, const double* mat, double* out) {
+  switch (order) {
+    case 2: *out = energy_all<2>(nq, nr, ns, q, mat); return 0;
+    case 4: *out = energy_all<4>(nq, nr, ns, q, mat); return 0;
+    case 6: *out = energy_all<6>(nq, nr, ns, q, mat); return 0;
+    default: return 1;
+  }
+}

@@ -10,7 +10,7 @@ import ctypes
 import numpy as np
 import pytest
 
-from oracle.elastic import Scheme, rhs
+from oracle.elastic import Scheme, energy, rhs
 from oracle.metrics import metrics
 from workloads.fields import random_state, smooth_state
 from workloads.geometry import make_map, node_coordinates
@@ -33,6 +33,8 @@ def hostop(tmp_path_factory):
     for fn in (lib.host_rhs, lib.host_rhs_f32):
         fn.argtypes = [ctypes.c_int] * 4 + [P] * 6
         fn.restype = ctypes.c_int
+    lib.host_energy.argtypes = [ctypes.c_int] * 4 + [P] * 3
+    lib.host_energy.restype = ctypes.c_int
     return lib
 
 
@@ -89,3 +91,23 @@ def test_kernel_operator_matches_oracle_fp32(hostop, order, nodes, bcname):
     want = rhs(Q, Scheme(order, nodes), J, a, mat, bc)
     err = np.abs(got - want).max(axis=(1, 2, 3)) / np.abs(want).max(axis=(1, 2, 3))
     assert err.max() < 5e-5, err
+
+
+@pytest.mark.parametrize("order,nodes", [(2, (9, 7, 8)), (4, (13, 12, 14)), (6, (18, 16, 17))])
+def test_kernel_energy_density_matches_oracle(hostop, order, nodes):
+    """The energy kernel's per-node density (one division, from the stored 1/(rho J), lambda/J,
+    mu/J) and norm weights give the oracle's discrete energy (Eq. physical_energy_discrete with
+    P~) to rounding, for a random state and medium on a curvilinear grid."""
+    X = node_coordinates(make_map("curvy", (1000.0, 1100.0, 900.0)), nodes)
+    J, a = metrics(*X, order)
+    rng = np.random.default_rng(order)
+    rho = rng.uniform(2000.0, 3000.0, J.shape)
+    mu = rho * rng.uniform(1500.0, 3000.0, J.shape) ** 2
+    lam = np.maximum(rho * rng.uniform(3000.0, 6000.0, J.shape) ** 2 - 2 * mu, 0.1 * mu)
+    Q = np.ascontiguousarray(random_state(nodes, 31 + order, 1.0, 1.0e6))
+    coef = np.ascontiguousarray(np.stack([1.0 / (rho * J), lam / J, mu / J]))
+    got = ctypes.c_double()
+    assert hostop.host_energy(order, nodes[0], nodes[1], nodes[2], Q.ctypes.data, coef.ctypes.data,
+                              ctypes.addressof(got)) == 0
+    want = energy(Q, Scheme(order, nodes), J, (rho, lam, mu))
+    assert abs(got.value - want) < 1e-12 * want, (got.value, want)
