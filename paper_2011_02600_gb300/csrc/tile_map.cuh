@@ -1,6 +1,6 @@
 // Tile geometry of the tiled stage kernel (kernels_tiled.cu): tile size and halo, the node
-// range each tile owns along q and r, the launch order of the tiles, and the per-thread rows
-// of D- and D+ along q.  Device code of the kernel; without nvcc the same source compiles as
+// range each tile owns along q and r, the launch order of the tiles, the per-thread rows of D-
+// and D+ along q, and the closure-row sums along s.  Device code of the kernel; without nvcc the same source compiles as
 // host C++, so that the index arithmetic can be checked for any grid size on a CPU.
 #pragma once
 
@@ -113,6 +113,55 @@ __device__ __forceinline__ void fill_q_rows(QRows<T>& Qr, int tx, int i0, int ow
     Qr.wm[c][tx] = c < CW ? wm[c] : T(0);
     Qr.wp[c][tx] = c < CW ? wp[c] : T(0);
   }
+}
+
+// Closure-row sums of the b planes at one end of s (HI: the s = 1 end) for the node
+// column col: for closure row r (plane r, or ns-1-r at the high end) and c = 0..2,
+//   scratch[(e*b + r)*6 + c]     = sum_p D-[r][p] F_s,c(plane p)
+//   scratch[(e*b + r)*6 + 3 + c] = sum_p D+[r][p] v_c(plane p)
+// over the cw planes p nearest the face (unit spacing; rows of the high end by
+// D+[N-1-i][N-1-j] = -D-[i][j]).  Each scratch row is a plane-sized array.
+template <typename T, int O, bool HI>
+__device__ __forceinline__ void s_closure_sums(const T* __restrict__ q, const T* __restrict__ met,
+                                               const Dims& d, int col, T* __restrict__ scratch) {
+  using C = OpCoef<O>;
+  constexpr int BC = C::b;
+  const long long fs = d.fs;
+  T am[BC][3], ap[BC][3];
+#pragma unroll
+  for (int r = 0; r < BC; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) am[r][c] = ap[r][c] = T(0);
+#pragma unroll
+  for (int p = 0; p < C::cw; ++p) {
+    const long long off = (long long)(HI ? d.ns - 1 - p : p) * d.plane + col;
+    T v[3], sg[6], a[3], F[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = __ldg(q + c * fs + off);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sg[c] = __ldg(q + (3 + c) * fs + off);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) a[c] = __ldg(met + (6 + c) * fs + off);
+    flux(a, sg, F);
+#pragma unroll
+    for (int r = 0; r < BC; ++r) {
+      const T wm = HI ? -Tab<T, O>::p(r, p) : Tab<T, O>::m(r, p);
+      const T wp = HI ? -Tab<T, O>::m(r, p) : Tab<T, O>::p(r, p);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        am[r][c] += wm * F[c];
+        ap[r][c] += wp * v[c];
+      }
+    }
+  }
+  T* out = scratch + (long long)(HI ? BC : 0) * 6 * d.plane + col;
+#pragma unroll
+  for (int r = 0; r < BC; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      out[(long long)(r * 6 + c) * d.plane] = am[r][c];
+      out[(long long)(r * 6 + 3 + c) * d.plane] = ap[r][c];
+    }
 }
 
 }  // namespace sbp

@@ -12,15 +12,19 @@
 //   * the tile launch order (swizzle_tiles) is a bijection onto the tiles;
 //   * apply_row (the rows of the general, metrics and adjoint kernels) equals the dense rows, the
 //     norm weights are symmetric and integrate constants exactly, and the applied operators
-//     satisfy the SBP relation H D+ + D-^T H = B (Sec. 4.1, Eq. upw_SBP) to rounding.
+//     satisfy the SBP relation H D+ + D-^T H = B (Sec. 4.1, Eq. upw_SBP) to rounding;
+//   * the closure-row sums along s (s_closure_sums) equal the closure rows of D- applied to
+//     F_s = sigma a_s and of D+ applied to v, at both ends.
 // Prints "ok" and exits 0, or lists the first failures and exits 1.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <vector>
 
 using std::max;
 using std::min;
 
+#define __ldg(p) (*(p))   // the read-only-cache load of the kernel is a plain load on the host
 #include "tile_map.cuh"
 
 using namespace sbp;
@@ -211,6 +215,56 @@ void check_sbp(int n) {
   CHECK(worst < 1e-13, "SBP relation n=%d O=%d: residual %g", n, O, worst);
 }
 
+// s_closure_sums on one node column: scratch row (end, r, c) = row r (or ns-1-r) of D- applied
+// to F_s,c = (sigma a_s)_c along s, and of D+ applied to v_c.
+template <typename T, int O>
+void check_s_closure(int ns) {
+  using C = OpCoef<O>;
+  Dims d;
+  d.nq = 1;
+  d.nr = 1;
+  d.ns = ns;
+  d.ldq = 1;
+  d.plane = 1;
+  d.fs = ns;
+  std::vector<T> q(9 * (size_t)ns), met(9 * (size_t)ns), scratch(2 * C::b * 6, T(-1));
+  unsigned x = 12345u + ns;
+  for (auto& v : q) v = T(((x = x * 1664525u + 1013904223u) >> 8) / double(1 << 24) - 0.5);
+  for (auto& v : met) v = T(((x = x * 1664525u + 1013904223u) >> 8) / double(1 << 24) - 0.5);
+  s_closure_sums<T, O, false>(q.data(), met.data(), d, 0, scratch.data());
+  s_closure_sums<T, O, true>(q.data(), met.data(), d, 0, scratch.data());
+  std::vector<double> F[3], v[3];
+  for (int c = 0; c < 3; ++c) {
+    F[c].assign(ns, 0.0);
+    v[c].assign(ns, 0.0);
+  }
+  for (int k = 0; k < ns; ++k) {
+    const double a0 = met[6 * ns + k], a1 = met[7 * ns + k], a2 = met[8 * ns + k];
+    const double sg[6] = {q[3 * ns + k], q[4 * ns + k], q[5 * ns + k], q[6 * ns + k], q[7 * ns + k], q[8 * ns + k]};
+    F[0][k] = a0 * sg[0] + a1 * sg[3] + a2 * sg[4];   // sigma a_s with sigma in Voigt order xx yy zz xy xz yz
+    F[1][k] = a0 * sg[3] + a1 * sg[1] + a2 * sg[5];
+    F[2][k] = a0 * sg[4] + a1 * sg[5] + a2 * sg[2];
+    for (int c = 0; c < 3; ++c) v[c][k] = q[c * ns + k];
+  }
+  const double tol = sizeof(T) == 8 ? 1e-13 : 1e-5;
+  for (int e = 0; e < 2; ++e)
+    for (int r = 0; r < C::b; ++r) {
+      const int plane = e ? ns - 1 - r : r;
+      const std::vector<double> rm = dense_row<O>(plane, ns, false), rp = dense_row<O>(plane, ns, true);
+      for (int c = 0; c < 3; ++c) {
+        double wm = 0.0, wp = 0.0, scale = 0.0;
+        for (int k = 0; k < ns; ++k) {
+          wm += rm[k] * F[c][k];
+          wp += rp[k] * v[c][k];
+          scale += std::fabs(rm[k]) + std::fabs(rp[k]);
+        }
+        const double gm = scratch[(e * C::b + r) * 6 + c], gp = scratch[(e * C::b + r) * 6 + 3 + c];
+        CHECK(std::fabs(gm - wm) <= tol * scale && std::fabs(gp - wp) <= tol * scale,
+              "s closure ns=%d O=%d end %d row %d c %d: (%g, %g) vs (%g, %g)", ns, O, e, r, c, gm, gp, wm, wp);
+      }
+    }
+}
+
 void check_swizzle(int nbx, int nby) {
   std::vector<char> seen((size_t)nbx * nby, 0);
   for (int lin = 0; lin < nbx * nby; ++lin) {
@@ -238,6 +292,8 @@ void check_order(const std::vector<int>& sizes) {
     check_apply_row<double, O>(n);
     check_apply_row<float, O>(n);
     check_weights<O>(n);
+    check_s_closure<double, O>(n);
+    check_s_closure<float, O>(n);
     if (n <= 64) check_sbp<O>(n);
   }
 }
