@@ -35,6 +35,12 @@ by tests/test_oracle_operators.py):
   semi-definite and the spectral radius of D+ at the value of the interior
   stencil.  These closures are therefore NOT Mattsson's published ones; they
   satisfy the same defining properties.
+* Odd orders 3, 5, 7 (Table 1) take the same construction with closure
+  accuracy p = (order - 1)/2 and b = 2, 4, 6: order 3 is unique, order 5 has
+  one free entry and order 7 four.  Their norms are forced by accuracy; the
+  free entries were again chosen numerically, once, for the smallest spectral
+  radius of D+ (N = 60) with H > 0 and M + M^T - B <= 0, then rounded to
+  rationals with denominators up to 100 and checked exactly.
 """
 from fractions import Fraction as Fr
 
@@ -63,9 +69,13 @@ TABLE2 = {
 # Closure width b and the chosen values of the free entries of M = H D+ (upper-left block).
 CLOSURE = {
     2: dict(b=2, free={}),
+    3: dict(b=2, free={}),
     4: dict(b=4, free={(3, 3): Fr(-4, 5)}),
+    5: dict(b=4, free={(3, 3): Fr(-3, 8)}),
     6: dict(b=6, free={(4, 4): Fr(-17, 25), (4, 5): Fr(131, 100),
                        (5, 4): Fr(-29, 100), (5, 5): Fr(-3, 5)}),
+    7: dict(b=6, free={(4, 4): Fr(-1, 4), (4, 5): Fr(47, 50),
+                       (5, 4): Fr(-27, 50), (5, 5): Fr(-1, 4)}),
 }
 
 
@@ -115,7 +125,7 @@ def closure(order):
     """Upper-left block Mc (b x b) of M = H D+ and the boundary weights w_0..w_{b-1}.
 
     Unknowns: Mc[i][j] (i, j < b) and w_i.  Equations, for closure rows i < b and
-    degrees m = 0..p (p = order/2), on unit spacing xi_j = j:
+    degrees m = 0..p (p = floor(order/2)), on unit spacing xi_j = j:
       D+ rows:  sum_j M[i, j] j^m            = m w_i i^(m-1)
       D- rows:  sum_j (B - M^T)[i, j] j^m    = m w_i i^(m-1)
     plus one equation per free parameter of CLOSURE.
@@ -182,7 +192,7 @@ def upwind_pair_exact(order, N):
     H is the list of diagonal weights.  Dp = H^-1 M, Dm = H^-1 (B - M^T).
     """
     if order not in CLOSURE:
-        raise ValueError("closures are built for orders 2, 4, 6")
+        raise ValueError("closures are built for orders 2 to 7")
     if N < min_nodes(order):
         raise ValueError(f"order {order} needs at least {min_nodes(order)} nodes")
     alpha = interior_stencil(order)

@@ -78,7 +78,7 @@ def _exact(order, N):
     return op.upwind_pair_exact(order, N)
 
 
-ORDERS = [2, 4, 6]
+ORDERS = [2, 3, 4, 5, 6, 7]   # even orders as the kernels use them; odd orders of the oracle (Table 1)
 
 
 @pytest.mark.parametrize("order", ORDERS)
@@ -217,3 +217,22 @@ def test_symbol_real_part_dissipative():
         a = op.interior_stencil(order)
         re = sum(float(c) * np.cos(j * k) for j, c in a.items())
         assert re.max() <= 1e-12
+
+
+def test_odd_order_norms_forced_by_accuracy():
+    """Odd orders 3, 5, 7 (Table 1) with b = 2, 4, 6: the boundary weights follow from the
+    closure-row accuracy conditions alone, whatever the free entries (the same values for
+    other choices of them), and order 3 has no free entry."""
+    assert op.CLOSURE[3]["free"] == {}
+    assert op.closure(3)[1] == [Fr(5, 12), Fr(13, 12)]
+    for order, alt in ((5, {(3, 3): Fr(-1, 3)}), (7, {(4, 4): Fr(-27, 100), (4, 5): Fr(91, 100),
+                                                      (5, 4): Fr(-51, 100), (5, 5): Fr(-1, 4)})):
+        w = op.closure(order)[1]
+        saved = op.CLOSURE[order]["free"]
+        try:
+            op.CLOSURE[order]["free"] = alt
+            assert op.closure(order)[1] == w
+        finally:
+            op.CLOSURE[order]["free"] = saved
+        # H integrates constants exactly on unit spacing: the b weights add up to b - 1/2
+        assert sum(w) == len(w) - Fr(1, 2)
