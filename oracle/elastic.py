@@ -38,20 +38,32 @@ over xi and i in Eq. gen_hyp_transformed_discrete_SAT).
 import numpy as np
 
 from .metrics import apply_axis
-from .operators import upwind_pair
+from .operators import traditional_op, upwind_pair
 
 ARRAY_AXIS = (2, 1, 0)   # xi = q, r, s -> array axis
 
 
 class Scheme:
-    """1D operators of one order on each axis of the reference cube [0, 1]^3."""
+    """1D operators of one order on each axis of the reference cube [0, 1]^3.
 
-    def __init__(self, order, nodes):
+    operator: "upwind" (the dual pair D-, D+ of Table 1 with their closures) or "traditional"
+    (the central operator D of Table 2, used as both D- and D+: the scheme the paper compares
+    the upwind one with).
+    """
+
+    def __init__(self, order, nodes, operator="upwind"):
         self.order = order
+        self.operator = operator
         self.nodes = tuple(nodes)        # (nq, nr, ns)
         self.H, self.Dm, self.Dp = [], [], []
         for N in self.nodes:
-            H, Dm, Dp = upwind_pair(order, N)
+            if operator == "upwind":
+                H, Dm, Dp = upwind_pair(order, N)
+            elif operator == "traditional":
+                H, D = traditional_op(order, N)
+                Dm = Dp = D
+            else:
+                raise ValueError(f"unknown operator family {operator!r}")
             self.H.append(H)
             self.Dm.append(Dm)
             self.Dp.append(Dp)

@@ -121,18 +121,12 @@ def _solve_exact(rows, rhs, nunk):
     return u
 
 
-def closure(order):
-    """Upper-left block Mc (b x b) of M = H D+ and the boundary weights w_0..w_{b-1}.
-
-    Unknowns: Mc[i][j] (i, j < b) and w_i.  Equations, for closure rows i < b and
-    degrees m = 0..p (p = floor(order/2)), on unit spacing xi_j = j:
+def _accuracy_system(alpha, b, p):
+    """Linear equations on the unknowns Mc[i][j] (index i b + j) and w_i (index b b + i): for
+    closure rows i < b and degrees m = 0..p, on unit spacing xi_j = j,
       D+ rows:  sum_j M[i, j] j^m            = m w_i i^(m-1)
       D- rows:  sum_j (B - M^T)[i, j] j^m    = m w_i i^(m-1)
-    plus one equation per free parameter of CLOSURE.
-    """
-    alpha = interior_stencil(order)
-    b = CLOSURE[order]["b"]
-    p = order // 2
+    with M equal to the Toeplitz stencil alpha outside the b x b corner block."""
     nunk = b * b + b
 
     def mi(i, j):
@@ -168,14 +162,31 @@ def closure(order):
                 row[wi(i)] -= m * Fr(i) ** (m - 1)
             rows.append(row)
             rhs.append(-const)
-    for (i, j), v in CLOSURE[order]["free"].items():
+    return rows, rhs, nunk
+
+
+def _pin(rows, rhs, b, nunk, free):
+    """Append one equation Mc[i][j] = v per entry of `free`."""
+    for (i, j), v in free.items():
         row = [Fr(0)] * nunk
-        row[mi(i, j)] = Fr(1)
+        row[i * b + j] = Fr(1)
         rows.append(row)
         rhs.append(v)
+
+
+def closure(order):
+    """Upper-left block Mc (b x b) of M = H D+ and the boundary weights w_0..w_{b-1}.
+
+    Unknowns: Mc[i][j] (i, j < b) and w_i.  Equations: the accuracy conditions of the D+ and
+    D- closure rows up to degree p = floor(order/2) (_accuracy_system), plus one equation per
+    free parameter of CLOSURE.
+    """
+    b = CLOSURE[order]["b"]
+    rows, rhs, nunk = _accuracy_system(interior_stencil(order), b, order // 2)
+    _pin(rows, rhs, b, nunk, CLOSURE[order]["free"])
     u = _solve_exact(rows, rhs, nunk)
-    Mc = [[u[mi(i, j)] for j in range(b)] for i in range(b)]
-    w = [u[wi(i)] for i in range(b)]
+    Mc = [[u[i * b + j] for j in range(b)] for i in range(b)]
+    w = [u[b * b + i] for i in range(b)]
     return Mc, w
 
 
@@ -186,18 +197,10 @@ def min_nodes(order):
     return 2 * CLOSURE[order]["b"] + max(r, q)
 
 
-def upwind_pair_exact(order, N):
-    """(H, Dm, Dp, M, B) on N nodes with unit spacing, as lists of Fractions.
-
-    H is the list of diagonal weights.  Dp = H^-1 M, Dm = H^-1 (B - M^T).
-    """
-    if order not in CLOSURE:
-        raise ValueError("closures are built for orders 2 to 7")
-    if N < min_nodes(order):
-        raise ValueError(f"order {order} needs at least {min_nodes(order)} nodes")
-    alpha = interior_stencil(order)
-    b = CLOSURE[order]["b"]
-    Mc, w = closure(order)
+def _assemble_exact(alpha, b, Mc, w, N):
+    """(H, M, B) on N nodes, unit spacing: M is the Toeplitz stencil alpha with the corner block
+    Mc at the upper left and, through M - J M^T J = B, its mirror at the lower right; H holds
+    the weights w at both ends and 1 inside."""
     n = N - 1
     M = [[Fr(0)] * N for _ in range(N)]
     for i in range(N):
@@ -217,6 +220,20 @@ def upwind_pair_exact(order, N):
     for i in range(b):
         H[i] = w[i]
         H[n - i] = w[i]
+    return H, M, Bm
+
+
+def upwind_pair_exact(order, N):
+    """(H, Dm, Dp, M, B) on N nodes with unit spacing, as lists of Fractions.
+
+    H is the list of diagonal weights.  Dp = H^-1 M, Dm = H^-1 (B - M^T).
+    """
+    if order not in CLOSURE:
+        raise ValueError("closures are built for orders 2 to 7")
+    if N < min_nodes(order):
+        raise ValueError(f"order {order} needs at least {min_nodes(order)} nodes")
+    Mc, w = closure(order)
+    H, M, Bm = _assemble_exact(interior_stencil(order), CLOSURE[order]["b"], Mc, w, N)
     Dp = [[M[i][j] / H[i] for j in range(N)] for i in range(N)]
     Dm = [[(Bm[i][j] - M[j][i]) / H[i] for j in range(N)] for i in range(N)]
     return H, Dm, Dp, M, Bm
@@ -263,6 +280,101 @@ def upwind_pair(order, N, length=1.0):
         Hf[i] = float(H0[i])
         Hf[N - 1 - i] = float(H0[i])
     return Hf * h, Dm, Dp
+
+
+# Traditional (central) diagonal-norm SBP operators of Table 2: closure width b and the chosen
+# values of the free entries of M = H D (upper-left block).
+TRADITIONAL = {
+    2: dict(b=1, free={}),
+    4: dict(b=4, free={}),
+    6: dict(b=6, free={(4, 2): Fr(-1, 10)}),
+}
+
+
+def traditional_stencil(order):
+    """Table 2 as a stencil {offset j: coefficient}: (D f)_i = sum_j gamma_j (f_{i+j} - f_{i-j})."""
+    st = {0: Fr(0)}
+    for j, c in enumerate(TABLE2[order], start=1):
+        st[j] = Fr(c)
+        st[-j] = -Fr(c)
+    return st
+
+
+def traditional_closure(order):
+    """Upper-left block Mc (b x b) of M = H D and the weights w_0..w_{b-1} of the traditional
+    operator.
+
+    A central operator is the case D- = D+ = D of the construction above, which asks for
+    M + M^T = B (then H D + D^T H = B, Section 4.1).  Inside, and across the edge of the corner
+    block, the antisymmetric stencil already gives M + M^T = 0, so the conditions are the
+    accuracy equations of _accuracy_system with Table 2's stencil (degree <= floor(order/2)),
+    Mc + Mc^T = diag(-1, 0, ..., 0), and one equation per free entry of TRADITIONAL.
+    """
+    b = TRADITIONAL[order]["b"]
+    rows, rhs, nunk = _accuracy_system(traditional_stencil(order), b, order // 2)
+    for i in range(b):
+        for j in range(i, b):
+            row = [Fr(0)] * nunk
+            row[i * b + j] += 1
+            row[j * b + i] += 1
+            rows.append(row)
+            rhs.append(Fr(-1) if i == j == 0 else Fr(0))
+    _pin(rows, rhs, b, nunk, TRADITIONAL[order]["free"])
+    u = _solve_exact(rows, rhs, nunk)
+    Mc = [[u[i * b + j] for j in range(b)] for i in range(b)]
+    w = [u[b * b + i] for i in range(b)]
+    return Mc, w
+
+
+def traditional_min_nodes(order):
+    """Fewest nodes per axis with disjoint closures (N >= 2b + order/2)."""
+    return 2 * TRADITIONAL[order]["b"] + order // 2
+
+
+def traditional_exact(order, N):
+    """(H, D, M, B) of the traditional operator on N nodes, unit spacing, as Fractions:
+    D = H^-1 M with M + M^T = B."""
+    if order not in TRADITIONAL:
+        raise ValueError("traditional closures are built for orders 2, 4, 6")
+    if N < traditional_min_nodes(order):
+        raise ValueError(f"order {order} needs at least {traditional_min_nodes(order)} nodes")
+    Mc, w = traditional_closure(order)
+    H, M, Bm = _assemble_exact(traditional_stencil(order), TRADITIONAL[order]["b"], Mc, w, N)
+    D = [[M[i][j] / H[i] for j in range(N)] for i in range(N)]
+    return H, D, M, Bm
+
+
+def traditional_op(order, N, length=1.0):
+    """Float64 (H, D) of the traditional operator on N nodes spanning [0, length]; D is a scipy
+    CSR matrix.  Rows within b of x = 0 come from the exact operator on
+    traditional_min_nodes(order) nodes (they do not depend on N), rows within b of the far end
+    from the mirror relation D[N-1-i, N-1-j] = -D[i, j], and Table 2's stencil elsewhere."""
+    import scipy.sparse as sps
+    if N < traditional_min_nodes(order):
+        raise ValueError(f"order {order} needs at least {traditional_min_nodes(order)} nodes")
+    b = TRADITIONAL[order]["b"]
+    H0, D0, _, _ = traditional_exact(order, traditional_min_nodes(order))
+    st = traditional_stencil(order)
+    h = length / (N - 1)
+    ri, ci, vi = [], [], []
+    for i in range(N):
+        if i < b:
+            ent = [(j, D0[i][j]) for j in range(len(D0)) if D0[i][j] != 0]
+        elif i > N - 1 - b:
+            ii = N - 1 - i
+            ent = [(N - 1 - j, -D0[ii][j]) for j in range(len(D0)) if D0[ii][j] != 0]
+        else:
+            ent = [(i + k, a) for k, a in st.items() if a != 0]
+        for j, a in ent:
+            ri.append(i)
+            ci.append(j)
+            vi.append(float(a) / h)
+    D = sps.csr_matrix((vi, (ri, ci)), shape=(N, N))
+    Hf = np.ones(N)
+    for i in range(b):
+        Hf[i] = float(H0[i])
+        Hf[N - 1 - i] = float(H0[i])
+    return Hf * h, D
 
 
 def dispersion_upwind(order, k):

@@ -9,7 +9,7 @@ from oracle import rk
 from oracle.elastic import (Scheme, apply_P, energy, face_penalty, flux, hat_variables,
                             inner_H, rhs, rhs_raw, strain_rows, surface_integral)
 from oracle.metrics import metrics
-from oracle.operators import CLOSURE, TABLE1
+from oracle.operators import CLOSURE, TABLE1, TRADITIONAL
 from oracle.pointwise import PointOracle
 from workloads.fields import gaussian_pulse, random_state, smooth_state
 from workloads.geometry import make_map, node_coordinates
@@ -271,12 +271,12 @@ def _plane_wave(kind, X, t, rho, lam, mu, dvec, pol, wl):
     return v, sig
 
 
-def _mms_error(order, n, kind, T=0.25, bc=None, wl=1.6):
+def _mms_error(order, n, kind, T=0.25, bc=None, wl=1.6, operator="upwind"):
     nodes = (n + 1, n + 1, n + 1)
     fmap = make_map("curvy", (1.0, 1.0, 1.0), eps=0.05)
     X = node_coordinates(fmap, nodes)
     J, a = metrics(*X, order)
-    sch = Scheme(order, nodes)
+    sch = Scheme(order, nodes, operator)
     rho, lam, mu = 1.0, 2.0, 1.0
     mat = tuple(np.full(J.shape, v) for v in (rho, lam, mu))
     dvec = np.array([1.0, 2.0, 2.0]) / 3.0
@@ -345,7 +345,7 @@ def test_plane_wave_convergence_with_free_surfaces(order, kind, lo):
     assert rate > lo, (e1, e2, rate)
 
 
-def _interior_truncation(order, n, kind, mapname, ext=1.0, medium=(1.0, 2.0, 1.0), wl=0.8):
+def _interior_truncation(order, n, kind, mapname, ext=1.0, medium=(1.0, 2.0, 1.0), wl=0.8, operator="upwind"):
     """max |dQ/dt_h(Q) - dQ/dt| / max |dQ/dt| for the exact plane wave of _plane_wave at t = 0,
     over the nodes at least b + max(r, q) from every face: there every row is the interior
     stencil of Table 1 applied to metrics formed by interior rows (the closure rows, their
@@ -367,9 +367,12 @@ def _interior_truncation(order, n, kind, mapname, ext=1.0, medium=(1.0, 2.0, 1.0
     S = lam * np.trace(E) * np.eye(3) + 2 * mu * E
     Sv = (S[0, 0], S[1, 1], S[2, 2], S[0, 1], S[0, 2], S[1, 2])
     Qt = np.stack([c * c * pol[i] * F2 for i in range(3)] + [-c * sv * F2 for sv in Sv])
-    R = rhs(np.stack(v + s), Scheme(order, nodes), J, a, mat, [("char", 0.0)] * 6)
-    r, q, _ = TABLE1[order]
-    m = CLOSURE[order]["b"] + max(r, q)
+    R = rhs(np.stack(v + s), Scheme(order, nodes, operator), J, a, mat, [("char", 0.0)] * 6)
+    if operator == "upwind":
+        r, q, _ = TABLE1[order]
+        m = CLOSURE[order]["b"] + max(r, q)
+    else:
+        m = TRADITIONAL[order]["b"] + order // 2
     inner = (slice(None),) + (slice(m, n + 1 - m),) * 3
     return np.abs(R - Qt)[inner].max() / np.abs(Qt).max()
 
