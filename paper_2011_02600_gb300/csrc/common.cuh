@@ -65,8 +65,11 @@ struct StageArgs {
   static __constant__ float kDpF##O[B][CW] = SBP_DP##O##_ROWS;         \
   static __constant__ float kDmF##O[B][CW] = SBP_DM##O##_ROWS;
 SBP_DECLARE_TABLES(2, 2, 4)
+SBP_DECLARE_TABLES(3, 2, 4)
 SBP_DECLARE_TABLES(4, 4, 7)
+SBP_DECLARE_TABLES(5, 4, 7)
 SBP_DECLARE_TABLES(6, 6, 10)
+SBP_DECLARE_TABLES(7, 6, 10)
 #undef SBP_DECLARE_TABLES
 
 template <typename T, int O>
@@ -78,11 +81,17 @@ struct Tab;
     __device__ __forceinline__ static T m(int i, int c) { return kDm##SUF##O[i][c]; }   \
   };
 SBP_TAB(double, D, 2)
+SBP_TAB(double, D, 3)
 SBP_TAB(double, D, 4)
+SBP_TAB(double, D, 5)
 SBP_TAB(double, D, 6)
+SBP_TAB(double, D, 7)
 SBP_TAB(float, F, 2)
+SBP_TAB(float, F, 3)
 SBP_TAB(float, F, 4)
+SBP_TAB(float, F, 5)
 SBP_TAB(float, F, 6)
+SBP_TAB(float, F, 7)
 #undef SBP_TAB
 
 // Row `pos` of D+ (PLUS) or D- on N nodes, unit spacing, applied through

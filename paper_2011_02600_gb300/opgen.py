@@ -5,19 +5,20 @@ Run ``python -m paper_2011_02600_gb300.opgen`` to rewrite
 this script.
 
 What it derives (Section 4.1 and Table 1 of Duru, Fung & Williams): for the
-interior orders 2, 4 and 6, the upwind dual pair (H, D-, D+) whose interior
+interior orders 2 to 7, the upwind dual pair (H, D-, D+) whose interior
 rows are Table 1's stencil alpha_j (D+) and its mirror beta_j = -alpha_{-j}
 (D-), and whose b closure rows at each end make
 
-  * D+ and D- exact for polynomials of degree <= order/2 in every row, and
+  * D+ and D- exact for polynomials of degree <= floor(order/2) in every row, and
   * H D+ + D-^T H = diag(-1, 0, ..., 0, 1)   (the SBP dual-pair relation),
 
 with D- the index-reversed negative of D+.  Writing P = H D+, only the
 upper-left b x b block of P and the first b entries of H are unknown.  The
-accuracy equations leave free entries (none for order 2, one for order 4,
-four for order 6); they are pinned to the values in FREE_ENTRIES, which keep
-P + P^T - B negative semi-definite and the spectral radius of D+ at that of
-the interior stencil.
+accuracy equations leave free entries (none for orders 2 and 3, one for orders
+4 and 5, four for orders 6 and 7); they are pinned to the values in
+FREE_ENTRIES, which keep P + P^T - B negative semi-definite and the spectral
+radius of D+ small.  The kernels are launched for orders 2, 4 and 6; the odd
+orders' tables are there for the kernel source's CPU checks.
 
 This module is independent of any other implementation of the operators in
 the repository: it carries its own statement of Table 1 and its own exact
@@ -29,18 +30,26 @@ from fractions import Fraction
 # Table 1 rows used by the kernels: (r, q, alpha_{-r}..alpha_{q}).
 STENCILS = {
     2: (0, 2, [Fraction(-3, 2), Fraction(2), Fraction(-1, 2)]),
+    3: (1, 2, [Fraction(-1, 3), Fraction(-1, 2), Fraction(1), Fraction(-1, 6)]),
     4: (1, 3, [Fraction(-1, 4), Fraction(-5, 6), Fraction(3, 2), Fraction(-1, 2), Fraction(1, 12)]),
+    5: (2, 3, [Fraction(1, 20), Fraction(-1, 2), Fraction(-1, 3), Fraction(1), Fraction(-1, 4), Fraction(1, 30)]),
     6: (2, 4, [Fraction(1, 30), Fraction(-2, 5), Fraction(-7, 12), Fraction(4, 3), Fraction(-1, 2),
                Fraction(2, 15), Fraction(-1, 60)]),
+    7: (3, 4, [Fraction(-1, 105), Fraction(1, 10), Fraction(-3, 5), Fraction(-1, 4), Fraction(1),
+               Fraction(-3, 10), Fraction(1, 15), Fraction(-1, 140)]),
 }
-BLOCK = {2: 2, 4: 4, 6: 6}
+BLOCK = {2: 2, 3: 2, 4: 4, 5: 4, 6: 6, 7: 6}
 # (row, col) of P = H D+ in the upper-left block -> fixed value
 FREE_ENTRIES = {
     2: {},
+    3: {},
     4: {(3, 3): Fraction(-4, 5)},
+    5: {(3, 3): Fraction(-3, 8)},
     6: {(4, 4): Fraction(-17, 25), (4, 5): Fraction(131, 100), (5, 4): Fraction(-29, 100),
         (5, 5): Fraction(-3, 5)},
+    7: {(4, 4): Fraction(-1, 4), (4, 5): Fraction(47, 50), (5, 4): Fraction(-27, 50), (5, 5): Fraction(-1, 4)},
 }
+ORDERS = (2, 3, 4, 5, 6, 7)
 
 
 def _rref_solve(eqs, names):
@@ -136,12 +145,12 @@ def _lit(x):
 
 
 def render():
-    out = ["// Upwind SBP dual-pair coefficients (orders 2, 4, 6) for the CUDA kernels.",
+    out = ["// Upwind SBP dual-pair coefficients (orders 2 to 7) for the CUDA kernels.",
            "// Generated by paper_2011_02600_gb300/opgen.py from Table 1 of arXiv 2011.02600 and the",
            "// closure conditions stated there; do not edit by hand.",
            "#pragma once", "", "#ifndef __CUDACC__", "#define __host__", "#define __device__", "#endif", "",
            "namespace sbp {", "", "template <int ORDER> struct OpCoef;", ""]
-    for order in (2, 4, 6):
+    for order in ORDERS:
         b, r, q, alpha, w, dp, dm = derive(order)
         cw = b + q
         out.append(f"template <> struct OpCoef<{order}> {{")

@@ -33,7 +33,8 @@ static AdjArgs<double> args(int order, int nq, int nr, int ns, const double* met
   A.met = met;
   A.mat = mat;
   const int N[3] = {nq, nr, ns};
-  const double w0 = order == 2 ? OpCoef<2>::w(0) : order == 4 ? OpCoef<4>::w(0) : OpCoef<6>::w(0);
+  const double w0 = order == 2 ? OpCoef<2>::w(0) : order == 3 ? OpCoef<3>::w(0) : order == 4 ? OpCoef<4>::w(0)
+                    : order == 5 ? OpCoef<5>::w(0) : order == 6 ? OpCoef<6>::w(0) : OpCoef<7>::w(0);
   for (int x = 0; x < 3; ++x) {
     A.inv_h[x] = N[x] - 1;
     A.inv_h0[x] = (N[x] - 1) / w0;
@@ -48,8 +49,11 @@ static AdjArgs<double> args(int order, int nq, int nr, int ns, const double* met
 static int dispatch(int order, AdjArgs<double>& A) {
   switch (order) {
     case 2: run<2>(A); return 0;
+    case 3: run<3>(A); return 0;
     case 4: run<4>(A); return 0;
+    case 5: run<5>(A); return 0;
     case 6: run<6>(A); return 0;
+    case 7: run<7>(A); return 0;
     default: return 1;
   }
 }

@@ -53,8 +53,11 @@ static int rhs_order(int order, int nq, int nr, int ns, const T* q, const T* met
                      const double* bc_gamma, T* out) {
   switch (order) {
     case 2: rhs_all<T, 2>(nq, nr, ns, q, met, mat, bc_kind, bc_gamma, out); return 0;
+    case 3: rhs_all<T, 3>(nq, nr, ns, q, met, mat, bc_kind, bc_gamma, out); return 0;
     case 4: rhs_all<T, 4>(nq, nr, ns, q, met, mat, bc_kind, bc_gamma, out); return 0;
+    case 5: rhs_all<T, 5>(nq, nr, ns, q, met, mat, bc_kind, bc_gamma, out); return 0;
     case 6: rhs_all<T, 6>(nq, nr, ns, q, met, mat, bc_kind, bc_gamma, out); return 0;
+    case 7: rhs_all<T, 7>(nq, nr, ns, q, met, mat, bc_kind, bc_gamma, out); return 0;
     default: return 1;
   }
 }
@@ -93,8 +96,11 @@ static double energy_all(int nq, int nr, int ns, const double* q, const double* 
 extern "C" int host_energy(int order, int nq, int nr, int ns, const double* q, const double* mat, double* out) {
   switch (order) {
     case 2: *out = energy_all<2>(nq, nr, ns, q, mat); return 0;
+    case 3: *out = energy_all<3>(nq, nr, ns, q, mat); return 0;
     case 4: *out = energy_all<4>(nq, nr, ns, q, mat); return 0;
+    case 5: *out = energy_all<5>(nq, nr, ns, q, mat); return 0;
     case 6: *out = energy_all<6>(nq, nr, ns, q, mat); return 0;
+    case 7: *out = energy_all<7>(nq, nr, ns, q, mat); return 0;
     default: return 1;
   }
 }

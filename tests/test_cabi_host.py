@@ -89,7 +89,7 @@ def test_generated_coefficients_match_oracle():
     from fractions import Fraction
     from oracle import operators as op
     from paper_2011_02600_gb300 import opgen
-    for order in (2, 4, 6):
+    for order in opgen.ORDERS:
         b, r, q, alpha, w, dp, dm = opgen.derive(order)
         H, Dm, Dp, _, _ = op.upwind_pair_exact(order, op.min_nodes(order))
         assert w == H[:b]

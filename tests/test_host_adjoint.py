@@ -4,7 +4,7 @@ the adjoint Runge-Kutta updates and the material gradient, with their division-f
 as host C++ and runs them over every node, FP64.  Against the oracle:
 
 * L^T equals the transpose of the oracle's assembled operator on a tiny grid, and satisfies
-  <L x, y> = <x, L^T y> with the oracle's L on larger grids, orders 2, 4, 6, every face kind;
+  <L x, y> = <x, L^T y> with the oracle's L on larger grids, orders 2 to 7, every face kind;
 * one adjoint stage updates Ub and Wb as the exact adjoint of the 2N-storage stage prescribes;
 * its material gradient equals dt <Wb_k, d(L U)/dm . dm> with the derivative of the oracle's
   right-hand side taken by the complex step (no cancellation error)."""
@@ -89,7 +89,8 @@ def test_transpose_full_matrix_tiny_grid(hostadj, bcname):
     assert np.abs(LT - Lm.T).max() < 1e-12 * np.abs(Lm).max()
 
 
-@pytest.mark.parametrize("order,nodes", [(2, (12, 9, 8)), (4, (14, 12, 11)), (6, (19, 17, 16))])
+@pytest.mark.parametrize("order,nodes", [(2, (12, 9, 8)), (3, (9, 8, 10)), (4, (14, 12, 11)), (5, (13, 12, 14)),
+                                         (6, (19, 17, 16)), (7, (17, 16, 18))])
 @pytest.mark.parametrize("bcname", sorted(BCS))
 def test_transpose_dot_product(hostadj, order, nodes, bcname):
     X, J, a, mat = _problem(order, nodes, 2)
@@ -105,7 +106,8 @@ def test_transpose_dot_product(hostadj, order, nodes, bcname):
         assert abs(lhs - rhs_) < 1e-12 * scale, (lhs, rhs_, scale)
 
 
-@pytest.mark.parametrize("order,nodes", [(2, (9, 8, 7)), (4, (13, 12, 11)), (6, (17, 16, 18))])
+@pytest.mark.parametrize("order,nodes", [(2, (9, 8, 7)), (3, (8, 9, 7)), (4, (13, 12, 11)), (5, (12, 11, 13)),
+                                         (6, (17, 16, 18)), (7, (16, 18, 17))])
 @pytest.mark.parametrize("bcname", ["char", "mixed"])
 def test_adjoint_stage_updates_and_gradient(hostadj, order, nodes, bcname):
     X, J, a, mat = _problem(order, nodes, 3)

@@ -4,7 +4,8 @@ characteristic penalties, P~) as host C++; its dQ/dt at every node of a curvilin
 random medium and a random state is compared with the oracle's right-hand side (Eq.
 gen_hyp_transformed_discrete_SAT) in FP64.  The metric terms are inputs here (the oracle's,
 Sec. 2.2); the stored coefficients 1/(rho J), lambda/J, mu/J are formed as the library forms
-them."""
+them.  Orders 2 to 7: the kernels are launched for 2, 4 and 6, and the odd orders' tables and
+rows are checked here ahead of their GPU runs."""
 import ctypes
 
 import numpy as np
@@ -56,7 +57,8 @@ def _host_rhs(lib, order, Q, J, a, mat, bc, dtype=np.float64):
     return out
 
 
-@pytest.mark.parametrize("order,nodes", [(2, (9, 7, 8)), (4, (13, 12, 14)), (6, (18, 16, 17))])
+@pytest.mark.parametrize("order,nodes", [(2, (9, 7, 8)), (3, (8, 9, 7)), (4, (13, 12, 14)), (5, (12, 13, 11)), (6, (18, 16, 17)),
+                                         (7, (17, 18, 16))])
 @pytest.mark.parametrize("bcname", sorted(BCS))
 def test_kernel_operator_matches_oracle_fp64(hostop, order, nodes, bcname):
     bc = BCS[bcname]
@@ -76,7 +78,8 @@ def test_kernel_operator_matches_oracle_fp64(hostop, order, nodes, bcname):
     assert err.max() < 1e-12, err
 
 
-@pytest.mark.parametrize("order,nodes", [(2, (9, 7, 8)), (4, (13, 12, 14)), (6, (18, 16, 17))])
+@pytest.mark.parametrize("order,nodes", [(2, (9, 7, 8)), (3, (8, 9, 7)), (4, (13, 12, 14)), (5, (12, 13, 11)), (6, (18, 16, 17)),
+                                         (7, (17, 18, 16))])
 @pytest.mark.parametrize("bcname", sorted(BCS))
 def test_kernel_operator_matches_oracle_fp32(hostop, order, nodes, bcname):
     """The FP32 instantiation (FP32 closure tables, weights and penalty arithmetic) on a smooth
@@ -93,7 +96,8 @@ def test_kernel_operator_matches_oracle_fp32(hostop, order, nodes, bcname):
     assert err.max() < 5e-5, err
 
 
-@pytest.mark.parametrize("order,nodes", [(2, (9, 7, 8)), (4, (13, 12, 14)), (6, (18, 16, 17))])
+@pytest.mark.parametrize("order,nodes", [(2, (9, 7, 8)), (3, (8, 9, 7)), (4, (13, 12, 14)), (5, (12, 13, 11)), (6, (18, 16, 17)),
+                                         (7, (17, 18, 16))])
 def test_kernel_energy_density_matches_oracle(hostop, order, nodes):
     """The energy kernel's per-node density (one division, from the stored 1/(rho J), lambda/J,
     mu/J) and norm weights give the oracle's discrete energy (Eq. physical_energy_discrete with

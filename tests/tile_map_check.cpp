@@ -1,5 +1,6 @@
 // CPU check of the tiled stage kernel's index arithmetic (paper_2011_02600_gb300/csrc/tile_map.cuh,
-// compiled here as host C++) for every grid size in a range, for orders 2, 4 and 6:
+// compiled here as host C++) for every grid size in a range, for orders 2 to 7 (the kernels are
+// launched for 2, 4 and 6; the odd orders are checked ahead of their GPU runs):
 //   * the tiles along q (width TX, origins on 4-node boundaries) and r (width TY) own disjoint
 //     node ranges that cover the axis, and every q origin keeps the tile loads on a 16-byte
 //     boundary;
@@ -53,6 +54,18 @@ template <> struct Closure<4> {
 template <> struct Closure<6> {
   static constexpr double P[6][10] = SBP_DP6_ROWS;
   static constexpr double M[6][10] = SBP_DM6_ROWS;
+};
+template <> struct Closure<3> {
+  static constexpr double P[2][4] = SBP_DP3_ROWS;
+  static constexpr double M[2][4] = SBP_DM3_ROWS;
+};
+template <> struct Closure<5> {
+  static constexpr double P[4][7] = SBP_DP5_ROWS;
+  static constexpr double M[4][7] = SBP_DM5_ROWS;
+};
+template <> struct Closure<7> {
+  static constexpr double P[6][10] = SBP_DP7_ROWS;
+  static constexpr double M[6][10] = SBP_DM7_ROWS;
 };
 
 // Row i of D+ (plus) or D- on n nodes as a dense vector: the closure rows within b of the
@@ -303,8 +316,11 @@ int main() {
   for (int n = 1; n <= 400; ++n) sizes.push_back(n);
   for (int n : {511, 512, 513, 1023, 1024, 1025, 1026, 1029, 2049, 4097}) sizes.push_back(n);
   check_order<2>(sizes);
+  check_order<3>(sizes);
   check_order<4>(sizes);
+  check_order<5>(sizes);
   check_order<6>(sizes);
+  check_order<7>(sizes);
   for (int nbx = 1; nbx <= 70; ++nbx)
     for (int nby = 1; nby <= 140; ++nby) check_swizzle(nbx, nby);
   if (failures) {
