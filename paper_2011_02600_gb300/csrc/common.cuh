@@ -58,7 +58,8 @@ struct StageArgs {
   double* grad;         // gradient accumulators (FP64, 3 fields)
 };
 
-// Closure rows of D+ and D- (unit spacing), one private copy per translation unit.
+// Closure rows of D+ and D- (unit spacing), one private copy per translation unit; orders
+// kTraditional + 2, 4, 6 are Table 2's central operators (both tables hold D).
 #define SBP_DECLARE_TABLES(O, B, CW)                                   \
   static __constant__ double kDpD##O[B][CW] = SBP_DP##O##_ROWS;        \
   static __constant__ double kDmD##O[B][CW] = SBP_DM##O##_ROWS;        \
@@ -70,6 +71,9 @@ SBP_DECLARE_TABLES(4, 4, 7)
 SBP_DECLARE_TABLES(5, 4, 7)
 SBP_DECLARE_TABLES(6, 6, 10)
 SBP_DECLARE_TABLES(7, 6, 10)
+SBP_DECLARE_TABLES(102, 1, 3)
+SBP_DECLARE_TABLES(104, 4, 6)
+SBP_DECLARE_TABLES(106, 6, 9)
 #undef SBP_DECLARE_TABLES
 
 template <typename T, int O>
@@ -92,6 +96,12 @@ SBP_TAB(float, F, 4)
 SBP_TAB(float, F, 5)
 SBP_TAB(float, F, 6)
 SBP_TAB(float, F, 7)
+SBP_TAB(double, D, 102)
+SBP_TAB(double, D, 104)
+SBP_TAB(double, D, 106)
+SBP_TAB(float, F, 102)
+SBP_TAB(float, F, 104)
+SBP_TAB(float, F, 106)
 #undef SBP_TAB
 
 // Row `pos` of D+ (PLUS) or D- on N nodes, unit spacing, applied through

@@ -209,10 +209,11 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
     }
     const Stage<T>& st = S.st[sidx];
     FluxTiles<T>& F = S.f[sidx];
-    // fluxes on the tile and its halo: F_q at columns -Q..TX-1+R, F_r at rows -Q..TY-1+R
-    for (int t = tid; t < TY * (Q + R + TX); t += TX * TY) {
-      const int row = t / (Q + R + TX);
-      const int cc = HX - Q + t % (Q + R + TX);
+    // fluxes on the tile and its halo: F_q at columns -QF..TX-1+R, F_r at rows -QF..TY-1+R
+    constexpr int QF = flux_halo<O>();
+    for (int t = tid; t < TY * (QF + R + TX); t += TX * TY) {
+      const int row = t / (QF + R + TX);
+      const int cc = HX - QF + t % (QF + R + TX);
       const T a[3] = {st.aq[0][row][cc], st.aq[1][row][cc], st.aq[2][row][cc]};
       T s[6];
 #pragma unroll
@@ -222,9 +223,9 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
 #pragma unroll
       for (int c = 0; c < 3; ++c) F.fq[c][row][cc] = Fv[c];
     }
-    for (int t = tid; t < TX * (Q + R + TY); t += TX * TY) {
+    for (int t = tid; t < TX * (QF + R + TY); t += TX * TY) {
       const int cl = t % TX;
-      const int rr = HX - Q + t / TX;
+      const int rr = HX - QF + t / TX;
       const T a[3] = {st.ar[0][rr][cl], st.ar[1][rr][cl], st.ar[2][rr][cl]};
       T s[6];
 #pragma unroll

@@ -54,6 +54,13 @@ __device__ __forceinline__ void swizzle_tiles(int lin, int nbx, int nby, int& bx
 
 constexpr int kMaxCW = 10;  // widest closure row (order 6)
 
+// Halo on the low side over which the kernel forms the q and r fluxes: the interior stencil's
+// reach q for the upwind operators; the whole loaded halo HX for the central operators
+// (OpCoef<kTraditional + order>), where the last tile along an axis can own closure rows that
+// reach node 0 from an origin beyond q.
+template <int O>
+__host__ __device__ constexpr int flux_halo() { return O > kTraditional ? HX : OpCoef<O>::q; }
+
 // Per-thread q rows of a tile that owns closure nodes: the smem column of tap 0 for
 // D- (of the flux tile) and D+ (of the state tile) and the weights of kMaxCW taps.
 template <typename T>
@@ -68,7 +75,7 @@ struct QRows {
 // starting at a shared-memory column: the closure row (the cw nodes nearest the face)
 // for a node within b of a q face, the interior stencil otherwise, zero weights for a
 // column the tile does not own ([own0, own1)).  Every tap lies in the computed flux
-// columns [HX-Q, HX+TX+R) and state columns [0, BXH).
+// columns [HX - flux_halo, HX+TX+R) and state columns [0, BXH).
 template <typename T, int O>
 __device__ __forceinline__ void fill_q_rows(QRows<T>& Qr, int tx, int i0, int own0, int own1, int nq) {
   using C = OpCoef<O>;

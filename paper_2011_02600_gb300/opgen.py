@@ -51,6 +51,16 @@ FREE_ENTRIES = {
 }
 ORDERS = (2, 3, 4, 5, 6, 7)
 
+# Table 2 (the traditional central operators): gamma_1..gamma_p, (D f)_i = sum_j gamma_j (f_{i+j} - f_{i-j}).
+CENTRAL = {
+    2: [Fraction(1, 2)],
+    4: [Fraction(2, 3), Fraction(-1, 12)],
+    6: [Fraction(3, 4), Fraction(-3, 20), Fraction(1, 60)],
+}
+CENTRAL_BLOCK = {2: 1, 4: 4, 6: 6}
+CENTRAL_FREE = {2: {}, 4: {}, 6: {(4, 2): Fraction(-1, 10)}}
+TRADITIONAL = 100   # OpCoef<TRADITIONAL + order>: the traditional operator of that order
+
 
 def _rref_solve(eqs, names):
     """eqs: list of (dict name->coef, rhs).  Returns dict name->value; raises if not unique."""
@@ -87,11 +97,23 @@ def _rref_solve(eqs, names):
 
 
 def derive(order):
-    """(b, alpha dict, H weights w[0..b-1], Dplus rows [b][b+q], Dminus rows [b][b+q])."""
-    r, q, coeffs = STENCILS[order]
-    alpha = {j: a for j, a in zip(range(-r, q + 1), coeffs)}
-    b = BLOCK[order]
-    p = order // 2
+    """(b, r, q, alpha dict, H weights w[0..b-1], Dplus rows [b][b+q], Dminus rows [b][b+q]).
+
+    order > TRADITIONAL: the traditional operator of order - TRADITIONAL (Table 2), the case
+    D- = D+ = D: its antisymmetric stencil, and P + P^T = B on the corner block added to the
+    accuracy equations (then H D + D^T H = B)."""
+    central = order > TRADITIONAL
+    if central:
+        o = order - TRADITIONAL
+        r = q = o // 2
+        alpha = {0: Fraction(0)}
+        for j, g in enumerate(CENTRAL[o], start=1):
+            alpha[j], alpha[-j] = g, -g
+        b, p, free = CENTRAL_BLOCK[o], o // 2, CENTRAL_FREE[o]
+    else:
+        r, q, coeffs = STENCILS[order]
+        alpha = {j: a for j, a in zip(range(-r, q + 1), coeffs)}
+        b, p, free = BLOCK[order], order // 2, FREE_ENTRIES[order]
     P = {(i, j): f"P{i}_{j}" for i in range(b) for j in range(b)}
     W = [f"w{i}" for i in range(b)]
 
@@ -123,11 +145,18 @@ def derive(order):
                 else:
                     known -= val * Fraction(j) ** m
             eqs.append((c, -known))
-    for (i, j), v in FREE_ENTRIES[order].items():
+    if central:
+        for i in range(b):
+            for j in range(i, b):
+                c = {P[(i, j)]: Fraction(1)}
+                c[P[(j, i)]] = c.get(P[(j, i)], 0) + Fraction(1)
+                eqs.append((c, Fraction(-1) if i == j == 0 else Fraction(0)))
+    for (i, j), v in free.items():
         eqs.append(({P[(i, j)]: Fraction(1)}, v))
     sol = _rref_solve(eqs, list(P.values()) + W)
     w = [sol[n] for n in W]
-    cw = b + q
+    cw = max(b + q, r + q + 1)   # closure rows reach b + q nodes; the kernels' q rows need
+    # a window as wide as the interior stencil too (wider only for the order-2 central operator)
     dplus = [[Fraction(0)] * cw for _ in range(b)]
     dminus = [[Fraction(0)] * cw for _ in range(b)]
     for i in range(b):
@@ -145,17 +174,23 @@ def _lit(x):
 
 
 def render():
-    out = ["// Upwind SBP dual-pair coefficients (orders 2 to 7) for the CUDA kernels.",
+    out = ["// Upwind SBP dual-pair coefficients (orders 2 to 7) and the traditional central operators",
+           "// (orders 2, 4, 6; OpCoef<kTraditional + order>, D- = D+) for the CUDA kernels.",
            "// Generated by paper_2011_02600_gb300/opgen.py from Table 1 of arXiv 2011.02600 and the",
            "// closure conditions stated there; do not edit by hand.",
            "#pragma once", "", "#ifndef __CUDACC__", "#define __host__", "#define __device__", "#endif", "",
-           "namespace sbp {", "", "template <int ORDER> struct OpCoef;", ""]
-    for order in ORDERS:
+           "namespace sbp {", "", "template <int ORDER> struct OpCoef;", "",
+           f"constexpr int kTraditional = {TRADITIONAL};  // OpCoef<kTraditional + order>: Table 2's operator", ""]
+    for order in ORDERS + tuple(TRADITIONAL + o for o in sorted(CENTRAL)):
         b, r, q, alpha, w, dp, dm = derive(order)
-        cw = b + q
+        cw = len(dp[0])
         out.append(f"template <> struct OpCoef<{order}> {{")
         out.append(f"  static constexpr int b = {b}, r = {r}, q = {q}, cw = {cw};")
-        out.append(f"  // interior D+ stencil alpha_j, j = -r..q (Table 1); 0 outside")
+        if order > TRADITIONAL:
+            out.append(f"  // traditional operator of order {order - TRADITIONAL}: central stencil alpha_j = -alpha_-j"
+                       " (Table 2), D- = D+")
+        else:
+            out.append(f"  // interior D+ stencil alpha_j, j = -r..q (Table 1); 0 outside")
         expr = " : ".join(f"j == {j} ? {_lit(alpha[j])}" for j in range(-r, q + 1)) + " : 0.0"
         out.append(f"  __host__ __device__ static constexpr double alpha(int j) {{ return {expr}; }}")
         out.append("  // diagonal norm weights w_0..w_{b-1} (H = h diag(w, 1, ..., 1, reversed w)); 1 inside")

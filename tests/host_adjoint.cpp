@@ -34,7 +34,9 @@ static AdjArgs<double> args(int order, int nq, int nr, int ns, const double* met
   A.mat = mat;
   const int N[3] = {nq, nr, ns};
   const double w0 = order == 2 ? OpCoef<2>::w(0) : order == 3 ? OpCoef<3>::w(0) : order == 4 ? OpCoef<4>::w(0)
-                    : order == 5 ? OpCoef<5>::w(0) : order == 6 ? OpCoef<6>::w(0) : OpCoef<7>::w(0);
+                    : order == 5 ? OpCoef<5>::w(0) : order == 6 ? OpCoef<6>::w(0) : order == 7 ? OpCoef<7>::w(0)
+                    : order == kTraditional + 2 ? OpCoef<kTraditional + 2>::w(0)
+                    : order == kTraditional + 4 ? OpCoef<kTraditional + 4>::w(0) : OpCoef<kTraditional + 6>::w(0);
   for (int x = 0; x < 3; ++x) {
     A.inv_h[x] = N[x] - 1;
     A.inv_h0[x] = (N[x] - 1) / w0;
@@ -54,6 +56,9 @@ static int dispatch(int order, AdjArgs<double>& A) {
     case 5: run<5>(A); return 0;
     case 6: run<6>(A); return 0;
     case 7: run<7>(A); return 0;
+    case kTraditional + 2: run<kTraditional + 2>(A); return 0;
+    case kTraditional + 4: run<kTraditional + 4>(A); return 0;
+    case kTraditional + 6: run<kTraditional + 6>(A); return 0;
     default: return 1;
   }
 }

@@ -58,6 +58,9 @@ static int rhs_order(int order, int nq, int nr, int ns, const T* q, const T* met
     case 5: rhs_all<T, 5>(nq, nr, ns, q, met, mat, bc_kind, bc_gamma, out); return 0;
     case 6: rhs_all<T, 6>(nq, nr, ns, q, met, mat, bc_kind, bc_gamma, out); return 0;
     case 7: rhs_all<T, 7>(nq, nr, ns, q, met, mat, bc_kind, bc_gamma, out); return 0;
+    case kTraditional + 2: rhs_all<T, kTraditional + 2>(nq, nr, ns, q, met, mat, bc_kind, bc_gamma, out); return 0;
+    case kTraditional + 4: rhs_all<T, kTraditional + 4>(nq, nr, ns, q, met, mat, bc_kind, bc_gamma, out); return 0;
+    case kTraditional + 6: rhs_all<T, kTraditional + 6>(nq, nr, ns, q, met, mat, bc_kind, bc_gamma, out); return 0;
     default: return 1;
   }
 }
@@ -101,6 +104,9 @@ extern "C" int host_energy(int order, int nq, int nr, int ns, const double* q, c
     case 5: *out = energy_all<5>(nq, nr, ns, q, mat); return 0;
     case 6: *out = energy_all<6>(nq, nr, ns, q, mat); return 0;
     case 7: *out = energy_all<7>(nq, nr, ns, q, mat); return 0;
+    case kTraditional + 2: *out = energy_all<kTraditional + 2>(nq, nr, ns, q, mat); return 0;
+    case kTraditional + 4: *out = energy_all<kTraditional + 4>(nq, nr, ns, q, mat); return 0;
+    case kTraditional + 6: *out = energy_all<kTraditional + 6>(nq, nr, ns, q, mat); return 0;
     default: return 1;
   }
 }

@@ -129,3 +129,19 @@ def test_energy_noalloc_rejects_bad_arguments_on_the_host(lib):
     _expect(1, L.sbp_energy_noalloc, q, mat, nodes, ldq, 1 << 31, 6, 32, 0, None)     # field stride >= 2^31
     _expect(1, L.sbp_energy_noalloc, q, mat, nodes, ldq, fs, 6, 32, 4097, None)       # beyond the static scratch
     _expect(1, L.sbp_energy_noalloc, q, mat, nodes, ldq, fs, 6, 32, -1, None)
+
+
+def test_generated_traditional_coefficients_match_oracle():
+    """The kernel header's traditional operators (OpCoef<kTraditional + order>, package generator)
+    equal the oracle's (independent derivation): norm, and both closure tables equal to D."""
+    from oracle import operators as op
+    from paper_2011_02600_gb300 import opgen
+    for order in (2, 4, 6):
+        b, r, q, alpha, w, dp, dm = opgen.derive(opgen.TRADITIONAL + order)
+        N = op.traditional_min_nodes(order) + 3
+        H, D, _, _ = op.traditional_exact(order, N)
+        assert w == H[:b] and dp == dm
+        for i in range(b):
+            for j in range(len(dp[i])):
+                assert dp[i][j] == D[i][j]
+        assert alpha == op.traditional_stencil(order)

@@ -142,3 +142,20 @@ def test_adjoint_stage_updates_and_gradient(hostadj, order, nodes, bcname):
         want = dt * float(np.sum(Wk * dLU))
         got = float(sum(np.sum(grad[f] * dm[f]) for f in range(3)))
         assert abs(got - want) < 1e-11 * abs(want), (got, want)
+
+
+@pytest.mark.parametrize("order,nodes", [(2, (7, 6, 8)), (4, (12, 11, 13)), (6, (16, 17, 18))])
+@pytest.mark.parametrize("bcname", sorted(BCS))
+def test_traditional_transpose_dot_product(hostadj, order, nodes, bcname):
+    """The adjoint bodies with the traditional operators (OpCoef<kTraditional + order>) satisfy
+    <L x, y> = <x, L^T y> with the oracle's traditional scheme."""
+    from paper_2011_02600_gb300.opgen import TRADITIONAL
+    X, J, a, mat = _problem(order, nodes, 4)
+    bc = BCS[bcname]
+    sch = Scheme(order, nodes, "traditional")
+    x = random_state(nodes, 70, 1.0, 1.0)
+    y = random_state(nodes, 71, 1.0, 1.0)
+    Lx = rhs(x, sch, J, a, mat, bc)
+    LTy = _LT(hostadj, TRADITIONAL + order, J, a, mat, bc, y)
+    lhs, rhs_ = float(np.sum(Lx * y)), float(np.sum(x * LTy))
+    assert abs(lhs - rhs_) < 1e-12 * float(np.sum(np.abs(Lx * y))), (lhs, rhs_)

@@ -115,3 +115,29 @@ def test_kernel_energy_density_matches_oracle(hostop, order, nodes):
                               ctypes.addressof(got)) == 0
     want = energy(Q, Scheme(order, nodes), J, (rho, lam, mu))
     assert abs(got.value - want) < 1e-12 * want, (got.value, want)
+
+
+@pytest.mark.parametrize("order,nodes", [(2, (7, 6, 8)), (4, (12, 11, 13)), (6, (16, 17, 18))])
+@pytest.mark.parametrize("bcname", sorted(BCS))
+def test_traditional_operator_matches_oracle_fp64(hostop, order, nodes, bcname):
+    """The traditional operators of Table 2 (OpCoef<kTraditional + order>, D- = D+ = D) through the
+    same kernel source, against the oracle's traditional scheme, and its energy."""
+    from paper_2011_02600_gb300.opgen import TRADITIONAL
+    bc = BCS[bcname]
+    X = node_coordinates(make_map("curvy", (1000.0, 1100.0, 900.0)), nodes)
+    J, a = metrics(*X, order)
+    mat = make_medium("smooth_gradient", Lz=900.0)(*X)
+    Q = random_state(nodes, 41 + order, 1.0, 1.0e6)
+    sch = Scheme(order, nodes, "traditional")
+    got = _host_rhs(hostop, TRADITIONAL + order, Q, J, a, mat, bc)
+    want = rhs(Q, sch, J, a, mat, bc)
+    err = np.abs(got - want).max(axis=(1, 2, 3)) / np.abs(want).max(axis=(1, 2, 3))
+    assert err.max() < 1e-12, err
+    rho, lam, mu = mat
+    coef = np.ascontiguousarray(np.stack([1.0 / (rho * J), lam / J, mu / J]))
+    Qc = np.ascontiguousarray(Q)
+    e = ctypes.c_double()
+    assert hostop.host_energy(TRADITIONAL + order, *nodes, Qc.ctypes.data, coef.ctypes.data,
+                              ctypes.addressof(e)) == 0
+    want_e = energy(Q, sch, J, mat)
+    assert abs(e.value - want_e) < 1e-12 * want_e

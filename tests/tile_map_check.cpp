@@ -1,6 +1,7 @@
 // CPU check of the tiled stage kernel's index arithmetic (paper_2011_02600_gb300/csrc/tile_map.cuh,
-// compiled here as host C++) for every grid size in a range, for orders 2 to 7 (the kernels are
-// launched for 2, 4 and 6; the odd orders are checked ahead of their GPU runs):
+// compiled here as host C++) for every grid size in a range, for the upwind orders 2 to 7 and the
+// traditional operators of orders 2, 4, 6 (the kernels are launched for the upwind orders 2, 4
+// and 6; the others are checked ahead of their GPU runs):
 //   * the tiles along q (width TX, origins on 4-node boundaries) and r (width TY) own disjoint
 //     node ranges that cover the axis, and every q origin keeps the tile loads on a 16-byte
 //     boundary;
@@ -67,6 +68,18 @@ template <> struct Closure<7> {
   static constexpr double P[6][10] = SBP_DP7_ROWS;
   static constexpr double M[6][10] = SBP_DM7_ROWS;
 };
+template <> struct Closure<102> {
+  static constexpr double P[1][3] = SBP_DP102_ROWS;
+  static constexpr double M[1][3] = SBP_DM102_ROWS;
+};
+template <> struct Closure<104> {
+  static constexpr double P[4][6] = SBP_DP104_ROWS;
+  static constexpr double M[4][6] = SBP_DM104_ROWS;
+};
+template <> struct Closure<106> {
+  static constexpr double P[6][9] = SBP_DP106_ROWS;
+  static constexpr double M[6][9] = SBP_DM106_ROWS;
+};
 
 // Row i of D+ (plus) or D- on n nodes as a dense vector: the closure rows within b of the
 // q = 0 face, at the far face D+[n-1-i][n-1-j] = -D-[i][j] and D-[n-1-i][n-1-j] = -D+[i][j],
@@ -106,7 +119,7 @@ void check_partition(int n, int w, int align, const char* axis) {
 template <typename T, int O>
 void check_q_rows(int n) {
   using C = OpCoef<O>;
-  constexpr int CW = C::cw, Q = C::q, R = C::r;
+  constexpr int CW = C::cw, R = C::r;
   const int nt = (n + TX - 1) / TX;
   static QRows<T> Qr;
   for (int t = 0; t < nt; ++t) {
@@ -114,7 +127,8 @@ void check_q_rows(int n) {
     for (int tx = 0; tx < TX; ++tx) {
       fill_q_rows<T, O>(Qr, tx, a.origin, a.own0, a.own1, n);
       const int bm = Qr.bm[tx], bp = Qr.bp[tx];
-      CHECK(bm >= HX - Q && bm + CW <= HX + TX + R, "q n=%d O=%d tile %d tx %d: D- taps [%d, %d) outside the flux columns",
+      CHECK(bm >= HX - flux_halo<O>() && bm + CW <= HX + TX + R,
+            "q n=%d O=%d tile %d tx %d: D- taps [%d, %d) outside the flux columns",
             n, O, t, tx, bm, bm + CW);
       CHECK(bp >= 0 && bp + CW <= BXH, "q n=%d O=%d tile %d tx %d: D+ taps [%d, %d) outside the state columns", n, O, t, tx,
             bp, bp + CW);
@@ -163,7 +177,7 @@ void check_r_taps(int n) {
           if (plus)
             CHECK(s >= 0 && s < BYH, "r n=%d O=%d node %d: D+ tap at node %d outside the state rows", n, O, j, c);
           else
-            CHECK(s >= HX - C::q && s < HX + TY + C::r, "r n=%d O=%d node %d: D- tap at node %d outside the flux rows", n,
+            CHECK(s >= HX - flux_halo<O>() && s < HX + TY + C::r, "r n=%d O=%d node %d: D- tap at node %d outside the flux rows", n,
                   O, j, c);
         }
       }
@@ -321,6 +335,9 @@ int main() {
   check_order<5>(sizes);
   check_order<6>(sizes);
   check_order<7>(sizes);
+  check_order<kTraditional + 2>(sizes);
+  check_order<kTraditional + 4>(sizes);
+  check_order<kTraditional + 6>(sizes);
   for (int nbx = 1; nbx <= 70; ++nbx)
     for (int nby = 1; nby <= 140; ++nby) check_swizzle(nbx, nby);
   if (failures) {
