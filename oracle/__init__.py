@@ -11,11 +11,16 @@ both sides use is the seeded input generators in ``workloads/``, which hold
 none of the method's arithmetic.
 
 Modules
-  operators  exact rational upwind SBP dual pairs (Section 4.1, Table 1)
+  operators  exact rational upwind SBP dual pairs of orders 2 to 7 (Section 4.1,
+             Table 1) and the traditional central operators of orders 2, 4, 6
+             (Table 2)
   rk         Carpenter-Kennedy 2N-storage RK4 (cited in Sections 1 and 7)
   metrics    Jacobian and metric terms (Section 2.2)
   elastic    semi-discrete RHS, SATs, energy, boundary terms (Sections 4-5,
-             Appendix A)
+             Appendix A), on either operator family
+  pointwise  the same right-hand side at single nodes (sampled checks of large grids)
+  adjoint    receiver misfit, complex-step derivatives, assembled operator
+  surrogate_net  the surrogate network in FP64 (with optional BF16 rounding points)
   source     discrete moment-tensor point source (Section 7.1)
   solver     time loop, receivers, energy history
 
