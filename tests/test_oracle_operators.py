@@ -236,3 +236,28 @@ def test_odd_order_norms_forced_by_accuracy():
             op.CLOSURE[order]["free"] = saved
         # H integrates constants exactly on unit spacing: the b weights add up to b - 1/2
         assert sum(w) == len(w) - Fr(1, 2)
+
+
+def test_group_velocity_and_spurious_modes():
+    """Section 6.2's observations on d omega / dk (negative slope = a spurious unresolved mode
+    travelling the wrong way), from Table 1 and Table 2:
+    * upwind orders 2 and 4: d omega/dk >= 0 on [0, pi]; order 6 nearly so (minimum -0.15,
+      near k = 0.9 pi);
+    * odd upwind orders 3, 5, 7, 9 and order 8: clearly negative somewhere (minimum <= -0.2);
+    * traditional orders 2 to 8: d omega/dk down to -1 or below, negative on 35-50 % of the
+      spectrum (exactly half for order 2, omega = sin k)."""
+    k = np.linspace(0, np.pi, 200001)
+    dk = k[1] - k[0]
+
+    def min_slope(w):
+        return (np.diff(w) / dk).min()
+    assert min_slope(op.dispersion_upwind(2, k)) >= -1e-9
+    assert min_slope(op.dispersion_upwind(4, k)) >= -1e-9
+    assert -0.2 < min_slope(op.dispersion_upwind(6, k)) < 0
+    for order in (3, 5, 7, 8, 9):
+        assert min_slope(op.dispersion_upwind(order, k)) < -0.2, order
+    for order in (2, 4, 6, 8):
+        w = op.dispersion_traditional(order, k)
+        frac = np.mean(np.diff(w) < 0)
+        assert min_slope(w) <= -1 + 1e-6 and 0.35 <= frac <= 0.5 + 1e-9, (order, frac)
+    assert abs(np.mean(np.diff(op.dispersion_traditional(2, k)) < 0) - 0.5) < 1e-4
