@@ -24,7 +24,6 @@ workload instead.
 """
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess

@@ -1,6 +1,5 @@
 """CPU tests of the C ABI: the library loads, exports every declared symbol, and
 rejects invalid arguments on the host (no compute calls, no GPU needed)."""
-import ctypes
 import os
 import re
 

@@ -7,8 +7,6 @@
   differences in 20 seeded directions (target: 1e-5 relative).
 * sqrt(N) checkpointing does not change the gradient; the autograd.Function returns it.
 """
-import math
-
 import numpy as np
 import pytest
 import torch

@@ -6,7 +6,6 @@ FP64: the adjoint gradient agrees with central finite differences (two seeded sm
 directions) to 1e-5.  FP32 forward with FP64 misfit: the gradient's directional
 derivatives stay within 1e-2 of the FP64 ones.
 """
-import numpy as np
 import pytest
 import torch
 

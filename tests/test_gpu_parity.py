@@ -19,7 +19,7 @@ import pytest
 import torch
 
 from oracle import rk
-from oracle.elastic import Scheme, energy, rhs
+from oracle.elastic import Scheme, rhs
 from oracle.metrics import metrics
 from oracle.pointwise import PointOracle
 from oracle.solver import OracleSolver

@@ -9,7 +9,6 @@ meets the stated FP32 target of 1e-4.
 """
 import numpy as np
 import pytest
-import torch
 
 from workloads.configs import config_by_name
 

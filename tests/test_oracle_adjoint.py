@@ -1,7 +1,7 @@
 """Pins of the oracle's derivative tools used to check the adjoint."""
 import numpy as np
 
-from oracle.adjoint import assemble_operator, complex_step, misfit
+from oracle.adjoint import assemble_operator, misfit
 from oracle.elastic import Scheme
 from oracle.metrics import metrics
 from workloads.geometry import make_map, node_coordinates
