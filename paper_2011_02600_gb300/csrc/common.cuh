@@ -251,6 +251,55 @@ __device__ __forceinline__ void apply_P(const T rv[3], const T e[6], T irhoJ, T 
   d[8] = muJ * e[5];
 }
 
+// Section 2.2: J and a[xi][eta] = J xi_eta at node t of the [s][r][q] enumeration from the node
+// coordinates xyz (3 FP64 fields), into jmet (J, then the 9 metrics; FP64).  Coordinate
+// derivatives use D_c = (D+ + D-)/2 along each axis.  Returns false where J <= 0.
+template <int O>
+__device__ __forceinline__ bool metrics_at(const double* __restrict__ xyz, double* __restrict__ jmet, const Dims& d,
+                                           long long t) {
+  const int i = (int)(t % d.nq);
+  const int j = (int)((t / d.nq) % d.nr);
+  const int k = (int)(t / ((long long)d.nq * d.nr));
+  const long long n0 = (long long)k * d.plane + (long long)j * d.ldq + i;
+  const int pos[3] = {i, j, k};
+  const int N[3] = {d.nq, d.nr, d.ns};
+  const long long stride[3] = {1, d.ldq, d.plane};
+  double der[3][3];  // der[xi][c] = d x_c / d xi
+#pragma unroll
+  for (int xi = 0; xi < 3; ++xi) {
+    double s[3] = {0, 0, 0};
+    auto acc = [&](int c, double w) {
+      const long long nb = n0 + (long long)(c - pos[xi]) * stride[xi];
+      s[0] += 0.5 * w * xyz[nb];
+      s[1] += 0.5 * w * xyz[d.fs + nb];
+      s[2] += 0.5 * w * xyz[2 * d.fs + nb];
+    };
+    apply_row<double, O, true>(pos[xi], N[xi], acc);
+    apply_row<double, O, false>(pos[xi], N[xi], acc);
+    const double ih = (double)(N[xi] - 1);
+    der[xi][0] = s[0] * ih;
+    der[xi][1] = s[1] * ih;
+    der[xi][2] = s[2] * ih;
+  }
+  // cross products: a_q = x_r x x_s, a_r = x_s x x_q, a_s = x_q x x_r (cofactors, Cramer's rule)
+  double a[3][3];
+#pragma unroll
+  for (int xi = 0; xi < 3; ++xi) {
+    const double* u = der[(xi + 1) % 3];
+    const double* v = der[(xi + 2) % 3];
+    a[xi][0] = u[1] * v[2] - u[2] * v[1];
+    a[xi][1] = u[2] * v[0] - u[0] * v[2];
+    a[xi][2] = u[0] * v[1] - u[1] * v[0];
+  }
+  const double J = der[0][0] * a[0][0] + der[0][1] * a[0][1] + der[0][2] * a[0][2];
+  jmet[n0] = J;
+#pragma unroll
+  for (int xi = 0; xi < 3; ++xi)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) jmet[(1 + 3 * xi + c) * d.fs + n0] = a[xi][c];
+  return J > 0.0;
+}
+
 // Energy density of one node over a single division: with l = lambda/J, m = mu/J,
 // r = 1/(rho J) and A = sum s_ii^2 + 2 sum s_ij^2,
 //   rho J |v|^2 + J sigma^T S sigma = |v|^2 / r + (A (3 l + 2 m) - l tr^2) / ((3 l + 2 m) 2 m)

@@ -8,55 +8,14 @@
 namespace sbp {
 
 // ---------------------------------------------------------------------------
-// Section 2.2: J and a[xi][eta] = J xi_eta from node coordinates, FP64.
-// Coordinate derivatives use D_c = (D+ + D-)/2 along each axis.
+// Section 2.2: J and a[xi][eta] = J xi_eta from node coordinates, FP64, one thread per node
+// (metrics_at in common.cuh).
 template <int O>
 __global__ void metrics_kernel(const double* __restrict__ xyz, double* __restrict__ jmet, Dims d,
                                unsigned* status) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)d.nq * d.nr * d.ns;
-  if (t >= total) return;
-  const int i = (int)(t % d.nq);
-  const int j = (int)((t / d.nq) % d.nr);
-  const int k = (int)(t / ((long long)d.nq * d.nr));
-  const long long n0 = (long long)k * d.plane + (long long)j * d.ldq + i;
-  const int pos[3] = {i, j, k};
-  const int N[3] = {d.nq, d.nr, d.ns};
-  const long long stride[3] = {1, d.ldq, d.plane};
-  double der[3][3];  // der[xi][c] = d x_c / d xi
-#pragma unroll
-  for (int xi = 0; xi < 3; ++xi) {
-    double s[3] = {0, 0, 0};
-    auto acc = [&](int c, double w) {
-      const long long nb = n0 + (long long)(c - pos[xi]) * stride[xi];
-      s[0] += 0.5 * w * xyz[nb];
-      s[1] += 0.5 * w * xyz[d.fs + nb];
-      s[2] += 0.5 * w * xyz[2 * d.fs + nb];
-    };
-    apply_row<double, O, true>(pos[xi], N[xi], acc);
-    apply_row<double, O, false>(pos[xi], N[xi], acc);
-    const double ih = (double)(N[xi] - 1);
-    der[xi][0] = s[0] * ih;
-    der[xi][1] = s[1] * ih;
-    der[xi][2] = s[2] * ih;
-  }
-  // cross products: a_q = x_r x x_s, a_r = x_s x x_q, a_s = x_q x x_r (cofactors, Cramer's rule)
-  double a[3][3];
-#pragma unroll
-  for (int xi = 0; xi < 3; ++xi) {
-    const double* u = der[(xi + 1) % 3];
-    const double* v = der[(xi + 2) % 3];
-    a[xi][0] = u[1] * v[2] - u[2] * v[1];
-    a[xi][1] = u[2] * v[0] - u[0] * v[2];
-    a[xi][2] = u[0] * v[1] - u[1] * v[0];
-  }
-  const double J = der[0][0] * a[0][0] + der[0][1] * a[0][1] + der[0][2] * a[0][2];
-  jmet[n0] = J;
-#pragma unroll
-  for (int xi = 0; xi < 3; ++xi)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) jmet[(1 + 3 * xi + c) * d.fs + n0] = a[xi][c];
-  if (!(J > 0.0)) atomicOr(status, 2u);
+  if (t >= (long long)d.nq * d.nr * d.ns) return;
+  if (!metrics_at<O>(xyz, jmet, d, t)) atomicOr(status, 2u);
 }
 
 cudaError_t launch_metrics(const double* xyz, double* jmet, const Dims& d, int order, unsigned* status,

@@ -110,3 +110,31 @@ extern "C" int host_energy(int order, int nq, int nr, int ns, const double* q, c
     default: return 1;
   }
 }
+
+// J and the metric terms (metrics_at of common.cuh) at every node of a densely stored grid:
+// xyz 3 fields, jmet 10 fields (J, then a[xi][eta]).  Returns the number of nodes with J <= 0.
+template <int O>
+static long long metrics_all(int nq, int nr, int ns, const double* xyz, double* jmet) {
+  Dims d;
+  d.nq = nq;
+  d.nr = nr;
+  d.ns = ns;
+  d.ldq = nq;
+  d.plane = nq * nr;
+  d.fs = (long long)nq * nr * ns;
+  long long bad = 0;
+  for (long long t = 0; t < d.fs; ++t) bad += metrics_at<O>(xyz, jmet, d, t) ? 0 : 1;
+  return bad;
+}
+
+extern "C" long long host_metrics(int order, int nq, int nr, int ns, const double* xyz, double* jmet) {
+  switch (order) {
+    case 2: return metrics_all<2>(nq, nr, ns, xyz, jmet);
+    case 3: return metrics_all<3>(nq, nr, ns, xyz, jmet);
+    case 4: return metrics_all<4>(nq, nr, ns, xyz, jmet);
+    case 5: return metrics_all<5>(nq, nr, ns, xyz, jmet);
+    case 6: return metrics_all<6>(nq, nr, ns, xyz, jmet);
+    case 7: return metrics_all<7>(nq, nr, ns, xyz, jmet);
+    default: return -1;
+  }
+}

@@ -36,6 +36,8 @@ def hostop(tmp_path_factory):
         fn.restype = ctypes.c_int
     lib.host_energy.argtypes = [ctypes.c_int] * 4 + [P] * 3
     lib.host_energy.restype = ctypes.c_int
+    lib.host_metrics.argtypes = [ctypes.c_int] * 4 + [P] * 2
+    lib.host_metrics.restype = ctypes.c_longlong
     return lib
 
 
@@ -141,3 +143,28 @@ def test_traditional_operator_matches_oracle_fp64(hostop, order, nodes, bcname):
                               ctypes.addressof(e)) == 0
     want_e = energy(Q, sch, J, mat)
     assert abs(e.value - want_e) < 1e-12 * want_e
+
+
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("geometry", ["curvy", "gaussian_hill"])
+def test_kernel_metrics_match_oracle(hostop, order, geometry):
+    """The metrics kernel's per-node body (metrics_at: D_c = (D+ + D-)/2 along each axis,
+    cofactors by Cramer's rule, Sec. 2.2) gives the oracle's J and a[xi][eta] to rounding; a
+    folded mesh is flagged (J <= 0)."""
+    nodes = (17, 16, 18)
+    ext = (1000.0, 1100.0, 900.0)
+    fmap = make_map("curvy", ext) if geometry == "curvy" else \
+        make_map("gaussian_hill", ext, hill_amp=300.0, hill_sigma=250.0)
+    X = node_coordinates(fmap, nodes)
+    xyz = np.ascontiguousarray(np.stack(X))
+    jmet = np.zeros((10,) + X[0].shape)
+    assert hostop.host_metrics(order, *nodes, xyz.ctypes.data, jmet.ctypes.data) == 0
+    J, a = metrics(*X, order)
+    assert np.abs(jmet[0] - J).max() < 1e-12 * np.abs(J).max()
+    for xi in range(3):
+        for c in range(3):
+            ref = a[xi][c]
+            assert np.abs(jmet[1 + 3 * xi + c] - ref).max() <= 1e-12 * max(np.abs(ref).max(), np.abs(J).max() ** (2 / 3))
+    folded = xyz.copy()
+    folded[0] = folded[0][:, :, ::-1]          # x reversed along q: J < 0 everywhere
+    assert hostop.host_metrics(order, *nodes, folded.ctypes.data, jmet.ctypes.data) == np.prod(nodes)
