@@ -13,6 +13,7 @@
 
 #include "launch.h"
 #include "sbp.h"
+#include "source_weights.h"
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -308,34 +309,6 @@ int check_ready(const SbpGrid* g) {
   if (!g) return fail(SBP_ERR_ARG, "null grid");
   if (!g->bound) return fail(SBP_ERR_STATE, "buffers not bound (sbp_bind)");
   return SBP_OK;
-}
-
-// 1D discrete delta: m+1 consecutive nodes from floor(xi0/h) - (m-1)/2 (centred on the
-// source's cell, shifted inwards at a face), moment conditions up to degree m.
-void delta_1d(double xi0, int N, int m, int* start, double* phi) {
-  const double h = 1.0 / (N - 1);
-  int c = (int)floor(xi0 / h) - (m - 1) / 2;
-  c = std::max(0, std::min(N - 1 - m, c));
-  *start = c;
-  // solve V^T phi = e0 with V[k][i] = x_i^k (Gaussian elimination, partial pivoting)
-  const int n = m + 1;
-  std::vector<double> A(n * (n + 1));
-  for (int k = 0; k < n; ++k) {
-    for (int i = 0; i < n; ++i) A[k * (n + 1) + i] = pow(((c + i) * h - xi0) / h, k);
-    A[k * (n + 1) + n] = k == 0 ? 1.0 : 0.0;
-  }
-  for (int col = 0; col < n; ++col) {
-    int p = col;
-    for (int r = col + 1; r < n; ++r)
-      if (fabs(A[r * (n + 1) + col]) > fabs(A[p * (n + 1) + col])) p = r;
-    for (int x = 0; x <= n; ++x) std::swap(A[col * (n + 1) + x], A[p * (n + 1) + x]);
-    for (int r = 0; r < n; ++r) {
-      if (r == col) continue;
-      const double f = A[r * (n + 1) + col] / A[col * (n + 1) + col];
-      for (int x = col; x <= n; ++x) A[r * (n + 1) + x] -= f * A[col * (n + 1) + x];
-    }
-  }
-  for (int i = 0; i < n; ++i) phi[i] = A[i * (n + 1) + n] / A[i * (n + 1) + i];
 }
 
 }  // namespace
@@ -691,7 +664,7 @@ int sbp_set_sources(SbpGrid* g, int32_t n, const SbpSource* srcs, const double* 
     const SbpSource* src = &srcs[m];
     int start[3];
     double phi[3][8];
-    for (int a = 0; a < 3; ++a) delta_1d(src->ref[a], N[a], mo, &start[a], phi[a]);
+    for (int a = 0; a < 3; ++a) sbp::delta_1d(src->ref[a], N[a], mo, &start[a], phi[a]);
     double Jrow[8];
     for (int kk = 0, c = 0; kk < n1; ++kk)
       for (int jj = 0; jj < n1; ++jj) {

@@ -10,6 +10,7 @@ using std::min;
 using std::sqrt;
 
 #include "common.cuh"
+#include "source_weights.h"
 
 using namespace sbp;
 
@@ -137,4 +138,11 @@ extern "C" long long host_metrics(int order, int nq, int nr, int ns, const doubl
     case 7: return metrics_all<7>(nq, nr, ns, xyz, jmet);
     default: return -1;
   }
+}
+
+// The point source's 1D discrete-delta weights as the library computes them (source_weights.h).
+extern "C" int host_delta_1d(double xi0, int N, int m, int* start, double* phi) {
+  if (m < 1 || m > 7 || N < m + 1) return 1;
+  sbp::delta_1d(xi0, N, m, start, phi);
+  return 0;
 }

@@ -38,6 +38,8 @@ def hostop(tmp_path_factory):
     lib.host_energy.restype = ctypes.c_int
     lib.host_metrics.argtypes = [ctypes.c_int] * 4 + [P] * 2
     lib.host_metrics.restype = ctypes.c_longlong
+    lib.host_delta_1d.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_int, P, P]
+    lib.host_delta_1d.restype = ctypes.c_int
     return lib
 
 
@@ -168,3 +170,26 @@ def test_kernel_metrics_match_oracle(hostop, order, geometry):
     folded = xyz.copy()
     folded[0] = folded[0][:, :, ::-1]          # x reversed along q: J < 0 everywhere
     assert hostop.host_metrics(order, *nodes, folded.ctypes.data, jmet.ctypes.data) == np.prod(nodes)
+
+
+@pytest.mark.parametrize("order", [2, 4, 6])
+def test_source_delta_weights_match_oracle(hostop, order):
+    """The 1D discrete-delta weights of sbp_set_sources (source_weights.h: order + 2 nodes,
+    moment conditions to degree order + 1; the paper does not describe the discretisation of
+    Eq. momententor_pointsource) against the oracle's, at positions across the whole axis
+    including both faces and the face-shifted supports; the moment conditions hold directly."""
+    from oracle.source import delta_weights_1d
+    m = order + 1
+    for N in (17, 33, 97):
+        h = 1.0 / (N - 1)
+        for xi0 in np.concatenate([np.linspace(0.0, 1.0, 257), [h / 3, 1 - h / 3, 0.5 + 1e-12]]):
+            start = ctypes.c_int()
+            phi = (ctypes.c_double * (m + 1))()
+            assert hostop.host_delta_1d(float(xi0), N, m, ctypes.addressof(start), ctypes.addressof(phi)) == 0
+            c, want = delta_weights_1d(float(xi0), N, m)
+            got = np.array(phi[:])
+            assert start.value == c
+            assert np.abs(got - want).max() < 1e-9 * max(1.0, np.abs(want).max())
+            xs = (np.arange(c, c + m + 1) * h - xi0) / h
+            mom = [float(np.sum(got * xs ** k)) for k in range(m + 1)]
+            assert abs(mom[0] - 1.0) < 1e-9 and max(abs(v) for v in mom[1:]) < 1e-8 * max(1.0, np.abs(xs).max() ** m)
