@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <stdint.h>
 
+#include "nn_elem.cuh"
 #include "sbp.h"
 
 namespace sbp_nn {
@@ -319,12 +320,7 @@ __global__ void im2col_kernel(const __nv_bfloat16* __restrict__ X, __nv_bfloat16
                               int T, int kw, int pad) {
   const long long n = (long long)C * kw * B * T;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const long long col = e % ((long long)B * T);
-    const long long row = e / ((long long)B * T);
-    const int c = (int)(row / kw), k = (int)(row % kw);
-    const int b = (int)(col / T), t = (int)(col % T);
-    const int ts = t + k - pad;
-    Xc[e] = (ts >= 0 && ts < T) ? X[(long long)c * B * T + (long long)b * T + ts] : __float2bfloat16(0.f);
+    im2col_at(X, Xc, B, T, kw, pad, e);
   }
 }
 
@@ -333,15 +329,7 @@ __global__ void col2im_kernel(const float* __restrict__ dXc, float* __restrict__
                               int kw, int pad) {
   const long long n = (long long)C * B * T;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(e / ((long long)B * T));
-    const long long col = e % ((long long)B * T);
-    const int b = (int)(col / T), t = (int)(col % T);
-    float s = 0.f;
-    for (int k = 0; k < kw; ++k) {
-      const int tt = t - k + pad;
-      if (tt >= 0 && tt < T) s += dXc[((long long)c * kw + k) * B * T + (long long)b * T + tt];
-    }
-    dX[e] = s;
+    col2im_at(dXc, dX, B, T, kw, pad, e);
   }
 }
 
@@ -445,13 +433,7 @@ __global__ void moment_combine_kernel(const float* __restrict__ G, const float* 
                                       int n_out, int B, int T) {
   const long long n = (long long)n_out * B * T;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const int o = (int)(e / ((long long)B * T));
-    const long long col = e % ((long long)B * T);
-    const int b = (int)(col / T);
-    float s = 0.f;
-#pragma unroll
-    for (int c = 0; c < 6; ++c) s += m[c * B + b] * G[((long long)c * n_out + o) * B * T + col];
-    y[e] = s;
+    moment_combine_at(G, m, y, n_out, B, T, e);
   }
 }
 
@@ -459,11 +441,7 @@ __global__ void moment_combine_bwd_kernel(const __nv_bfloat16* __restrict__ dy, 
                                           __nv_bfloat16* __restrict__ dG, int n_out, int B, int T) {
   const long long n = 6LL * n_out * B * T;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-    const long long row = e / ((long long)B * T);
-    const long long col = e % ((long long)B * T);
-    const int c = (int)(row / n_out), o = (int)(row % n_out);
-    const int b = (int)(col / T);
-    dG[e] = __float2bfloat16(m[c * B + b] * __bfloat162float(dy[(long long)o * B * T + col]));
+    moment_combine_bwd_at(dy, m, dG, n_out, B, T, e);
   }
 }
 
