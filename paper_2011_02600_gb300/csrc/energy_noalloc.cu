@@ -9,6 +9,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <cudaTypedefs.h>
+
 #include <mutex>
 
 #include "launch.h"
@@ -28,8 +30,38 @@ constexpr int kMaxDevices = 64;
 // [kMaxPartials + 1]: status bits (low 32 bits of the slot).  32.8 KB per device.
 static __device__ __align__(256) double g_energy_scratch[kMaxPartials + 2];
 
+// Set-up state per device: the scratch's device address and the unique id of the context it
+// was looked up in.  A device reset (cudaDeviceReset) ends that context; the next call finds a
+// different id, looks the address up again and does not use the stale one.
+struct ScratchSlot {
+  unsigned long long ctx_id = 0;
+  void* addr = nullptr;
+};
 std::mutex g_setup_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
+ScratchSlot g_scratch[kMaxDevices];
+
+// Unique id of the calling thread's current context (driver API through the runtime's
+// entry-point query, so that the library needs no link against libcuda); 0 if there is none.
+unsigned long long current_context_id() {
+  static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (PFN_cuCtxGetCurrent_v4000)p;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (PFN_cuCtxGetId_v12000)p;
+  });
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+    return 0;
+  return id;
+}
 
 int reject(int code, const char* msg) {
   sbp::set_last_error(msg);
@@ -53,7 +85,8 @@ extern "C" int sbp_energy_noalloc(const void* q, const void* mat, int32_t nq, in
     return reject(SBP_ERR_ARG, "nblocks must lie in 0..4096 (the static scratch holds 4096 partial sums)");
   if (nblocks == 0) nblocks = kDefaultPartials;
 
-  // Once per device, with that device current: the device address of the scratch.
+  // Set-up, once per device (and again after a device reset), with that device current: the
+  // device address of the scratch.  Host code cannot use g_energy_scratch itself as an address.
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return reject(SBP_ERR_CUDA, cudaGetErrorString(e));
@@ -61,13 +94,16 @@ extern "C" int sbp_energy_noalloc(const void* q, const void* mat, int32_t nq, in
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    ScratchSlot& slot = g_scratch[dev];
+    const unsigned long long id = current_context_id();
+    if (!slot.addr || id == 0 || id != slot.ctx_id) {
       void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_energy_scratch);
+      e = cudaGetSymbolAddress(&p, g_energy_scratch);  // creates the context if there was none yet
       if (e != cudaSuccess) return reject(SBP_ERR_CUDA, cudaGetErrorString(e));
-      g_scratch_addr[dev] = p;
+      slot.addr = p;
+      slot.ctx_id = current_context_id();
     }
-    base = g_scratch_addr[dev];
+    base = slot.addr;
   }
   double* partial = (double*)base;
   double* result = partial + kMaxPartials;
