@@ -117,9 +117,18 @@ def max_over_ranks(x, dist, device="cpu"):
     return float(t.item())
 
 
-def oracle_step_sample(sub, stages=5):
-    """Time the FP64 oracle on a sub-block (the top `sub` nodes of the workload's grid, same map,
-    medium and spacing): `stages` Runge-Kutta stages.  Returns (node-stages, seconds)."""
+_BARRIER = None
+
+
+def _pool_init(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def oracle_step_sample(sub, stages=5, j0=0):
+    """Time the FP64 oracle on a sub-block (the top `sub` nodes of the workload's grid from r
+    index j0, same map, medium and spacing): `stages` Runge-Kutta stages.  Returns (node-stages,
+    seconds)."""
     import numpy as np
 
     from oracle import rk
@@ -131,7 +140,7 @@ def oracle_step_sample(sub, stages=5):
     from workloads.media import make_medium
     cfg = config_by_name(WORKLOAD)
     nq, nr, ns = cfg.nodes
-    i, j, k = np.arange(sub[0]), np.arange(sub[1]), np.arange(ns - sub[2], ns)
+    i, j, k = np.arange(sub[0]), np.arange(j0, j0 + sub[1]), np.arange(ns - sub[2], ns)
     fmap, fmed = make_map(cfg), make_medium(cfg)
     X = [np.broadcast_to(c, (sub[2], sub[1], sub[0])).copy()
          for c in fmap(i[None, None, :] / (nq - 1), j[None, :, None] / (nr - 1), k[:, None, None] / (ns - 1))]
@@ -141,6 +150,8 @@ def oracle_step_sample(sub, stages=5):
     I, Jj, K = np.meshgrid(i, j, k, indexing="ij")
     Q = np.stack(smooth_state(cfg.nodes, 11, I.T, Jj.T, K.T))
     dQ = np.zeros_like(Q)
+    if _BARRIER is not None:
+        _BARRIER.wait(timeout=600)   # every core starts its timed stages together
     t0 = time.perf_counter()
     for s in range(stages):
         dQ *= rk.A[s]
@@ -149,27 +160,74 @@ def oracle_step_sample(sub, stages=5):
     return sub[0] * sub[1] * sub[2] * stages, time.perf_counter() - t0
 
 
+def _oracle_worker(a):
+    import os as _os
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        _os.environ[v] = "1"
+    return oracle_step_sample(a[0], j0=a[1])
+
+
+def host_cores():
+    """Host cores available to this process and the CPU model (as /proc/cpuinfo names it)."""
+    try:
+        n = len(os.sched_getaffinity(0))
+    except Exception:
+        n = os.cpu_count() or 1
+    model = ""
+    try:
+        for ln in open("/proc/cpuinfo"):
+            k = ln.split(":")[0].strip().lower()
+            if k in ("model name", "cpu model", "hardware") and ":" in ln:
+                model = ln.split(":", 1)[1].strip()
+                break
+            if k == "cpu part" and not model:
+                model = "Arm part " + ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return n, (model or platform.processor() or platform.machine())
+
+
+def oracle_parallel_sample(sub, nproc, repeats=1):
+    """The oracle on nproc host cores at once: nproc spawned processes (one thread each), each
+    timing one Runge-Kutta step on its own sub-block of the workload (the top `sub` nodes, at
+    successive r offsets), after a barrier so that the timed stages run together.  Returns a
+    list of (node-stages, seconds) per repeat: the node-stages of all cores and the slowest
+    core's time."""
+    import multiprocessing as mp
+    jobs = [(sub, (w * sub[1]) % (1025 - sub[1])) for w in range(nproc)]
+    ctx = mp.get_context("spawn")
+    out = []
+    with ctx.Pool(nproc, initializer=_pool_init, initargs=(ctx.Barrier(nproc),)) as pool:
+        for _ in range(repeats):
+            res = pool.map(_oracle_worker, jobs, chunksize=1)
+            out.append((sum(r[0] for r in res), max(r[1] for r in res)))
+    return out
+
+
+REF_SUB = (257, 33, 17)     # per core and step of the reference arm
+CPU_SUB = (1025, 33, 33)    # per core of the cpu_baseline
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    sub = (257, 33, 17)
-    n_per_step = 0
-    for _ in range(args.warmup):
-        oracle_step_sample(sub)
-    tot = 0.0
-    for _ in range(args.steps):
-        n, t = oracle_step_sample(sub)
-        n_per_step = n
-        tot += t
-    value = n_per_step * args.steps / tot / 1e6
+    sub = REF_SUB
+    nproc, model = host_cores()
+    runs = oracle_parallel_sample(sub, nproc, args.warmup + args.steps)[args.warmup:]
+    tot = sum(t for _, t in runs)
+    n_tot = sum(n for n, _ in runs)
+    value = n_tot / tot / 1e6
+    what = (f"per step, {nproc} spawned processes (one thread each) on {nproc} host cores ({model}), each one "
+            f"5-stage RK step of the FP64 oracle on its own {sub[0]}x{sub[1]}x{sub[2]} block of the top of the "
+            f"workload, started together after a barrier; time = the slowest core's")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"top {sub[0]}x{sub[1]}x{sub[2]} nodes of the workload, one RK step",
-                   "nodes": list(sub), "order": 6},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"one 5-stage RK step on the top {sub[0]}x{sub[1]}x{sub[2]} nodes per step"},
+        "config": {"workload": WORKLOAD, "sample": what, "nodes": list(sub), "order": 6},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc, "cpu_model": model, "kind": "oracle",
+                         "sample": what},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -468,28 +526,30 @@ def main():
                 "launches": launches, "peak_source": "nominal FP64 rate",
                 "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak}
 
-    # end to end: state in from pinned host memory, one step, state and energy out, per step
+    # end to end through the C ABI: per step, the state uploaded from pinned host memory
+    # (sbp_set_state), one RK step (sbp_step_n), the state downloaded to pinned host memory
+    # (sbp_get_state, which returns once the copy has landed)
     e2e = None
     try:
         nbytes = 9 * s.fs * elem
         tdt = torch.float32 if elem == 4 else torch.float64
         host_in = torch.empty(9 * s.fs, dtype=tdt, pin_memory=True)
         host_out = torch.empty(9 * s.fs, dtype=tdt, pin_memory=True)
-        host_in.copy_(s.qbuf[s.current].cpu())
+        L.sbp_get_state(h, host_in, L.SBP_MEM_HOST, _stream())
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
         torch.cuda.synchronize()
         ev[0].record(stream)
         for _ in range(args.e2e_steps):
-            s.qbuf[s.current].copy_(host_in, non_blocking=True)
+            L.sbp_set_state(h, host_in, L.SBP_MEM_HOST, _stream())
             L.sbp_step_n(h, 1, dt, _stream())
-            host_out.copy_(s.qbuf[s.current], non_blocking=True)
+            L.sbp_get_state(h, host_out, L.SBP_MEM_HOST, _stream())
         ev[1].record(stream)
         torch.cuda.synchronize()
         e_ms = ev[0].elapsed_time(ev[1]) / args.e2e_steps
         e2e = {"value": nodes * 5 / (e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes, "ms_per_step": e_ms,
-               "what": "per step: the 9-field state copied in from pinned host memory, one RK step "
-                       "through the C ABI, the state copied back to pinned host memory"}
+               "what": "per step, all through the C ABI: sbp_set_state from pinned host memory (the 9-field "
+                       "state in the grid layout), sbp_step_n(1), sbp_get_state to pinned host memory"}
         del host_in, host_out
     except Exception as ex:  # pinned memory can be unavailable
         e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
@@ -497,11 +557,14 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        sub = (1025, 97, 33)
-        n, t = oracle_step_sample(sub)
-        cpu = {"value": n / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one 5-stage RK step of the FP64 oracle (numpy/scipy, one thread) on the top "
-                         f"{sub[0]}x{sub[1]}x{sub[2]} nodes of the workload ({t:.1f} s)"}
+        sub = CPU_SUB
+        nproc, model = host_cores()
+        n, t = oracle_parallel_sample(sub, nproc)[0]
+        cpu = {"value": n / t / 1e6, "unit": UNIT, "cores": nproc, "cpu_model": model, "kind": "oracle",
+               "sample": f"{nproc} spawned processes (numpy/scipy, one thread each) on {nproc} host cores, each "
+                         f"one 5-stage RK step of the FP64 oracle on its own {sub[0]}x{sub[1]}x{sub[2]} block of "
+                         f"the top of the workload, started together after a barrier ({t:.1f} s, the slowest "
+                         f"core's time)"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

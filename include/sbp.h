@@ -7,8 +7,9 @@
  *
  *   P~^-1 dQ/dt = sum_xi D-_xi F_xi(Q) + sum_xi B_xi(D+_xi Q) + sum SAT     (Sections 4.2, 5)
  *
- * with the upwind SBP pair (H, D-, D+) of interior order 2, 4 or 6 along q, r
- * and s (Section 4.1, Table 1), metric terms e_xi = J grad(xi) (Section 2.2),
+ * with the upwind SBP pair (H, D-, D+) of interior order 2 to 7 along q, r
+ * and s (Section 4.1, Table 1) or a traditional central SBP operator (Table 2),
+ * metric terms e_xi = J grad(xi) (Section 2.2),
  * the free-surface penalty (Eq. SAT_free_surface) or the general penalty with
  * parameter gamma (Eq. SAT_General) on each face, fused with the stages of the
  * five-stage 2N-storage fourth-order Runge-Kutta scheme the paper uses
@@ -58,6 +59,13 @@ extern "C" {
 #define SBP_ERR_STATE 5        /* call out of sequence (e.g. stepping before sbp_bind) */
 #define SBP_ERR_MESH 6         /* non-positive Jacobian or invalid moduli found on the device */
 
+/* Operator codes (SbpGridDesc.order): 2..7 are the upwind dual pairs of Table 1
+ * (Section 4.1, Eq. upw_SBP), even and odd orders; SBP_TRADITIONAL + 2, 4, 6 are
+ * the traditional central SBP operators of Table 2, applied in place of both D-
+ * and D+ (Section 6.2 compares them with the upwind pairs; Section 7.2 runs them
+ * on topography).  The adjoint entry points accept the codes 2, 4 and 6. */
+#define SBP_TRADITIONAL 100
+
 #define SBP_BC_FREE 0  /* free surface, Eq. SAT_free_surface */
 #define SBP_BC_CHAR 1  /* general condition with gamma, Eq. BC_General2 / Eq. SAT_General */
 
@@ -69,7 +77,7 @@ extern "C" {
 
 typedef struct SbpGridDesc {
   int32_t nq, nr, ns;     /* nodes per axis; each >= sbp_min_nodes(order) */
-  int32_t order;          /* interior order of the upwind pair: 2, 4 or 6 */
+  int32_t order;          /* operator code: upwind order 2..7, or SBP_TRADITIONAL + 2, 4, 6 */
   int32_t precision;      /* 32 or 64 */
   int32_t bc_kind[6];     /* SBP_BC_FREE or SBP_BC_CHAR per face */
   double bc_gamma[6];     /* gamma in [-1, 1] for SBP_BC_CHAR faces (Eq. BC_General2) */
@@ -88,7 +96,8 @@ typedef struct SbpSource {
   double f0, t0, T;       /* Ricker peak frequency and delay; LOH1 time constant */
 } SbpSource;
 
-/* Smallest node count per axis for an order: 2b + max(r, q) (b closure rows). */
+/* Smallest node count per axis for an operator code: 2b + max(r, q) (b closure
+ * rows, interior stencil reach r and q).  ARG for an unknown code. */
 int sbp_min_nodes(int32_t order, int32_t* out);
 
 /* Validate desc and create a grid handle (host memory only).  ARG on bad sizes,
@@ -118,7 +127,8 @@ int sbp_bind(SbpGrid* grid, void* q0, void* q1, void* dq, void* met, void* mat);
 
 /* Section 2.2: from node coordinates xyz (3 FP64 fields x, y, z; device)
  * compute J and a[xi][eta] = J xi_eta (Cramer's rule, derivatives with
- * D_c = (D+ + D-)/2 of the grid's order) into jmet (10 FP64 fields: J, then
+ * D_c = (D+ + D-)/2 of the upwind pair of the grid's order, also for the
+ * traditional operators) into jmet (10 FP64 fields: J, then
  * the 9 metrics; device, caller-owned).  Flags SBP_STATUS_BAD_MESH where J <= 0. */
 int sbp_metrics(SbpGrid* grid, const double* xyz, double* jmet, void* stream);
 
@@ -179,11 +189,48 @@ int sbp_set_source(SbpGrid* grid, const SbpSource* src, const double* jmet, void
  * one batch share their time function (stf, f0, t0, T); UNSUPPORTED otherwise. */
 int sbp_set_sources(SbpGrid* grid, int32_t n, const SbpSource* srcs, const double* jmet, void* stream);
 
-/* Receivers: n nodes given by host int32 (i, j, k) triples; traces is a device
- * buffer of B*n*3*n_t elements of the solver precision, trace[b][r][c][step]
- * (velocity component c of receiver r in state b after step `step`); steps
- * beyond n_t are not recorded.  n = 0 removes the receivers. */
+/* Receivers (the stations of Section 7: particle velocity at surface nodes):
+ * n nodes (at most 65535) given by host int32 (i, j, k) triples; traces is a
+ * device buffer of B*n*3*n_t elements of the solver precision,
+ * trace[b][r][c][step] (velocity component c of receiver r in state b after
+ * step `step`); steps beyond n_t are not recorded.  traces = NULL makes the
+ * library allocate and own the trace buffer (zeroed; freed by the next
+ * sbp_set_receivers or by sbp_destroy); sbp_record_receivers copies it out.
+ * n = 0 removes the receivers.  A rejected list leaves the current one in place. */
 int sbp_set_receivers(SbpGrid* grid, int32_t n, const int32_t* ijk, void* traces, int32_t n_t);
+
+/* Receivers by physical position: xyz holds n host FP64 (x, y, z) triples; each
+ * receiver records at the node nearest to its point (Euclidean distance in the
+ * node coordinates `coords`: 3 FP64 device fields x, y, z in the grid layout, as
+ * given to sbp_metrics), searched among the nodes of face `face` (0..5, e.g. 5
+ * for the free surface s = 1) or of the whole grid (face = -1); of nodes at
+ * exactly the same distance the one first in [s][r][q] order is taken.  Then as
+ * sbp_set_receivers(n, ijk, traces, n_t); ijk_out (host, 3 n int32, may be NULL)
+ * receives the chosen nodes.  Synchronises the device.  ARG for non-finite
+ * positions, a bad face or n outside 0..65535. */
+int sbp_set_receivers_xyz(SbpGrid* grid, int32_t n, const double* xyz, const double* coords, int32_t face,
+                          void* traces, int32_t n_t, int32_t* ijk_out);
+
+/* Memory and layout flags of the copy calls below. */
+#define SBP_MEM_HOST 1      /* the caller's buffer is host memory (pageable or pinned); else device */
+#define SBP_LAYOUT_DENSE 2  /* fields packed [field][s][r][q] without padding; else the grid layout */
+
+/* Copy the recorded traces (B*n*3*n_t elements of the solver precision,
+ * trace[b][r][c][step], steps not yet recorded hold zeros) to dst: host memory
+ * with flags = SBP_MEM_HOST (the call then synchronises the stream), device
+ * memory with flags = 0 (asynchronous).  STATE if no receivers are set. */
+int sbp_record_receivers(SbpGrid* grid, void* dst, int32_t flags, void* stream);
+
+/* Upload / download the current state (9 B fields of the solver precision):
+ * src/dst in host (SBP_MEM_HOST) or device memory, in the grid layout (9 B
+ * fields of fs elements, padding included) or packed [b*9 + field][s][r][q]
+ * (SBP_LAYOUT_DENSE).  Both are enqueued on the stream; a download to host
+ * memory synchronises the stream before returning; an upload from pinned host
+ * memory is asynchronous, so the buffer must stay unchanged until the stream
+ * has passed the copy.  The Runge-Kutta register needs no reset: a step's first
+ * stage does not read it. */
+int sbp_set_state(SbpGrid* grid, const void* src, int32_t flags, void* stream);
+int sbp_get_state(SbpGrid* grid, void* dst, int32_t flags, void* stream);
 
 /* Transposed operator: out = L^T w with L = P~ M the map Q -> dQ/dt of sbp_rhs
  * (penalties included, no source), transposed in the plain Euclidean inner
@@ -242,8 +289,10 @@ int sbp_rk_coefficients(double* A, double* B, double* C);
  * kept until the process exits; nblocks (1..4096) partial sums are used, 0
  * selects 1184 (what sbp_energy uses, which gives the same result).  Sizes
  * outside these limits return SBP_ERR_ARG.  The first call on each device looks
- * up the array's device address; make that first call before any stream
- * capture.  Every call reuses the same array: calls that overlap on the GPU
+ * up the array's device address, and so does the first call after a device
+ * reset (cudaDeviceReset gives the device a new context, in which the array
+ * may sit elsewhere); make that first call before any stream capture.  Every
+ * call reuses the same array: calls that overlap on the GPU
  * (other streams, other threads) race and must be serialised by the caller.
  * Synchronises the stream; SBP_ERR_NONFINITE if the energy is not finite. */
 int sbp_energy_noalloc(const void* q, const void* mat, int32_t nq, int32_t nr, int32_t ns, int64_t ldq,

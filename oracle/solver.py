@@ -13,13 +13,15 @@ class OracleSolver:
     """Plain FP64 solver on one curvilinear block.
 
     x, y, z: node coordinates [s][r][q]; mat: (rho, lam, mu) arrays; bc: six
-    face conditions (q0, q1, r0, r1, s0, s1).
+    face conditions (q0, q1, r0, r1, s0, s1); operator: "upwind" (Table 1) or
+    "traditional" (Table 2), as in elastic.Scheme.  The metric terms use the upwind pair's
+    D_c of the same order either way.
     """
 
-    def __init__(self, order, x, y, z, mat, bc):
+    def __init__(self, order, x, y, z, mat, bc, operator="upwind"):
         self.nodes = (x.shape[2], x.shape[1], x.shape[0])
         self.order = order
-        self.scheme = Scheme(order, self.nodes)
+        self.scheme = Scheme(order, self.nodes, operator)
         self.J, self.a = metrics(x, y, z, order)
         self.mat = tuple(np.asarray(m, dtype=float) for m in mat)
         self.bc = list(bc)

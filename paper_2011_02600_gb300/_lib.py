@@ -11,6 +11,9 @@ from . import build as _build
 
 SBP_BC_FREE = 0
 SBP_BC_CHAR = 1
+SBP_TRADITIONAL = 100
+SBP_MEM_HOST = 1
+SBP_LAYOUT_DENSE = 2
 ERRORS = {1: "ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "NONFINITE", 5: "STATE", 6: "MESH"}
 
 EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sbp_bind", "sbp_metrics",
@@ -20,7 +23,8 @@ EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sb
             "sbp_rk_coefficients", "sbp_energy_noalloc", "sbp_rhs_adjoint", "sbp_adjoint_stage",
             "sbp_misfit", "sbp_set_batch", "sbp_set_sources", "sbp_nn_gemm", "sbp_nn_im2col", "sbp_nn_col2im",
             "sbp_nn_upsample2", "sbp_nn_relu_backward", "sbp_nn_bias_grad", "sbp_nn_mse", "sbp_nn_adam",
-            "sbp_nn_mlp_to_conv", "sbp_nn_cast_bf16", "sbp_nn_moment_combine", "sbp_selftest_wait_timeout", "sbp_last_error")
+            "sbp_nn_mlp_to_conv", "sbp_nn_cast_bf16", "sbp_nn_moment_combine", "sbp_selftest_wait_timeout", "sbp_last_error",
+            "sbp_set_receivers_xyz", "sbp_record_receivers", "sbp_set_state", "sbp_get_state")
 
 
 class SbpError(RuntimeError):
@@ -95,6 +99,10 @@ def lib(path=None):
         "sbp_nn_moment_combine": [P, P, P, P, P, i32, i32, i32, i32, P],
         "sbp_selftest_wait_timeout": [P, ctypes.c_uint32, P],
         "sbp_set_sources": [P, i32, ctypes.POINTER(SbpSource), P, P],
+        "sbp_set_receivers_xyz": [P, i32, P, P, i32, P, i32, P],
+        "sbp_record_receivers": [P, P, i32, P],
+        "sbp_set_state": [P, P, i32, P],
+        "sbp_get_state": [P, P, i32, P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -224,6 +232,35 @@ def sbp_set_receivers(h, ijk, traces, n_t):
     import numpy as np
     arr = np.ascontiguousarray(np.asarray(ijk, dtype=np.int32).reshape(-1, 3))
     _check(lib().sbp_set_receivers(h, len(arr), arr.ctypes.data if len(arr) else None, _ptr(traces), n_t))
+
+
+def sbp_set_receivers_xyz(h, xyz, coords, face, traces, n_t):
+    """Receivers at the nodes nearest to host points xyz (n x 3); returns the chosen (i, j, k)."""
+    import numpy as np
+    arr = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+    ijk = np.zeros((len(arr), 3), dtype=np.int32)
+    _check(lib().sbp_set_receivers_xyz(h, len(arr), arr.ctypes.data if len(arr) else None, _ptr(coords), face,
+                                       _ptr(traces), n_t, ijk.ctypes.data if len(arr) else None))
+    return ijk
+
+
+def _buf(x):
+    """Pointer of a torch tensor or a numpy array (host memory)."""
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    return _ptr(x)
+
+
+def sbp_record_receivers(h, dst, flags, stream):
+    _check(lib().sbp_record_receivers(h, _buf(dst), flags, stream))
+
+
+def sbp_set_state(h, src, flags, stream):
+    _check(lib().sbp_set_state(h, _buf(src), flags, stream))
+
+
+def sbp_get_state(h, dst, flags, stream):
+    _check(lib().sbp_get_state(h, _buf(dst), flags, stream))
 
 
 def sbp_status(h, stream):

@@ -56,8 +56,60 @@ void rk_stage_times(double c[5]) {
   }
 }
 
-int closure_b(int order) { return order == 2 ? 2 : order == 4 ? 4 : 6; }
-int stencil_reach(int order) { return order == 2 ? 2 : order == 4 ? 3 : 4; }  // max(r, q)
+// Properties of an operator code: the upwind orders 2 to 7 of Table 1 and the traditional
+// operators kTraditional + 2, 4, 6 of Table 2.  b: closure rows at each end; reach:
+// max(r, q) of the interior stencil; w0: first norm weight; metric_order: the upwind order
+// whose D_c = (D+ + D-)/2 forms the metric terms; accuracy: the design order (the source's
+// moment conditions use it).
+struct OpInfo {
+  bool ok = false;
+  int b = 0, reach = 0, metric_order = 0, accuracy = 0;
+  double w0 = 0.0;
+  bool adjoint = false;  // the adjoint kernels are built for this operator
+};
+template <int O>
+OpInfo op_info_of(int accuracy, int metric_order, bool adjoint) {
+  OpInfo I;
+  I.ok = true;
+  I.b = sbp::OpCoef<O>::b;
+  I.reach = sbp::OpCoef<O>::r > sbp::OpCoef<O>::q ? sbp::OpCoef<O>::r : sbp::OpCoef<O>::q;
+  I.w0 = sbp::OpCoef<O>::w(0);
+  I.metric_order = metric_order;
+  I.accuracy = accuracy;
+  I.adjoint = adjoint;
+  return I;
+}
+OpInfo op_info(int order) {
+  switch (order) {
+    case 2: return op_info_of<2>(2, 2, true);
+    case 3: return op_info_of<3>(3, 3, false);
+    case 4: return op_info_of<4>(4, 4, true);
+    case 5: return op_info_of<5>(5, 5, false);
+    case 6: return op_info_of<6>(6, 6, true);
+    case 7: return op_info_of<7>(7, 7, false);
+    case sbp::kTraditional + 2: return op_info_of<sbp::kTraditional + 2>(2, 2, false);
+    case sbp::kTraditional + 4: return op_info_of<sbp::kTraditional + 4>(4, 4, false);
+    case sbp::kTraditional + 6: return op_info_of<sbp::kTraditional + 6>(6, 6, false);
+    default: return OpInfo{};
+  }
+}
+int closure_b(int order) { return op_info(order).b; }
+
+// Norm weight w(pos) of the operator `order` on N nodes (H = h diag(w)).
+double norm_weight_any(int order, int pos, int N) {
+  switch (order) {
+    case 2: return sbp::norm_weight<2>(pos, N);
+    case 3: return sbp::norm_weight<3>(pos, N);
+    case 4: return sbp::norm_weight<4>(pos, N);
+    case 5: return sbp::norm_weight<5>(pos, N);
+    case 6: return sbp::norm_weight<6>(pos, N);
+    case 7: return sbp::norm_weight<7>(pos, N);
+    case sbp::kTraditional + 2: return sbp::norm_weight<sbp::kTraditional + 2>(pos, N);
+    case sbp::kTraditional + 4: return sbp::norm_weight<sbp::kTraditional + 4>(pos, N);
+    case sbp::kTraditional + 6: return sbp::norm_weight<sbp::kTraditional + 6>(pos, N);
+    default: return 0.0;
+  }
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -104,6 +156,7 @@ struct SbpGrid {
   int32_t* rec_off = nullptr;
   int rec_n = 0;
   void* traces = nullptr;
+  bool traces_owned = false;  // traces allocated by the library (sbp_set_receivers with traces = NULL)
   int n_t = 0;
   bool use_tiled = true;
   void* sclose = nullptr;  // tiled kernel scratch (s-closure sums), owned by the library
@@ -163,8 +216,7 @@ sbp::StageArgs<T> make_args(const SbpGrid* g, const void* q, void* qout, int mod
     A.bc_kind[f] = g->desc.bc_kind[f];
     A.bc_gamma[f] = (T)g->desc.bc_gamma[f];
   }
-  double w0 = g->desc.order == 2 ? sbp::OpCoef<2>::w(0) : g->desc.order == 4 ? sbp::OpCoef<4>::w(0)
-                                                                               : sbp::OpCoef<6>::w(0);
+  const double w0 = op_info(g->desc.order).w0;
   for (int x = 0; x < 3; ++x) {
     A.inv_h[x] = (T)(N[x] - 1);
     A.inv_h0[x] = (T)((double)(N[x] - 1) / w0);
@@ -375,6 +427,34 @@ int adjoint_impl(SbpGrid* g, int mode, int stage, double dt, const void* u, void
   return SBP_OK;
 }
 
+// Copy the 9 B state fields between the bound buffer dev (grid layout) and a caller buffer
+// ext: host or device memory (SBP_MEM_HOST), in the grid layout (9 B fields of fs elements) or
+// packed [field][s][r][q] (SBP_LAYOUT_DENSE).  A copy to host memory synchronises the stream.
+int copy_state(SbpGrid* g, void* dev, const void* ext, int flags, bool in, cudaStream_t st) {
+  const bool host = (flags & SBP_MEM_HOST) != 0;
+  const bool dense = (flags & SBP_LAYOUT_DENSE) != 0;
+  const cudaMemcpyKind kind = host ? (in ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost) : cudaMemcpyDeviceToDevice;
+  const int nf = 9 * g->nb;
+  const size_t e = (size_t)g->elem;
+  cudaError_t err = cudaSuccess;
+  if (!dense) {
+    const size_t bytes = (size_t)nf * g->dims.fs * e;
+    err = in ? cudaMemcpyAsync(dev, ext, bytes, kind, st) : cudaMemcpyAsync(const_cast<void*>(ext), dev, bytes, kind, st);
+  } else {
+    // one pitched copy per field: nr*ns rows of nq elements, row pitch ldq in the grid layout
+    const size_t row = (size_t)g->desc.nq * e, pitch = (size_t)g->dims.ldq * e;
+    const size_t rows = (size_t)g->desc.nr * g->desc.ns, field = row * rows;
+    for (int f = 0; f < nf && err == cudaSuccess; ++f) {
+      char* d = (char*)dev + (size_t)f * g->dims.fs * e;
+      char* x = (char*)const_cast<void*>(ext) + (size_t)f * field;
+      err = in ? cudaMemcpy2DAsync(d, pitch, x, row, row, rows, kind, st)
+               : cudaMemcpy2DAsync(x, row, d, pitch, row, rows, kind, st);
+    }
+  }
+  if (err == cudaSuccess && host && !in) err = cudaStreamSynchronize(st);
+  return err == cudaSuccess ? SBP_OK : cuda_fail(err, in ? "state upload" : "state download");
+}
+
 }  // namespace
 
 extern "C" {
@@ -382,9 +462,12 @@ extern "C" {
 const char* sbp_last_error(void) { return g_last_error.c_str(); }
 
 int sbp_min_nodes(int32_t order, int32_t* out) {
-  if (order != 2 && order != 4 && order != 6) return fail(SBP_ERR_ARG, "order must be 2, 4 or 6");
+  const OpInfo I = op_info(order);
+  if (!I.ok)
+    return fail(SBP_ERR_ARG, "order must be 2..7 (upwind, Table 1) or %d, %d, %d (traditional, Table 2)",
+                SBP_TRADITIONAL + 2, SBP_TRADITIONAL + 4, SBP_TRADITIONAL + 6);
   if (!out) return fail(SBP_ERR_ARG, "null output");
-  *out = 2 * closure_b(order) + stencil_reach(order);
+  *out = 2 * I.b + I.reach;
   return SBP_OK;
 }
 
@@ -445,6 +528,7 @@ int sbp_destroy(SbpGrid* g) {
   cudaFree(g->src_off);
   cudaFree(g->src_w);
   cudaFree(g->rec_off);
+  if (g->traces_owned) cudaFree(g->traces);
   cudaFree(g->sclose);
   delete g;
   return SBP_OK;
@@ -493,7 +577,8 @@ int sbp_bind(SbpGrid* g, void* q0, void* q1, void* dq, void* met, void* mat) {
 int sbp_metrics(SbpGrid* g, const double* xyz, double* jmet, void* stream) {
   if (int rc = check_ready(g)) return rc;
   if (!xyz || !jmet) return fail(SBP_ERR_ARG, "null coordinate or metric buffer");
-  cudaError_t e = sbp::launch_metrics(xyz, jmet, g->dims, g->desc.order, g->status, (cudaStream_t)stream);
+  cudaError_t e =
+      sbp::launch_metrics(xyz, jmet, g->dims, op_info(g->desc.order).metric_order, g->status, (cudaStream_t)stream);
   return e == cudaSuccess ? SBP_OK : cuda_fail(e, "metrics");
 }
 
@@ -648,24 +733,20 @@ int sbp_set_sources(SbpGrid* g, int32_t n, const SbpSource* srcs, const double* 
       return fail(SBP_ERR_UNSUPPORTED, "sources of one batch must share their time function");
   }
   const int order = g->desc.order;
-  const int mo = order + 1;
+  const int mo = op_info(order).accuracy + 1;
   const int N[3] = {g->desc.nq, g->desc.nr, g->desc.ns};
   const int n1 = mo + 1, per = n1 * n1 * n1;
   std::vector<long long> off((size_t)per * n);
   std::vector<double> w((size_t)per * n * 6);
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = cudaStreamSynchronize(st);
-  auto wgt = [&](int a, int pos) {
-    const double w0 = order == 2 ? sbp::norm_weight<2>(pos, N[a])
-                      : order == 4 ? sbp::norm_weight<4>(pos, N[a]) : sbp::norm_weight<6>(pos, N[a]);
-    return w0 / (N[a] - 1);
-  };
+  auto wgt = [&](int a, int pos) { return norm_weight_any(order, pos, N[a]) / (N[a] - 1); };
   for (int m = 0; m < n && e == cudaSuccess; ++m) {
     const SbpSource* src = &srcs[m];
     int start[3];
-    double phi[3][8];
+    double phi[3][10];  // up to accuracy + 2 = 9 nodes per axis
     for (int a = 0; a < 3; ++a) sbp::delta_1d(src->ref[a], N[a], mo, &start[a], phi[a]);
-    double Jrow[8];
+    double Jrow[10];
     for (int kk = 0, c = 0; kk < n1; ++kk)
       for (int jj = 0; jj < n1; ++jj) {
         // the Jacobian along this q row of the source's stencil box, one copy per row
@@ -713,7 +794,8 @@ int sbp_set_batch(SbpGrid* g, int32_t nb) {
 
 int sbp_set_receivers(SbpGrid* g, int32_t n, const int32_t* ijk, void* traces, int32_t n_t) {
   if (int rc = check_ready(g)) return rc;
-  if (n < 0 || (n > 0 && (!ijk || !traces || n_t <= 0))) return fail(SBP_ERR_ARG, "bad receiver arguments");
+  if (n < 0 || (n > 0 && (!ijk || n_t <= 0))) return fail(SBP_ERR_ARG, "bad receiver arguments");
+  if (n > 65535) return fail(SBP_ERR_ARG, "at most 65535 receivers");
   // validate every receiver before the current ones are dropped
   std::vector<int32_t> off(n);
   for (int r = 0; r < n; ++r) {
@@ -722,21 +804,104 @@ int sbp_set_receivers(SbpGrid* g, int32_t n, const int32_t* ijk, void* traces, i
       return fail(SBP_ERR_ARG, "receiver %d outside the grid", r);
     off[r] = (int32_t)((long long)k * g->dims.plane + (long long)j * g->dims.ldq + i);
   }
+  const size_t trace_bytes = (size_t)g->nb * n * 3 * (size_t)(n > 0 ? n_t : 0) * g->elem;
+  void* own = nullptr;
+  if (n > 0 && !traces) {
+    // the library keeps the traces; sbp_record_receivers copies them out
+    cudaError_t e = cudaMalloc(&own, trace_bytes);
+    if (e == cudaSuccess) e = cudaMemset(own, 0, trace_bytes);
+    if (e != cudaSuccess) {
+      cudaFree(own);
+      return cuda_fail(e, "trace buffer");
+    }
+  }
   cudaFree(g->rec_off);
+  if (g->traces_owned) cudaFree(g->traces);
   g->rec_off = nullptr;
+  g->traces = nullptr;
+  g->traces_owned = false;
   g->rec_n = 0;
+  g->n_t = 0;
   if (n == 0) return SBP_OK;
   cudaError_t e = cudaMalloc(&g->rec_off, sizeof(int32_t) * n);
   if (e == cudaSuccess) e = cudaMemcpy(g->rec_off, off.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_fail(e, "receiver buffers");
+  if (e != cudaSuccess) {
+    cudaFree(own);
+    return cuda_fail(e, "receiver buffers");
+  }
   g->rec_n = n;
-  g->traces = traces;
+  g->traces = own ? own : traces;
+  g->traces_owned = own != nullptr;
   g->n_t = n_t;
   return SBP_OK;
 }
 
+int sbp_set_receivers_xyz(SbpGrid* g, int32_t n, const double* xyz, const double* coords, int32_t face,
+                          void* traces, int32_t n_t, int32_t* ijk_out) {
+  if (int rc = check_ready(g)) return rc;
+  if (n < 0 || n > 65535) return fail(SBP_ERR_ARG, "receiver count must lie in 0..65535");
+  if (n == 0) return sbp_set_receivers(g, 0, nullptr, nullptr, 0);
+  if (!xyz || !coords || n_t <= 0) return fail(SBP_ERR_ARG, "bad receiver arguments");
+  if (face < -1 || face > 5) return fail(SBP_ERR_ARG, "face must be -1 (every node) or 0..5");
+  for (int r = 0; r < 3 * n; ++r)
+    if (!isfinite(xyz[r])) return fail(SBP_ERR_ARG, "receiver %d: position is not finite", r / 3);
+  double* tg = nullptr;
+  unsigned long long* scratch = nullptr;
+  cudaError_t e = cudaMalloc(&tg, sizeof(double) * 3 * n);
+  if (e == cudaSuccess) e = cudaMalloc(&scratch, sizeof(unsigned long long) * 2 * n);
+  if (e == cudaSuccess) e = cudaMemcpy(tg, xyz, sizeof(double) * 3 * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = sbp::launch_locate(coords, g->dims, face, tg, n, scratch, scratch + n, nullptr);
+  std::vector<unsigned long long> node(n);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(node.data(), scratch + n, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost);
+  cudaFree(tg);
+  cudaFree(scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "receiver location");
+  std::vector<int32_t> ijk(3 * n);
+  const long long nq = g->desc.nq, nr = g->desc.nr;
+  for (int r = 0; r < n; ++r) {
+    if (node[r] == ~0ULL) return fail(SBP_ERR_ARG, "receiver %d: no node at a finite distance", r);
+    const long long t = (long long)node[r];
+    ijk[3 * r] = (int32_t)(t % nq);
+    ijk[3 * r + 1] = (int32_t)((t / nq) % nr);
+    ijk[3 * r + 2] = (int32_t)(t / (nq * nr));
+  }
+  if (int rc = sbp_set_receivers(g, n, ijk.data(), traces, n_t)) return rc;
+  if (ijk_out) memcpy(ijk_out, ijk.data(), sizeof(int32_t) * 3 * n);
+  return SBP_OK;
+}
+
+int sbp_record_receivers(SbpGrid* g, void* dst, int32_t flags, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (g->rec_n == 0) return fail(SBP_ERR_STATE, "no receivers set (sbp_set_receivers)");
+  if (!dst) return fail(SBP_ERR_ARG, "null destination");
+  if (flags & ~SBP_MEM_HOST) return fail(SBP_ERR_ARG, "flags: only SBP_MEM_HOST applies to traces");
+  const size_t bytes = (size_t)g->nb * g->rec_n * 3 * (size_t)g->n_t * g->elem;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool host = (flags & SBP_MEM_HOST) != 0;
+  cudaError_t e = cudaMemcpyAsync(dst, g->traces, bytes, host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && host) e = cudaStreamSynchronize(st);
+  return e == cudaSuccess ? SBP_OK : cuda_fail(e, "trace copy");
+}
+
+int sbp_set_state(SbpGrid* g, const void* src, int32_t flags, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!src) return fail(SBP_ERR_ARG, "null source");
+  if (flags & ~(SBP_MEM_HOST | SBP_LAYOUT_DENSE)) return fail(SBP_ERR_ARG, "unknown flags");
+  return copy_state(g, g->q[g->cur], src, flags, true, (cudaStream_t)stream);
+}
+
+int sbp_get_state(SbpGrid* g, void* dst, int32_t flags, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!dst) return fail(SBP_ERR_ARG, "null destination");
+  if (flags & ~(SBP_MEM_HOST | SBP_LAYOUT_DENSE)) return fail(SBP_ERR_ARG, "unknown flags");
+  return copy_state(g, g->q[g->cur], dst, flags, false, (cudaStream_t)stream);
+}
+
 int sbp_rhs_adjoint(SbpGrid* g, const void* w, void* out, void* scratch, void* stream) {
   if (int rc = check_ready(g)) return rc;
+  if (!op_info(g->desc.order).adjoint) return fail(SBP_ERR_UNSUPPORTED, "the adjoint is built for orders 2, 4, 6");
   if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
   if (!w || !out || !scratch || w == out || w == scratch || out == scratch)
     return fail(SBP_ERR_ARG, "rhs_adjoint needs distinct input, output and scratch buffers");
@@ -750,6 +915,7 @@ int sbp_adjoint_stage(SbpGrid* g, int32_t stage, double dt, const void* u_stage,
                       void* scratch, const double* rlmj, double* grad, void* stream) {
   if (int rc = check_ready(g)) return rc;
   if (g->nb != 1) return fail(SBP_ERR_UNSUPPORTED, "the adjoint runs on unbatched grids");
+  if (!op_info(g->desc.order).adjoint) return fail(SBP_ERR_UNSUPPORTED, "the adjoint is built for orders 2, 4, 6");
   if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
   if (stage < 0 || stage > 4) return fail(SBP_ERR_ARG, "stage must be 0..4");
   if (!(dt > 0) || !isfinite(dt)) return fail(SBP_ERR_ARG, "dt must be positive and finite");

@@ -26,6 +26,9 @@ cudaError_t launch_metrics(const double* xyz, double* jmet, const Dims& d, int o
     case 2: metrics_kernel<2><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
     case 4: metrics_kernel<4><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
     case 6: metrics_kernel<6><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
+    case 3: metrics_kernel<3><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
+    case 5: metrics_kernel<5><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
+    case 7: metrics_kernel<7><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -145,6 +148,18 @@ cudaError_t launch_energy(const T* q, const T* mat, const Dims& d, int order, do
     case 2: energy_kernel<T, 2><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
     case 4: energy_kernel<T, 4><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
     case 6: energy_kernel<T, 6><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
+    case 3: energy_kernel<T, 3><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
+    case 5: energy_kernel<T, 5><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
+    case 7: energy_kernel<T, 7><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
+    case kTraditional + 2:
+      energy_kernel<T, kTraditional + 2><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status);
+      break;
+    case kTraditional + 4:
+      energy_kernel<T, kTraditional + 4><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status);
+      break;
+    case kTraditional + 6:
+      energy_kernel<T, kTraditional + 6><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status);
+      break;
     default: return cudaErrorInvalidValue;
   }
   cudaError_t e = cudaGetLastError();
@@ -207,6 +222,77 @@ cudaError_t launch_receivers(const T* q, const Dims& d, const int32_t* off, int 
   receivers_kernel<T><<<(nb * n * 3 + 127) / 128, 128, 0, st>>>(q, d, off, n, nb, bstride, traces, n_t, step);
   return cudaGetLastError();
 }
+// ---------------------------------------------------------------------------
+// Receivers by position: the node nearest (Euclidean, in the node coordinates xyz) to each
+// target point, among the nodes of one face (0..5) or of the whole grid (face < 0).  Pass 1
+// finds the smallest squared distance per target (atomicMin on the bits of a non-negative
+// double, which order like the values); pass 2 takes the smallest node index at exactly that
+// distance, so the choice is deterministic.
+__device__ __forceinline__ long long locate_candidate(const Dims& d, int face, long long t) {
+  // t-th candidate node as a linear [s][r][q] node index (not an offset)
+  if (face < 0) return t;
+  const int xi = face / 2;
+  const int side = face % 2;
+  const long long nq = d.nq, nr = d.nr, ns = d.ns;
+  if (xi == 0) {  // (k, j) plane at i = 0 or nq - 1
+    const long long j = t % nr, k = t / nr;
+    return (k * nr + j) * nq + (side ? nq - 1 : 0);
+  }
+  if (xi == 1) {  // (k, i) plane at j = 0 or nr - 1
+    const long long i = t % nq, k = t / nq;
+    return (k * nr + (side ? nr - 1 : 0)) * nq + i;
+  }
+  return (long long)(side ? ns - 1 : 0) * nr * nq + t;  // (j, i) plane at k = 0 or ns - 1
+}
+
+__device__ __forceinline__ double locate_dist2(const double* __restrict__ xyz, const Dims& d, long long node,
+                                               const double* __restrict__ target) {
+  const long long i = node % d.nq, j = (node / d.nq) % d.nr, k = node / ((long long)d.nq * d.nr);
+  const long long off = k * d.plane + j * d.ldq + i;
+  const double dx = xyz[off] - target[0], dy = xyz[d.fs + off] - target[1], dz = xyz[2 * d.fs + off] - target[2];
+  return dx * dx + dy * dy + dz * dz;
+}
+
+__global__ void locate_min_kernel(const double* __restrict__ xyz, Dims d, int face, long long ncand,
+                                  const double* __restrict__ targets, unsigned long long* __restrict__ best) {
+  const int r = blockIdx.y;
+  const double* tg = targets + 3 * r;
+  double m = 1.0 / 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < ncand; t += (long long)gridDim.x * blockDim.x)
+    m = fmin(m, locate_dist2(xyz, d, locate_candidate(d, face, t), tg));
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m < 1.0 / 0.0) atomicMin(best + r, (unsigned long long)__double_as_longlong(m));
+}
+
+__global__ void locate_index_kernel(const double* __restrict__ xyz, Dims d, int face, long long ncand,
+                                    const double* __restrict__ targets, const unsigned long long* __restrict__ best,
+                                    unsigned long long* __restrict__ index) {
+  const int r = blockIdx.y;
+  const double* tg = targets + 3 * r;
+  const unsigned long long b = best[r];
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < ncand; t += (long long)gridDim.x * blockDim.x) {
+    const long long node = locate_candidate(d, face, t);
+    if ((unsigned long long)__double_as_longlong(locate_dist2(xyz, d, node, tg)) == b)
+      atomicMin(index + r, (unsigned long long)node);
+  }
+}
+
+cudaError_t launch_locate(const double* xyz, const Dims& d, int face, const double* targets, int n,
+                          unsigned long long* best, unsigned long long* index, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const long long ncand = face < 0 ? (long long)d.nq * d.nr * d.ns
+                          : face < 2 ? (long long)d.nr * d.ns : face < 4 ? (long long)d.nq * d.ns
+                                                                         : (long long)d.nq * d.nr;
+  cudaError_t e = cudaMemsetAsync(best, 0xff, sizeof(unsigned long long) * n, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(index, 0xff, sizeof(unsigned long long) * n, st);
+  if (e != cudaSuccess) return e;
+  const long long want = (ncand + 255) / 256;
+  const dim3 grid((unsigned)(want < 1216 ? want : 1216), (unsigned)n);
+  locate_min_kernel<<<grid, 256, 0, st>>>(xyz, d, face, ncand, targets, best);
+  locate_index_kernel<<<grid, 256, 0, st>>>(xyz, d, face, ncand, targets, best, index);
+  return cudaGetLastError();
+}
+
 template cudaError_t launch_receivers<float>(const float*, const Dims&, const int32_t*, int, int, long long, float*,
                                              int, long long, cudaStream_t);
 template cudaError_t launch_receivers<double>(const double*, const Dims&, const int32_t*, int, int, long long,

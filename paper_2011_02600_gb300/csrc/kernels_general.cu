@@ -49,6 +49,12 @@ cudaError_t launch_stage_general(const StageArgs<T>& A, int order, const BoxList
     case 2: stage_general_kernel<T, 2><<<grid, threads, 0, st>>>(A, L); break;
     case 4: stage_general_kernel<T, 4><<<grid, threads, 0, st>>>(A, L); break;
     case 6: stage_general_kernel<T, 6><<<grid, threads, 0, st>>>(A, L); break;
+    case 3: stage_general_kernel<T, 3><<<grid, threads, 0, st>>>(A, L); break;
+    case 5: stage_general_kernel<T, 5><<<grid, threads, 0, st>>>(A, L); break;
+    case 7: stage_general_kernel<T, 7><<<grid, threads, 0, st>>>(A, L); break;
+    case kTraditional + 2: stage_general_kernel<T, kTraditional + 2><<<grid, threads, 0, st>>>(A, L); break;
+    case kTraditional + 4: stage_general_kernel<T, kTraditional + 4><<<grid, threads, 0, st>>>(A, L); break;
+    case kTraditional + 6: stage_general_kernel<T, kTraditional + 6><<<grid, threads, 0, st>>>(A, L); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -508,8 +508,21 @@ cudaError_t launch_kind(const StageArgs<T>& A, int order, const TmaSet& tm, cuda
     case 2: return launch_tiled_order<T, 2, KIND>(A, tm, st);
     case 4: return launch_tiled_order<T, 4, KIND>(A, tm, st);
     case 6: return launch_tiled_order<T, 6, KIND>(A, tm, st);
-    default: return cudaErrorNotSupported;
+    default: break;
   }
+  // the odd orders of Table 1 and the traditional operators of Table 2: forward stage only
+  if constexpr (KIND == 0) {
+    switch (order) {
+      case 3: return launch_tiled_order<T, 3, 0>(A, tm, st);
+      case 5: return launch_tiled_order<T, 5, 0>(A, tm, st);
+      case 7: return launch_tiled_order<T, 7, 0>(A, tm, st);
+      case kTraditional + 2: return launch_tiled_order<T, kTraditional + 2, 0>(A, tm, st);
+      case kTraditional + 4: return launch_tiled_order<T, kTraditional + 4, 0>(A, tm, st);
+      case kTraditional + 6: return launch_tiled_order<T, kTraditional + 6, 0>(A, tm, st);
+      default: break;
+    }
+  }
+  return cudaErrorNotSupported;
 }
 
 template <typename T>

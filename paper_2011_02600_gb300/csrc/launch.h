@@ -60,4 +60,11 @@ template <typename T>
 cudaError_t launch_receivers(const T* q, const Dims& d, const int32_t* off, int n, int nb, long long bstride,
                              T* traces, int n_t, long long step, cudaStream_t st);
 
+// Nearest node to each of n target points (3 FP64 values each, device) among the nodes of
+// face `face` (0..5) or of the whole grid (face < 0), from the node coordinates xyz (3 FP64
+// fields, device).  best, index: n device words each (scratch); index[r] receives the linear
+// [s][r][q] node index of target r (smallest index among nodes at exactly the same distance).
+cudaError_t launch_locate(const double* xyz, const Dims& d, int face, const double* targets, int n,
+                          unsigned long long* best, unsigned long long* index, cudaStream_t st);
+
 }  // namespace sbp

@@ -18,23 +18,33 @@ def ctypes_stream(s):
     return s.cuda_stream
 
 
+def _on_host(x):
+    """True for numpy arrays and CPU tensors."""
+    return not isinstance(x, torch.Tensor) or x.device.type == "cpu"
+
+
 class ElasticSolver:
     """One curvilinear block on one GPU.
 
-    nodes = (nq, nr, ns); order in {2, 4, 6}; precision in {32, 64};
+    nodes = (nq, nr, ns); order: 2..7 for the upwind pairs of Table 1, 2, 4 or 6 with
+    operator="traditional" for the central operators of Table 2; precision in {32, 64};
     bc: six face conditions ("free",) / ("char", gamma).
     """
 
-    def __init__(self, nodes, order, precision=32, bc=None, device="cuda", batch=1):
+    def __init__(self, nodes, order, precision=32, bc=None, device="cuda", batch=1, operator="upwind"):
         if bc is None:
             bc = [("char", 0.0)] * 5 + [("free",)]
+        if operator not in ("upwind", "traditional"):
+            raise ValueError(f"unknown operator family {operator!r}")
         self.nodes = tuple(int(n) for n in nodes)
         self.order = order
+        self.operator = operator
+        self.code = order + (L.SBP_TRADITIONAL if operator == "traditional" else 0)
         self.precision = precision
         self.bc = list(bc)
         self.device = torch.device(device)
         self.dtype = torch.float32 if precision == 32 else torch.float64
-        self.h = L.sbp_create_grid(self.nodes, order, precision, self.bc)
+        self.h = L.sbp_create_grid(self.nodes, self.code, precision, self.bc)
         self.batch = int(batch)
         if self.batch != 1:
             L.sbp_set_batch(self.h, self.batch)
@@ -151,7 +161,7 @@ class ElasticSolver:
         (between steps; see checkpoint.py for the format)."""
         from . import checkpoint
         t, step = L.sbp_get_time(self.h)
-        header = dict(nodes=list(self.nodes), order=self.order, precision=self.precision, batch=self.batch,
+        header = dict(nodes=list(self.nodes), order=self.code, precision=self.precision, batch=self.batch,
                       ldq=self.ldq, fs=self.fs, time=t, step=step)
         data = checkpoint.pack(header, [self.qbuf[self.current].cpu().numpy(), self.dq.cpu().numpy()])
         with open(path, "wb") as f:
@@ -163,7 +173,7 @@ class ElasticSolver:
         from . import checkpoint
         with open(path, "rb") as f:
             header, (q, dq) = checkpoint.unpack(f.read())
-        want = dict(nodes=list(self.nodes), order=self.order, precision=self.precision, batch=self.batch,
+        want = dict(nodes=list(self.nodes), order=self.code, precision=self.precision, batch=self.batch,
                     ldq=self.ldq, fs=self.fs)
         for k, v in want.items():
             if header.get(k) != v:
@@ -194,11 +204,49 @@ class ElasticSolver:
         L.sbp_set_sources(self.h, [dict(ref=sc["ref"], moment=sc["moment"], stf=0, f0=f0, t0=t0) for sc in sources],
                           self.jmet, _stream())
 
+    def upload_state(self, src, dense=True):
+        """Copy the current state in from a host numpy array or a torch tensor (host or device):
+        [B * 9][ns][nr][nq] packed when dense, else the flat grid layout (sbp_set_state)."""
+        flags = (L.SBP_LAYOUT_DENSE if dense else 0) | (L.SBP_MEM_HOST if _on_host(src) else 0)
+        L.sbp_set_state(self.h, src, flags, _stream())
+
+    def download_state(self, dst, dense=True):
+        """Copy the current state out to dst (host numpy array or torch tensor; sbp_get_state)."""
+        flags = (L.SBP_LAYOUT_DENSE if dense else 0) | (L.SBP_MEM_HOST if _on_host(dst) else 0)
+        L.sbp_get_state(self.h, dst, flags, _stream())
+        return dst
+
+    def set_receivers_at(self, points, coords, n_t, face=5):
+        """Receivers at the nodes nearest to the physical points (n x 3), searched on face `face`
+        (5: the top surface s = 1; -1: every node) of the node coordinates coords (3, ns, nr, nq).
+        The library keeps the traces (read them with record_receivers).  Returns the chosen
+        (i, j, k) per receiver."""
+        xyz_b = self.to_layout(torch.as_tensor(coords), torch.float64)
+        ijk = L.sbp_set_receivers_xyz(self.h, points, xyz_b, face, None, n_t)
+        self.traces = None
+        self._rec_shape = (len(ijk), n_t)
+        return ijk
+
+    def record_receivers(self, host=True):
+        """The traces recorded so far: [B][n][3][n_t] (without the batch axis when B = 1), a host
+        numpy array (host=True) or a device tensor."""
+        import numpy as np
+        n, n_t = self._rec_shape
+        shape = (self.batch, n, 3, n_t)
+        if host:
+            out = np.zeros(shape, dtype=np.float32 if self.precision == 32 else np.float64)
+            L.sbp_record_receivers(self.h, out, L.SBP_MEM_HOST, _stream())
+        else:
+            out = torch.zeros(shape, dtype=self.dtype, device=self.device)
+            L.sbp_record_receivers(self.h, out, 0, _stream())
+        return out if self.batch > 1 else out[0]
+
     def set_receivers(self, ijk, n_t):
         """Traces view [member][receiver][component][step] (the member axis only when batched)."""
         n = len(ijk)
         self.traces = torch.zeros(self.batch * max(n, 1) * 3 * n_t, dtype=self.dtype, device=self.device)
         L.sbp_set_receivers(self.h, ijk, self.traces, n_t)
+        self._rec_shape = (n, n_t)
         tr = self.traces.view(self.batch, -1, 3, n_t)[:, :n]
         return tr if self.batch > 1 else tr[0]
 

@@ -32,12 +32,14 @@ def _fill_chunks(s, buf, nf, fn):
             v[f, k0:k1].copy_(vals[f].expand(k1 - k0, nr, nq))
 
 
-def build_solver(cfg, precision=None, device="cuda", keep_metrics=False, batch=1):
-    """ElasticSolver for a WorkloadConfig with metrics and material set.
+def build_solver(cfg, precision=None, device="cuda", keep_metrics=False, batch=1, operator="upwind"):
+    """ElasticSolver for a WorkloadConfig with metrics and material set (operator: "upwind" or
+    "traditional", of the config's order).
 
     Returns (solver, info) with info = dict(dt=..., hmin=..., cpmax=...)."""
     precision = precision or cfg.precisions[0]
-    s = ElasticSolver(cfg.nodes, cfg.order, precision, list(cfg.bc), device=device, batch=batch)
+    s = ElasticSolver(cfg.nodes, cfg.order, precision, list(cfg.bc), device=device, batch=batch,
+                      operator=operator)
     fmap = make_map(cfg, xp=torch)
     fmed = make_medium(cfg, xp=torch)
     import paper_2011_02600_gb300._lib as L

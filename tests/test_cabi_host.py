@@ -31,10 +31,17 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_min_nodes(lib):
+    """2b + max(r, q) for every operator code, against the oracle's own minimum sizes."""
+    from oracle.operators import min_nodes, traditional_min_nodes
     assert L.sbp_min_nodes(2) == 6 and L.sbp_min_nodes(4) == 11 and L.sbp_min_nodes(6) == 16
-    with pytest.raises(L.SbpError) as e:
-        L.sbp_min_nodes(3)
-    assert e.value.code == 1
+    for order in range(2, 8):
+        assert L.sbp_min_nodes(order) == min_nodes(order)
+    for order in (2, 4, 6):
+        assert L.sbp_min_nodes(L.SBP_TRADITIONAL + order) == traditional_min_nodes(order)
+    for bad in (1, 8, 9, 100, 103, 105, 107):
+        with pytest.raises(L.SbpError) as e:
+            L.sbp_min_nodes(bad)
+        assert e.value.code == 1
 
 
 def _expect(code, fn, *a):
@@ -46,11 +53,13 @@ def _expect(code, fn, *a):
 def test_create_grid_validation(lib):
     free = [("free",)] * 6
     _expect(1, L.sbp_create_grid, (15, 20, 20), 6, 32, free)        # too few nodes for order 6
-    _expect(1, L.sbp_create_grid, (20, 20, 20), 5, 32, free)        # odd order
-    # the odd orders and the traditional operators (order codes 100 + 2, 4, 6) have kernel tables
-    # but are not launched: the library refuses them until their GPU parity runs
-    for order in (3, 7, 102, 104, 106):
-        _expect(1, L.sbp_create_grid, (20, 20, 20), order, 32, free)
+    _expect(1, L.sbp_create_grid, (20, 20, 20), 8, 32, free)        # order 8: no closure
+    _expect(1, L.sbp_create_grid, (20, 20, 20), 103, 32, free)      # no odd traditional operator
+    _expect(1, L.sbp_create_grid, (15, 15, 15), 7, 32, free)        # order 7 needs 16 nodes
+    _expect(1, L.sbp_create_grid, (14, 15, 15), 106, 32, free)      # traditional 6 needs 15
+    # the odd upwind orders and the traditional operators (codes 100 + 2, 4, 6) are accepted
+    for order in (3, 5, 7, 102, 104, 106):
+        L.sbp_destroy(L.sbp_create_grid((20, 20, 20), order, 32, free))
     _expect(1, L.sbp_create_grid, (20, 20, 20), 4, 16, free)        # precision
     _expect(1, L.sbp_create_grid, (20, 20, 20), 4, 32, [("char", 1.5)] + free[1:])
     _expect(1, L.sbp_create_grid, (40000, 40000, 4000), 2, 32, free)  # over 2^31 elements per field
