@@ -12,8 +12,8 @@ nodes * 5 * steps / time.
     python bench.py --workload surrogate97_o4
 
 The second form times one misfit gradient of the adjoint workload (129 x 129 x 97, order 4,
-FP32 forward with FP64 misfit, 1500 steps, sqrt(N) checkpoints): forward run, checkpoint
-recomputation and adjoint stages, with the adjoint stage kernels' roofline.  The third times the
+FP32 forward with FP64 misfit, 1500 steps, sqrt(N) checkpoints, its eight sources as one batch):
+forward run, checkpoint recomputation and adjoint stages, with the adjoint stage kernels' roofline.  The third times the
 surrogate network's training iterations at full size and its largest GEMM against the BF16 peak.
 
 One JSON line on rank 0.  With --gpus N > 1 (torchrun) every rank runs an
@@ -248,10 +248,10 @@ def run_adjoint(args, local):
     from workloads.configs import config_by_name
     cfg = config_by_name("adjoint129_o4")
     nsteps = args.adj_steps or cfg.steps
-    p, _, _ = workload_problem(cfg, 32, nsteps=nsteps)
+    p, _, _ = workload_problem(cfg, 32, source_index="all", nsteps=nsteps)   # the eight sources, one batch
     s = p.s
     nq, nr, ns = cfg.nodes
-    nodes = nq * nr * ns
+    nodes = nq * nr * ns * p.B            # node-member pairs
     p.forward()                       # warm-up: one untimed forward run and gradient
     p.gradient()
     torch.cuda.synchronize()
@@ -284,9 +284,11 @@ def run_adjoint(args, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "adjoint129_o4", "nodes": list(cfg.nodes), "order": cfg.order,
-                   "checkpoint_every": p.C, "receivers": len(p.receivers),
+                   "checkpoint_every": p.C, "receivers": len(p.receivers), "sources": p.B,
+                   "batch": "the sources' states advance together (one launch per kernel)",
                    "warmup": "one untimed forward run and gradient over the same steps",
-                   "what": "node-stages of the forward problem per second of forward run + gradient"},
+                   "what": "node-stages of the forward problem (nodes x sources x 5 x steps) per second of "
+                           "forward run + gradient"},
         "forward_ms": t_fwd, "gradient_ms": t_grad, "misfit": phi,
         "gradient_norm": float(g.double().norm()),
         "roofline": {"bound": "hbm", "kernel": "adjoint stage (prep + stage)", "achieved": achieved,
@@ -355,16 +357,21 @@ def run_surrogate_kernels(args, local):
     A_ = torch.randn(M, K, generator=g).to(torch.bfloat16).cuda()
     B_ = torch.randn(K, N, generator=g).to(torch.bfloat16).cuda()
     C_ = torch.empty(M, N, device="cuda")
-    for _ in range(3):
-        L.sbp_nn_gemm(M, N, K, A_, K, 0, B_, N, 0, C_, N, 0, None, 0, 0.0, _stream())
-    torch.cuda.synchronize()
-    reps = 20
-    ev[0].record(stream)
-    for _ in range(reps):
-        L.sbp_nn_gemm(M, N, K, A_, K, 0, B_, N, 0, C_, N, 0, None, 0, 0.0, _stream())
-    ev[1].record(stream)
-    torch.cuda.synchronize()
-    g_ms = ev[0].elapsed_time(ev[1]) / reps
+    def time_gemm(path, reps=20):
+        L.sbp_nn_set_gemm_path(path)
+        for _ in range(3):
+            L.sbp_nn_gemm(M, N, K, A_, K, 0, B_, N, 0, C_, N, 0, None, 0, 0.0, _stream())
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        for _ in range(reps):
+            L.sbp_nn_gemm(M, N, K, A_, K, 0, B_, N, 0, C_, N, 0, None, 0, 0.0, _stream())
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        L.sbp_nn_set_gemm_path(0)
+        return ev[0].elapsed_time(ev[1]) / reps
+    g_ms = time_gemm(2)                  # tcgen05 kernel
+    legacy_ms = time_gemm(1)             # mma.sync kernel, for comparison
+    status = L.sbp_nn_status()
     tflops = 2.0 * M * N * K / (g_ms / 1e3) / 1e12
     peaks = _peaks()
     peak = peaks["bf16_tflops"] if peaks else 1900.0
@@ -377,10 +384,12 @@ def run_surrogate_kernels(args, local):
                    "hidden": net.hidden, "channels": net.C, "params": net.n_params()},
         "ms_per_iteration": it_ms, "gemm_tflop_per_iteration": it_flops / 1e12,
         "gemm_tflops_in_iterations": it_flops / (it_ms / 1e3) / 1e12,
-        "roofline": {"bound": "tensor", "kernel": "gemm_bf16_pipe_kernel (cp.async, ldmatrix, mma.sync m16n8k16)",
+        "roofline": {"bound": "tensor", "kernel": "gemm_tc_kernel (TMA, tcgen05.mma kind::f16, TMEM accumulator)",
                      "shape": [M, N, K], "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
-                     "frac": tflops / peak, "avg_launch_ms": g_ms,
+                     "frac": tflops / peak, "avg_launch_ms": g_ms, "status_bits": status,
                      "peak_source": "measured (cuBLAS bf16 burst)" if peaks else "fallback"},
+        "legacy_mma_sync_gemm": {"avg_launch_ms": legacy_ms,
+                                 "achieved_tflops": 2.0 * M * N * K / (legacy_ms / 1e3) / 1e12},
     }
     print(json.dumps(line), flush=True)
 

@@ -97,7 +97,9 @@ typedef struct SbpSource {
 } SbpSource;
 
 /* Smallest node count per axis for an operator code: 2b + max(r, q) (b closure
- * rows, interior stencil reach r and q).  ARG for an unknown code. */
+ * rows, interior stencil reach r and q), for a traditional operator at least that
+ * of the upwind pair of the same order, whose D_c forms the metric terms.  ARG for
+ * an unknown code. */
 int sbp_min_nodes(int32_t order, int32_t* out);
 
 /* Validate desc and create a grid handle (host memory only).  ARG on bad sizes,
@@ -237,27 +239,31 @@ int sbp_get_state(SbpGrid* grid, void* dst, int32_t flags, void* stream);
  * product of the 9-field vectors.  Built from the dual-pair relation of
  * Section 4.1 (Eq. upw_SBP): D-^T = B H^-1 - H D+ H^-1, D+^T = B H^-1 - H D- H^-1,
  * so it reuses the forward rows on H^-1 P~ w plus face terms.  w, out, scratch:
- * 9 fields each (device, distinct). */
+ * 9 B fields each (device, distinct; every member of a batch transformed).
+ * UNSUPPORTED for operator codes other than 2, 4, 6. */
 int sbp_rhs_adjoint(SbpGrid* grid, const void* w, void* out, void* scratch, void* stream);
 
-/* (Unbatched grids only.)  Adjoint of fused Runge-Kutta stage k (the exact discrete adjoint of the
+/* Adjoint of fused Runge-Kutta stage k (the exact discrete adjoint of the
  * 2N-storage stage; run k = 4..0 after the adjoint of a step's later stages):
  *   wbar <- wbar + B_k ubar;  ubar <- ubar + dt L^T wbar;
  *   grad += dt (d(L u_stage)/d(rho, lambda, mu))^T wbar;  wbar <- A_k wbar.
- * ubar, wbar, scratch: 9 fields (solver precision, device, updated in place);
- * u_stage: the forward stage input U_k (9 fields); rlmj: FP64 rho, lambda, mu, J
- * (4 fields); grad: FP64 3 fields (accumulated; may be NULL to skip the gradient,
- * then u_stage and rlmj may be NULL).  The impedances of the general penalty
- * are differentiated too. */
+ * ubar, wbar, scratch: 9 B fields (solver precision, device, updated in place;
+ * member b at fields 9b..9b+8 as for the bound state); u_stage: the forward
+ * stage inputs U_k of the B states (9 B fields); rlmj: FP64 rho, lambda, mu, J
+ * (4 fields); grad: FP64 3 fields, shared by the B states, which all add into it
+ * (the gradient of the summed misfit; may be NULL to skip the gradient, then
+ * u_stage and rlmj may be NULL).  The impedances of the general penalty are
+ * differentiated too.  UNSUPPORTED for operator codes other than 2, 4, 6. */
 int sbp_adjoint_stage(SbpGrid* grid, int32_t stage, double dt, const void* u_stage, void* ubar, void* wbar,
                       void* scratch, const double* rlmj, double* grad, void* stream);
 
-/* Receiver misfit of the state q (9 fields): for each receiver r and velocity
- * component c, diff = v_c - data[3r + c] (data: FP64 device, 3 per receiver);
- * acc[3r + c] += weight diff^2 / 2 (FP64 device, may be NULL) and, if ubar is
- * not NULL, ubar_c += weight diff at the receiver node (the adjoint source;
- * receivers that share a node add their sources atomically, so the order of
- * those additions is unspecified).  Needs sbp_set_receivers. */
+/* Receiver misfit of the B states q (9 B fields): for member b, receiver r and
+ * velocity component c, diff = v_c - data[(b n + r) 3 + c] (data: FP64 device,
+ * 3 n per member); acc[(b n + r) 3 + c] += weight diff^2 / 2 (FP64 device, may
+ * be NULL) and, if ubar (9 B fields) is not NULL, ubar_c of member b += weight
+ * diff at the receiver node (the adjoint source; receivers that share a node add
+ * their sources atomically, so the order of those additions is unspecified).
+ * Needs sbp_set_receivers. */
 int sbp_misfit(SbpGrid* grid, const void* q, const double* data, double weight, double* acc, void* ubar,
                void* stream);
 
@@ -309,10 +315,21 @@ int sbp_energy_noalloc(const void* q, const void* mat, int32_t nq, int32_t nr, i
  * A^T (A stored K x M) when transA; op(B) = B (K x N, ldb) or B^T (B stored
  * N x K) when transB.  A, B BF16; accumulation FP32 on tensor cores; C FP32
  * (c_bf16 = 0, beta 0 or 1) or BF16 (c_bf16 = 1, beta must be 0); bias FP32
- * per row or NULL. */
+ * per row or NULL.  Operands with leading dimensions that are multiples of 8
+ * elements and 16-byte aligned bases run on the tcgen05 tensor cores (TMA
+ * operand tiles, FP32 accumulator in tensor memory) when M, N >= 128 and
+ * K >= 64; other products on the mma.sync kernels (sbp_nn_set_gemm_path). */
 int sbp_nn_gemm(int32_t M, int32_t N, int32_t K, const void* A, int64_t lda, int32_t transA, const void* B,
                 int64_t ldb, int32_t transB, void* C, int64_t ldc, int32_t c_bf16, const float* bias, int32_t relu,
                 float beta, void* stream);
+/* Which kernels sbp_nn_gemm uses, for the whole process: 0 = automatic (above),
+ * 1 = the mma.sync kernels only, 2 = the tcgen05 kernel for every product whose
+ * operands it can load.  ARG for other values. */
+int sbp_nn_set_gemm_path(int32_t path);
+/* Device-side findings of the surrogate kernels, read and cleared (synchronises
+ * the device): bit 1 = a bounded wait of the tcgen05 GEMM gave up, so that
+ * GEMM skipped its output. */
+int sbp_nn_status(uint32_t* bits);
 /* 1D convolution lowering, activations laid out [channel][batch * T]:
  * im2col: Xc[(c kw + k)][b T + t] = X[c][b T + t + k - pad] (zero outside the
  * sample); col2im sums the kw shifted copies back (FP32 in and out). */

@@ -24,7 +24,8 @@ EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sb
             "sbp_misfit", "sbp_set_batch", "sbp_set_sources", "sbp_nn_gemm", "sbp_nn_im2col", "sbp_nn_col2im",
             "sbp_nn_upsample2", "sbp_nn_relu_backward", "sbp_nn_bias_grad", "sbp_nn_mse", "sbp_nn_adam",
             "sbp_nn_mlp_to_conv", "sbp_nn_cast_bf16", "sbp_nn_moment_combine", "sbp_selftest_wait_timeout", "sbp_last_error",
-            "sbp_set_receivers_xyz", "sbp_record_receivers", "sbp_set_state", "sbp_get_state")
+            "sbp_set_receivers_xyz", "sbp_record_receivers", "sbp_set_state", "sbp_get_state",
+            "sbp_nn_set_gemm_path", "sbp_nn_status")
 
 
 class SbpError(RuntimeError):
@@ -103,6 +104,8 @@ def lib(path=None):
         "sbp_record_receivers": [P, P, i32, P],
         "sbp_set_state": [P, P, i32, P],
         "sbp_get_state": [P, P, i32, P],
+        "sbp_nn_set_gemm_path": [i32],
+        "sbp_nn_status": [ctypes.POINTER(ctypes.c_uint32)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -316,6 +319,16 @@ def sbp_set_sources(h, sources, jmet, stream):
 def sbp_nn_gemm(M, N, K, A, lda, transA, B, ldb, transB, C, ldc, c_bf16, bias, relu, beta, stream):
     _check(lib().sbp_nn_gemm(M, N, K, _ptr(A), lda, transA, _ptr(B), ldb, transB, _ptr(C), ldc, c_bf16, _ptr(bias),
                              relu, beta, stream))
+
+
+def sbp_nn_set_gemm_path(path):
+    _check(lib().sbp_nn_set_gemm_path(path))
+
+
+def sbp_nn_status():
+    v = ctypes.c_uint32()
+    _check(lib().sbp_nn_status(ctypes.byref(v)))
+    return v.value
 
 
 def sbp_nn_im2col(X, Xc, C, B, T, kw, pad, stream):

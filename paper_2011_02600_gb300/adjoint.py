@@ -19,25 +19,45 @@ from .solver import _stream
 
 class MisfitProblem:
     """solver: ElasticSolver set up with keep_metrics=True; receivers: (i, j, k) list;
-    data: FP64 tensor [n_rec][3][nsteps]; source: dict for ElasticSolver.set_source or None."""
+    data: FP64 tensor [n_rec][3][nsteps], or [B][n_rec][3][nsteps] for a batched solver of B
+    states; source: dict for ElasticSolver.set_source or None; sources: for a batched solver,
+    one dict (ref, moment) per state, sharing the Ricker frequency f0.  The misfit is the sum
+    over the states; the gradient, that of the sum (the adjoint stages run every state in one
+    launch and add into one gradient)."""
 
-    def __init__(self, solver, receivers, data, dt, nsteps, source=None, checkpoint_every=None):
+    def __init__(self, solver, receivers, data, dt, nsteps, source=None, checkpoint_every=None, sources=None,
+                 f0=2.0):
         if solver.jmet is None:
             raise ValueError("the solver must keep its metrics (setup(..., keep_metrics=True))")
         self.s = solver
         self.receivers = [tuple(int(x) for x in r) for r in receivers]
         self.nsteps = int(nsteps)
         self.dt = float(dt)
-        self.data = torch.as_tensor(data, dtype=torch.float64, device=solver.device).permute(2, 0, 1).contiguous()
+        self.B = solver.batch
+        self.data = self._layout(data)
         self.C = int(checkpoint_every or max(1, math.ceil(math.sqrt(self.nsteps))))
         self.source = source
         s = solver
         self.rlmj = s.new_fields(4, torch.float64)
-        self.acc = torch.zeros(len(self.receivers) * 3, dtype=torch.float64, device=s.device)
+        self.acc = torch.zeros(self.B * len(self.receivers) * 3, dtype=torch.float64, device=s.device)
         s.set_receivers(self.receivers, max(1, self.nsteps))
-        if source is not None:
+        if sources is not None:
+            s.set_sources(sources, f0=f0)
+        elif source is not None:
             s.set_source(**source)
         self.ckpt = {}
+
+    def _layout(self, data):
+        """[nsteps][B * n_rec * 3] (member-major, as the misfit kernel reads it)."""
+        d = torch.as_tensor(data, dtype=torch.float64, device=self.s.device)
+        if d.dim() == 3:
+            d = d.unsqueeze(0)
+        return d.permute(3, 0, 1, 2).reshape(d.shape[3], -1).contiguous()
+
+    def recorded(self):
+        """The traces of the last forward run as data: [B][n_rec][3][nsteps] (FP64)."""
+        n_rec = len(self.receivers)
+        return self.s.traces.view(self.B, -1, 3, max(1, self.nsteps))[:, :n_rec].double()
 
     def set_material(self, rho, lam, mu):
         s = self.s
@@ -83,11 +103,12 @@ class MisfitProblem:
         """d Phi / d(rho, lambda, mu): FP64 tensor [3][ns][nr][nq] (after forward())."""
         s = self.s
         st = _stream()
-        ubar = s.new_fields(9)
-        wbar = s.new_fields(9)
-        scratch = s.new_fields(9)
+        nf = 9 * self.B
+        ubar = s.new_fields(nf)
+        wbar = s.new_fields(nf)
+        scratch = s.new_fields(nf)
         grad = s.new_fields(3, torch.float64)
-        stage_in = [s.new_fields(9) for _ in range(5)]
+        stage_in = [s.new_fields(nf) for _ in range(5)]
         starts = sorted(self.ckpt)
         for seg in reversed(starts):
             end = min(seg + self.C, self.nsteps)
@@ -138,28 +159,38 @@ def workload_materials(solver, cfg, anomaly):
     return tuple(m.expand(*shape).contiguous() for m in fmed(x, y, z))
 
 
-def workload_problem(cfg, precision, source_index=0, nsteps=None, checkpoint_every=None):
+def workload_problem(cfg, precision, source_index=0, nsteps=None, checkpoint_every=None, nodes=None):
     """MisfitProblem for the adjoint workload: data recorded with the true model (background
-    plus a Gaussian vs anomaly) for one of its seeded sources at the 64 surface receivers;
-    material set to the background.  Returns (problem, true_material, background_material)."""
+    plus a Gaussian vs anomaly) at the 64 surface receivers for one of its seeded sources
+    (source_index), or for all of them as one batch (source_index = "all": the workload's
+    eight sources, one state each); material set to the background.  nodes: a smaller grid of
+    the same workload (tests).  Returns (problem, true_material, background_material)."""
+    import dataclasses
     from workloads.acquisition import moment_sources, surface_receivers
     from .workload_setup import build_solver
     from .source_util import moment_tensor_voigt
+    if nodes is not None:
+        cfg = dataclasses.replace(cfg, nodes=tuple(nodes))
     nsteps = nsteps or cfg.steps
-    s, info = build_solver(cfg, precision=precision, keep_metrics=True)
     srcs = moment_sources(cfg.seed, cfg.extra.get("n_sources", 8))
-    sp = srcs[source_index]
-    Mv = moment_tensor_voigt(sp["strike"], sp["dip"], sp["rake"], sp["M0"])
+    chosen = srcs if source_index == "all" else [srcs[source_index]]
+    s, info = build_solver(cfg, precision=precision, keep_metrics=True, batch=len(chosen))
+    sources = [dict(ref=sp["ref"], moment=list(moment_tensor_voigt(sp["strike"], sp["dip"], sp["rake"], sp["M0"])))
+               for sp in chosen]
     rec = surface_receivers(cfg.nodes, 8)
     n_rec = len(rec)
-    p = MisfitProblem(s, rec, torch.zeros(n_rec, 3, nsteps, dtype=torch.float64), info["dt"], nsteps,
-                      source=dict(ref=sp["ref"], moment=list(Mv), stf="ricker", f0=cfg.extra.get("f0", 2.0)),
-                      checkpoint_every=checkpoint_every)
+    f0 = cfg.extra.get("f0", 2.0)
+    zeros = torch.zeros(len(chosen), n_rec, 3, nsteps, dtype=torch.float64)
+    if len(chosen) == 1:
+        p = MisfitProblem(s, rec, zeros[0], info["dt"], nsteps, checkpoint_every=checkpoint_every,
+                          source=dict(**sources[0], stf="ricker", f0=f0))
+    else:
+        p = MisfitProblem(s, rec, zeros, info["dt"], nsteps, checkpoint_every=checkpoint_every, sources=sources,
+                          f0=f0)
     true_m = workload_materials(s, cfg, anomaly=True)
     back_m = workload_materials(s, cfg, anomaly=False)
     p.set_material(*true_m)
     p.forward()
-    data = s.traces.view(-1, 3, max(1, nsteps))[:n_rec].double()
-    p.data = data.permute(2, 0, 1).contiguous()
+    p.data = p._layout(p.recorded())
     p.set_material(*back_m)
     return p, true_m, back_m

@@ -11,7 +11,6 @@ spacing, and the relative L2 error of the surface seismograms against the refere
 nodes and times.  Every step runs in the library's kernels.
 """
 import dataclasses
-import math
 
 import numpy as np
 import torch
@@ -36,16 +35,18 @@ def coarse_receivers(nodes, n_side=4, margin=0.2):
     return [(i, j, ns - 1) for j in ir for i in iq]
 
 
-def hill_run(order, operator, refine=1, precision=32, t_end=None, dt_coarse=None, base="hill129_o6"):
+def hill_run(order, operator, refine=1, precision=32, t_end=None, dt_coarse=None, f0=None, cfl=None,
+             base="hill129_o6"):
     """One run of the Gaussian-hill workload with spacing h / refine.  The time step is
-    dt_coarse / refine (dt_coarse: the workload's own CFL rule on the coarse grid when None) and
-    the run covers t_end (default: the workload's steps at dt_coarse).  Returns (traces
-    [receiver][component][coarse sample], dt_coarse, seconds of GPU time): the velocity at the
-    coarse receivers' nodes after every coarse step."""
+    dt_coarse / refine (dt_coarse: the workload's CFL rule on the coarse grid, at Courant number
+    cfl, when None) and the run covers t_end (default: the workload's steps at dt_coarse); f0:
+    the Ricker frequency (default the workload's).  Returns (traces [receiver][component][coarse
+    sample], dt_coarse, seconds of GPU time): the velocity at the coarse receivers' nodes after
+    every coarse step."""
     cfg = config_by_name(base)
     coarse = cfg.nodes
     nodes = tuple((n - 1) * refine + 1 for n in coarse)
-    rc = dataclasses.replace(cfg, nodes=nodes, order=order)
+    rc = dataclasses.replace(cfg, nodes=nodes, order=order, cfl=cfl or cfg.cfl)
     s, info = build_solver(rc, precision=precision, keep_metrics=True, operator=operator)
     if dt_coarse is None:
         if refine != 1:
@@ -59,7 +60,7 @@ def hill_run(order, operator, refine=1, precision=32, t_end=None, dt_coarse=None
     Lz = cfg.extent[2]
     s_ref = (Lz - cfg.extra["src_depth"] + h) / (Lz + h)          # 3 km below the summit
     s.set_source((0.5, 0.5, s_ref), moment_tensor_voigt(sp["strike"], sp["dip"], sp["rake"], sp["M0"]),
-                 "ricker", f0=cfg.extra["f0"])
+                 "ricker", f0=f0 or cfg.extra["f0"])
     rec = [(i * refine, j * refine, nodes[2] - 1) for (i, j, _) in coarse_receivers(coarse)]
     tr = s.set_receivers(rec, n_coarse * refine)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -79,17 +80,29 @@ def rel_l2(a, b):
     return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
 
 
-def compare(operators=OPERATORS, refine=2, ref_order=6, precision=32, t_end=None):
+# The comparison's run: a 1 Hz Ricker source (the slowest layer, vs = 1 km/s, then has about
+# 2.6 nodes per shortest significant S wavelength, 2.5 f0, on the 156 m grid: marginally
+# resolved, the regime of Section 7.2), 12 s of simulated time, and one time step for every
+# operator (as in Section 7.2), at Courant number 0.25: the upwind order-2 pair, whose D+ has
+# the largest spectral radius, is unstable at the workload's 0.5.
+COMPARE_F0 = 1.0
+COMPARE_T_END = 12.0
+COMPARE_CFL = 0.25
+
+
+def compare(operators=OPERATORS, refine=2, ref_order=6, precision=32, t_end=COMPARE_T_END, f0=COMPARE_F0,
+            cfl=COMPARE_CFL):
     """Relative L2 seismogram error of each operator against the refined reference run.
     Returns dict(errors={(order, family): err}, ref=(order, refine), dt=..., seconds=...)."""
-    first, dt_c, _ = hill_run(ref_order, "upwind", 1, precision, t_end)
-    ref, _, t_ref = hill_run(ref_order, "upwind", refine, precision, t_end, dt_coarse=dt_c)
+    first, dt_c, t_first = hill_run(ref_order, "upwind", 1, precision, t_end, f0=f0, cfl=cfl)
+    ref, _, t_ref = hill_run(ref_order, "upwind", refine, precision, t_end, dt_coarse=dt_c, f0=f0, cfl=cfl)
     errors, secs = {}, {"reference": t_ref}
     for order, fam in operators:
         if (order, fam) == (ref_order, "upwind"):
-            tr, t = first, math.nan
+            tr, t = first, t_first
         else:
-            tr, _, t = hill_run(order, fam, 1, precision, t_end, dt_coarse=dt_c)
+            tr, _, t = hill_run(order, fam, 1, precision, t_end, dt_coarse=dt_c, f0=f0, cfl=cfl)
         errors[(order, fam)] = rel_l2(tr, ref)
         secs[(order, fam)] = t
-    return dict(errors=errors, ref=(ref_order, refine), dt=dt_c, seconds=secs, samples=ref.shape[-1])
+    return dict(errors=errors, ref=(ref_order, refine), dt=dt_c, seconds=secs, samples=ref.shape[-1], f0=f0,
+                cfl=cfl, t_end=t_end)

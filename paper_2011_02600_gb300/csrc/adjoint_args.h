@@ -21,6 +21,8 @@ struct AdjArgs {
   Dims d;
   T rk_a, rk_b, dt;
   int mode;            // 0: out = L^T w; 1: adjoint stage
+  int nb;              // independent states (a batch): every 9-field buffer holds nb members
+  long long bstride;   // elements between consecutive members (9 fields)
   int bc_kind[6];
   T bc_gamma[6];
   T inv_h[3];

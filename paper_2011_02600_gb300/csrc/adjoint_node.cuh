@@ -11,6 +11,30 @@
 
 namespace sbp {
 
+// Gradient accumulation: the members of a batch add to the same node, so the device adds
+// atomically (the host build, one thread, adds directly).
+__device__ __forceinline__ void grad_add(double* p, double v) {
+#ifdef __CUDA_ARCH__
+  atomicAdd(p, v);
+#else
+  *p += v;
+#endif
+}
+
+// The buffers of batch member b (every 9-field buffer advanced by b member strides; the
+// gradient, the coefficients and rho, lambda, mu, J are shared by the members).
+template <typename T>
+__device__ __forceinline__ AdjArgs<T> adjoint_member(AdjArgs<T> A, int b) {
+  const long long o = (long long)b * A.bstride;
+  if (A.ubar_next) A.ubar_next += o;
+  if (A.ubar_out) A.ubar_out += o;
+  if (A.wbar_in) A.wbar_in += o;
+  if (A.wbar) A.wbar += o;
+  if (A.yhat) A.yhat += o;
+  if (A.u) A.u += o;
+  return A;
+}
+
 template <typename T, int O>
 __device__ __forceinline__ void adjoint_prep_at(const AdjArgs<T>& A, long long t) {
   const Dims d = A.d;
@@ -122,9 +146,9 @@ __device__ __forceinline__ void adjoint_stage_at(const AdjArgs<T>& A, long long 
   gradient_terms(rv, e, qc, wk, y, pos, N, a, irhoJ, lamJ, muJ, rho, J, A.bc_kind, A.bc_gamma, A.inv_h0,
                  (double)A.dt, g);
   const double g_rho = g[0], g_lam = g[1], g_mu = g[2];
-  A.grad[n0] += g_rho;
-  A.grad[fs + n0] += g_lam;
-  A.grad[2 * fs + n0] += g_mu;
+  grad_add(A.grad + n0, g_rho);
+  grad_add(A.grad + fs + n0, g_lam);
+  grad_add(A.grad + 2 * fs + n0, g_mu);
 }
 
 }  // namespace sbp

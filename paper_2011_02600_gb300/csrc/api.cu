@@ -195,7 +195,7 @@ sbp::BoxList whole_grid(const SbpGrid* g) {
 template <typename T>
 sbp::StageArgs<T> make_args(const SbpGrid* g, const void* q, void* qout, int mode, double a, double bcoef,
                             double dt, int nb = 1) {
-  sbp::StageArgs<T> A;
+  sbp::StageArgs<T> A{};
   A.nb = nb;
   A.bstride = 9 * g->dims.fs;
   A.q = (const T*)q;
@@ -285,7 +285,8 @@ int encode_maps(const SbpGrid* g, const void* q, int nb, sbp::TmaSet* out) {
   return rc;
 }
 
-// Tensor maps of an unbatched input buffer of the tiled kernel, encoded once per pointer.
+// Tensor maps of an input buffer of the tiled kernel holding the grid's B states, encoded
+// once per pointer.
 int cached_maps(SbpGrid* g, const void* p, const sbp::TmaSet** out) {
   for (auto& c : g->tma_cache)
     if (c.first == p) {
@@ -294,7 +295,7 @@ int cached_maps(SbpGrid* g, const void* p, const sbp::TmaSet** out) {
     }
   if (g->tma_cache.size() >= 16) g->tma_cache.clear();
   g->tma_cache.emplace_back(p, sbp::TmaSet{});
-  if (int rc = encode_maps(g, p, 1, &g->tma_cache.back().second)) {
+  if (int rc = encode_maps(g, p, g->nb, &g->tma_cache.back().second)) {
     g->tma_cache.pop_back();
     return rc;
   }
@@ -369,7 +370,9 @@ namespace {
 template <typename T>
 int adjoint_impl(SbpGrid* g, int mode, int stage, double dt, const void* u, void* ubar, const void* win, void* wbar,
                  void* scratch, const double* rlmj, double* grad, cudaStream_t st) {
-  sbp::AdjArgs<T> A;
+  sbp::AdjArgs<T> A{};
+  A.nb = g->nb;
+  A.bstride = 9 * g->dims.fs;
   A.ubar_next = mode == 1 ? (const T*)ubar : nullptr;
   A.ubar_out = (T*)ubar;
   A.wbar_in = (const T*)win;
@@ -403,7 +406,7 @@ int adjoint_impl(SbpGrid* g, int mode, int stage, double dt, const void* u, void
     cudaError_t e = sbp::launch_adjoint_prep<T>(A, g->desc.order, st);
     if (e != cudaSuccess) return cuda_fail(e, "adjoint prep");
     sbp::StageArgs<T> S2 = make_args<T>(g, nullptr, nullptr, mode == 1 ? sbp::kModeStage : sbp::kModeRhs,
-                                        mode == 1 ? kRkA[stage] : 0.0, 0.0, dt, 1);
+                                        mode == 1 ? kRkA[stage] : 0.0, 0.0, dt, g->nb);
     S2.ubar_next = A.ubar_next;
     S2.ubar_out = A.ubar_out;
     S2.wbar = A.wbar;
@@ -467,7 +470,10 @@ int sbp_min_nodes(int32_t order, int32_t* out) {
     return fail(SBP_ERR_ARG, "order must be 2..7 (upwind, Table 1) or %d, %d, %d (traditional, Table 2)",
                 SBP_TRADITIONAL + 2, SBP_TRADITIONAL + 4, SBP_TRADITIONAL + 6);
   if (!out) return fail(SBP_ERR_ARG, "null output");
-  *out = 2 * I.b + I.reach;
+  // the metric terms apply the upwind pair of the operator's order: its size bound holds too
+  const OpInfo Im = op_info(I.metric_order);
+  const int own = 2 * I.b + I.reach, met = 2 * Im.b + Im.reach;
+  *out = own > met ? own : met;
   return SBP_OK;
 }
 
@@ -914,7 +920,6 @@ int sbp_rhs_adjoint(SbpGrid* g, const void* w, void* out, void* scratch, void* s
 int sbp_adjoint_stage(SbpGrid* g, int32_t stage, double dt, const void* u_stage, void* ubar, void* wbar,
                       void* scratch, const double* rlmj, double* grad, void* stream) {
   if (int rc = check_ready(g)) return rc;
-  if (g->nb != 1) return fail(SBP_ERR_UNSUPPORTED, "the adjoint runs on unbatched grids");
   if (!op_info(g->desc.order).adjoint) return fail(SBP_ERR_UNSUPPORTED, "the adjoint is built for orders 2, 4, 6");
   if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
   if (stage < 0 || stage > 4) return fail(SBP_ERR_ARG, "stage must be 0..4");
@@ -931,10 +936,12 @@ int sbp_misfit(SbpGrid* g, const void* q, const double* data, double weight, dou
   if (int rc = check_ready(g)) return rc;
   if (g->rec_n == 0) return fail(SBP_ERR_STATE, "no receivers set (sbp_set_receivers)");
   if (!q || !data) return fail(SBP_ERR_ARG, "null state or data");
-  cudaError_t e = g->elem == 4 ? sbp::launch_misfit<float>((const float*)q, g->dims, g->rec_off, g->rec_n, data,
-                                                            weight, acc, (float*)ubar, (cudaStream_t)stream)
-                               : sbp::launch_misfit<double>((const double*)q, g->dims, g->rec_off, g->rec_n, data,
-                                                             weight, acc, (double*)ubar, (cudaStream_t)stream);
+  const long long bs = 9 * g->dims.fs;
+  cudaError_t e = g->elem == 4 ? sbp::launch_misfit<float>((const float*)q, g->dims, g->rec_off, g->rec_n, g->nb, bs,
+                                                            data, weight, acc, (float*)ubar, (cudaStream_t)stream)
+                               : sbp::launch_misfit<double>((const double*)q, g->dims, g->rec_off, g->rec_n, g->nb,
+                                                             bs, data, weight, acc, (double*)ubar,
+                                                             (cudaStream_t)stream);
   return e == cudaSuccess ? SBP_OK : cuda_fail(e, "misfit");
 }
 

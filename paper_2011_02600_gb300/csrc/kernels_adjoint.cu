@@ -23,11 +23,12 @@
 
 namespace sbp {
 
+// blockIdx.y: member of a batch of independent states.
 template <typename T, int O>
 __global__ void adjoint_prep_kernel(AdjArgs<T> A) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)A.d.nq * A.d.nr * A.d.ns) return;
-  adjoint_prep_at<T, O>(A, t);
+  adjoint_prep_at<T, O>(adjoint_member(A, blockIdx.y), t);
 }
 
 // One thread per node: L^T, the stage updates and the gradient (adjoint_node.cuh).
@@ -35,13 +36,13 @@ template <typename T, int O>
 __global__ void __launch_bounds__(256) adjoint_stage_kernel(AdjArgs<T> A) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)A.d.nq * A.d.nr * A.d.ns) return;
-  adjoint_stage_at<T, O>(A, t);
+  adjoint_stage_at<T, O>(adjoint_member(A, blockIdx.y), t);
 }
 
 template <typename T>
 cudaError_t launch_adjoint_prep(const AdjArgs<T>& A, int order, cudaStream_t st) {
   const long long total = (long long)A.d.nq * A.d.nr * A.d.ns;
-  const unsigned blocks = (unsigned)((total + 255) / 256);
+  const dim3 blocks((unsigned)((total + 255) / 256), (unsigned)A.nb);
   switch (order) {
     case 2: adjoint_prep_kernel<T, 2><<<blocks, 256, 0, st>>>(A); break;
     case 4: adjoint_prep_kernel<T, 4><<<blocks, 256, 0, st>>>(A); break;
@@ -56,7 +57,7 @@ cudaError_t launch_adjoint(const AdjArgs<T>& A, int order, cudaStream_t st) {
   cudaError_t e = launch_adjoint_prep<T>(A, order, st);
   if (e != cudaSuccess) return e;
   const long long total = (long long)A.d.nq * A.d.nr * A.d.ns;
-  const unsigned blocks = (unsigned)((total + 255) / 256);
+  const dim3 blocks((unsigned)((total + 255) / 256), (unsigned)A.nb);
   switch (order) {
     case 2: adjoint_stage_kernel<T, 2><<<blocks, 256, 0, st>>>(A); break;
     case 4: adjoint_stage_kernel<T, 4><<<blocks, 256, 0, st>>>(A); break;
@@ -68,24 +69,26 @@ cudaError_t launch_adjoint(const AdjArgs<T>& A, int order, cudaStream_t st) {
 
 // Receivers: misfit 1/2 w (v - d)^2 accumulated per receiver component in FP64, and the
 // adjoint source w (v - d) added to ubar (if given) at the receiver node.  The add is atomic:
-// receivers that share a node each contribute their own source.
+// receivers that share a node each contribute their own source.  Thread t covers member
+// t / (3 n) of a batch (its state, data, accumulators and ubar at member stride bstride).
 template <typename T>
-__global__ void misfit_kernel(const T* __restrict__ q, Dims d, const int32_t* __restrict__ off, int n,
-                              const double* __restrict__ data, double w, double* __restrict__ acc, T* ubar) {
+__global__ void misfit_kernel(const T* __restrict__ q, Dims d, const int32_t* __restrict__ off, int n, int nb,
+                              long long bstride, const double* __restrict__ data, double w,
+                              double* __restrict__ acc, T* ubar) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * 3) return;
-  const int r = t / 3, c = t % 3;
-  const long long idx = (long long)c * d.fs + off[r];
+  if (t >= n * 3 * nb) return;
+  const int b = t / (3 * n), r = (t / 3) % n, c = t % 3;
+  const long long idx = (long long)b * bstride + (long long)c * d.fs + off[r];
   const double diff = (double)q[idx] - data[t];
   if (acc) acc[t] += 0.5 * w * diff * diff;
   if (ubar) atomicAdd(&ubar[idx], (T)(w * diff));
 }
 
 template <typename T>
-cudaError_t launch_misfit(const T* q, const Dims& d, const int32_t* off, int n, const double* data, double w,
-                          double* acc, T* ubar, cudaStream_t st) {
+cudaError_t launch_misfit(const T* q, const Dims& d, const int32_t* off, int n, int nb, long long bstride,
+                          const double* data, double w, double* acc, T* ubar, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
-  misfit_kernel<T><<<(n * 3 + 127) / 128, 128, 0, st>>>(q, d, off, n, data, w, acc, ubar);
+  misfit_kernel<T><<<(n * 3 * nb + 127) / 128, 128, 0, st>>>(q, d, off, n, nb, bstride, data, w, acc, ubar);
   return cudaGetLastError();
 }
 
@@ -93,9 +96,9 @@ template cudaError_t launch_adjoint<float>(const AdjArgs<float>&, int, cudaStrea
 template cudaError_t launch_adjoint<double>(const AdjArgs<double>&, int, cudaStream_t);
 template cudaError_t launch_adjoint_prep<float>(const AdjArgs<float>&, int, cudaStream_t);
 template cudaError_t launch_adjoint_prep<double>(const AdjArgs<double>&, int, cudaStream_t);
-template cudaError_t launch_misfit<float>(const float*, const Dims&, const int32_t*, int, const double*, double,
-                                          double*, float*, cudaStream_t);
-template cudaError_t launch_misfit<double>(const double*, const Dims&, const int32_t*, int, const double*, double,
-                                           double*, double*, cudaStream_t);
+template cudaError_t launch_misfit<float>(const float*, const Dims&, const int32_t*, int, int, long long,
+                                          const double*, double, double*, float*, cudaStream_t);
+template cudaError_t launch_misfit<double>(const double*, const Dims&, const int32_t*, int, int, long long,
+                                           const double*, double, double*, double*, cudaStream_t);
 
 }  // namespace sbp

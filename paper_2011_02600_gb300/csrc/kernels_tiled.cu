@@ -121,6 +121,11 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
   T* __restrict__ dqm = A.dq + (A.mode == kModeRhs ? 0 : boff);
   T* __restrict__ scl = A.sclose + (long long)member * A.sc_bstride;
   const T* __restrict__ met = A.met;
+  // this member's adjoint buffers (the adjoint passes; the gradient is shared by the members)
+  const T* ub_next = A.ubar_next ? A.ubar_next + boff : nullptr;
+  T* ub_out = A.ubar_out ? A.ubar_out + boff : nullptr;
+  T* wbm = A.wbar ? A.wbar + boff : nullptr;
+  const T* yhm = A.yhat ? A.yhat + boff : nullptr;
   const int col = j * d.ldq + i;
 
   if (tid == 0) {
@@ -190,23 +195,22 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
     if (KIND == 1 && A.mode != kModeRhs) {
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        dqi[c] = A.ubar_next ? ld(A.ubar_next, c * fs + off) : T(0);
-        pre[c] = ld(A.wbar, c * fs + off);
+        dqi[c] = ub_next ? ld(ub_next, c * fs + off) : T(0);
+        pre[c] = ld(wbm, c * fs + off);
       }
     }
     if (KIND == 2) {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) pre[c] = ld(A.wbar, c * fs + off);
+      for (int c = 0; c < 9; ++c) pre[c] = ld(wbm, c * fs + off);
       rj[0] = active ? __ldg(A.rlmj + off) : 0.0;
       rj[1] = active ? __ldg(A.rlmj + 3 * fs + off) : 0.0;
     }
 
-    if (!mbar_wait_bounded(&S.bar[sidx], phase, kWaitLimit)) {
-      // The copy never completed (the only one in flight is the one waited for): record
-      // it and leave; the host sees SBP_STATUS_TIMEOUT.
-      if (tid == 0) atomicOr(A.status, 8u);
-      return;
-    }
+    // Each thread waits for the plane's copy with a bounded wait; the block decides together
+    // at the plane's barrier below (__syncthreads_or), so that either every thread goes on or
+    // every thread leaves.  Until then a thread whose wait gave up only reads shared memory at
+    // fixed in-bounds indices.
+    const bool landed = mbar_wait_bounded(&S.bar[sidx], phase, kWaitLimit);
     const Stage<T>& st = S.st[sidx];
     FluxTiles<T>& F = S.f[sidx];
     // fluxes on the tile and its halo: F_q at columns -QF..TX-1+R, F_r at rows -QF..TY-1+R
@@ -235,7 +239,13 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
 #pragma unroll
       for (int c = 0; c < 3; ++c) F.fr[c][rr][cl] = Fv[c];
     }
-    __syncthreads();
+    if (__syncthreads_or(!landed)) {
+      // The plane's copy did not complete in time for some thread (it is the only copy in
+      // flight: the next plane's is issued below).  Record it and leave together; the host sees
+      // SBP_STATUS_TIMEOUT.  The outstanding copy is abandoned.
+      if (tid == 0) atomicOr(A.status, 8u);
+      return;
+    }
     if (tid == 0 && k + 1 < ke) {
       fence_proxy_async_smem();
       issue_plane(S, sidx ^ 1, tm, i0, j0, k + 1, member);
@@ -408,12 +418,12 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
         const T m9[9] = {vb[0], vb[1], vb[2], sb[0], sb[1], sb[2], sb[3], sb[4], sb[5]};
         if (A.mode == kModeRhs) {
 #pragma unroll
-          for (int f = 0; f < 9; ++f) A.ubar_out[f * fs + off] = m9[f];
+          for (int f = 0; f < 9; ++f) ub_out[f * fs + off] = m9[f];
         } else {
 #pragma unroll
           for (int f = 0; f < 9; ++f) {
-            A.ubar_out[f * fs + off] = dqi[f] + A.dt * m9[f];
-            A.wbar[f * fs + off] = A.rk_a * pre[f];
+            ub_out[f * fs + off] = dqi[f] + A.dt * m9[f];
+            wbm[f * fs + off] = A.rk_a * pre[f];
           }
         }
       } else {
@@ -423,7 +433,7 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
           const T H = norm_weight_t<T, O>(i, d.nq) * A.h[0] * norm_weight_t<T, O>(j, d.nr) * A.h[1] *
                       norm_weight_t<T, O>(k, d.ns) * A.h[2];
 #pragma unroll
-          for (int f = 0; f < 9; ++f) y[f] = H * A.yhat[f * fs + off];
+          for (int f = 0; f < 9; ++f) y[f] = H * yhm[f * fs + off];
         }
         double g[3];
         gradient_terms(rv, e, qc, pre, y, pos, N, a, irhoJ, lamJ, muJ, rj[0], rj[1], A.bc_kind, A.bc_gamma,
@@ -532,7 +542,6 @@ cudaError_t launch_stage_tiled(const StageArgs<T>& A, int order, const TmaSet& t
 
 template <typename T>
 cudaError_t launch_adjoint_tiled(const StageArgs<T>& A, int order, int pass, const TmaSet& tm, cudaStream_t st) {
-  if (A.nb != 1) return cudaErrorInvalidValue;
   if (pass == 1) {
     if (!A.ubar_out || (A.mode != kModeRhs && !A.wbar)) return cudaErrorInvalidValue;
     return launch_kind<T, 1>(A, order, tm, st);

@@ -18,8 +18,8 @@ template <typename T>
 cudaError_t launch_adjoint_prep(const AdjArgs<T>& A, int order, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_misfit(const T* q, const Dims& d, const int32_t* off, int n, const double* data, double w,
-                          double* acc, T* ubar, cudaStream_t st);
+cudaError_t launch_misfit(const T* q, const Dims& d, const int32_t* off, int n, int nb, long long bstride,
+                          const double* data, double w, double* acc, T* ubar, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_stage_general(const StageArgs<T>& A, int order, const BoxList& L, cudaStream_t st);
@@ -31,7 +31,8 @@ cudaError_t launch_stage_tiled(const StageArgs<T>& A, int order, const TmaSet& t
 
 // The tiled kernel's adjoint passes (after launch_adjoint_prep): pass 2, the material
 // gradient on q = U_k (tensor maps of U_k), then pass 1, L^T on q = yhat (maps of yhat),
-// which replaces Wb_k by A_k Wb_k.  Unbatched grids only.
+// which replaces Wb_k by A_k Wb_k.  A.nb members (tensor maps over all of them); the members
+// add their gradients into the one shared gradient.
 template <typename T>
 cudaError_t launch_adjoint_tiled(const StageArgs<T>& A, int order, int pass, const TmaSet& tm, cudaStream_t st);
 

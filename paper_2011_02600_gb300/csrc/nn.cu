@@ -1,6 +1,8 @@
-// Kernels of the learned surrogate: a BF16 tensor-core GEMM with FP32
+// Kernels of the learned surrogate: BF16 tensor-core GEMMs with FP32
 // accumulation and the small layer kernels around it (1D convolution as
 // im2col + GEMM, nearest upsampling, ReLU, bias gradients, MSE loss, Adam).
+// sbp_nn_gemm runs the tcgen05 kernel of nn_tc.cu where the operands allow it;
+// the mma.sync kernels below serve small and unaligned products.
 //
 // Matrices are row-major.  The GEMM computes
 //     C[M x N] = beta * C + op(A)[M x K] op(B)[K x N] (+ bias[m]) (ReLU)
@@ -461,6 +463,15 @@ namespace sbp {
 void set_last_error(const char* msg);
 }
 
+namespace sbp_nn {
+// nn_tc.cu: the tcgen05 GEMM (cudaErrorNotSupported when the operands do not suit TMA) and
+// its status word.
+cudaError_t launch_gemm_tc(int M, int N, int K, const void* A, long long lda, int ta, const void* B, long long ldb,
+                           int tb, void* C, long long ldc, int c_bf16, const float* bias, int relu, float beta,
+                           int sms, cudaStream_t st);
+cudaError_t gemm_tc_status(unsigned* bits);
+}  // namespace sbp_nn
+
 namespace {
 int nn_status(cudaError_t e) {
   if (e == cudaSuccess) return SBP_OK;
@@ -471,6 +482,9 @@ int nn_bad(const char* msg) {
   sbp::set_last_error(msg);
   return SBP_ERR_ARG;
 }
+// GEMM path (sbp_nn_set_gemm_path): 0 automatic, 1 mma.sync kernels only, 2 tcgen05 whenever possible.
+int g_gemm_path = 0;
+
 // SM count of the current device (152 on GB300, also the value taken if the query fails).
 int device_sms() {
   int dev = 0, n = 0;
@@ -494,6 +508,14 @@ int sbp_nn_gemm(int32_t M, int32_t N, int32_t K, const void* A, int64_t lda, int
   if (c_bf16 && beta != 0.f) return nn_bad("accumulation (beta) needs an FP32 output");
   const cudaStream_t st = (cudaStream_t)stream;
   const bool aligned = lda % 8 == 0 && ldb % 8 == 0 && (uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0;
+  // the tensor-core (tcgen05) kernel: TMA-loadable operands; automatically for tiles of at least
+  // 128 x 128 (smaller products leave most of its 128 x 256 tile empty)
+  const bool use_tc = aligned && g_gemm_path != 1 && (g_gemm_path == 2 || (M >= 128 && N >= 128 && K >= 64));
+  if (use_tc) {
+    cudaError_t e = launch_gemm_tc(M, N, K, A, lda, transA, B, ldb, transB, C, ldc, c_bf16, bias, relu, beta,
+                                   device_sms(), st);
+    if (e != cudaErrorNotSupported) return nn_status(e);
+  }
   if (!aligned) {
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
     if (grid.y > 65535) return nn_bad("M too large");
@@ -529,6 +551,21 @@ int sbp_nn_gemm(int32_t M, int32_t N, int32_t K, const void* A, int64_t lda, int
                                                   (const __nv_bfloat16*)B, ldb, transB, C, ldc, c_bf16, bias, relu,
                                                   beta);
   return nn_status(cudaGetLastError());
+}
+
+int sbp_nn_set_gemm_path(int32_t path) {
+  if (path < 0 || path > 2) return nn_bad("GEMM path must be 0 (automatic), 1 (mma.sync) or 2 (tcgen05)");
+  g_gemm_path = path;
+  return SBP_OK;
+}
+
+int sbp_nn_status(uint32_t* bits) {
+  if (!bits) return nn_bad("null output");
+  unsigned v = 0;
+  cudaError_t e = gemm_tc_status(&v);
+  if (e != cudaSuccess) return nn_status(e);
+  *bits = v;
+  return SBP_OK;
 }
 
 int sbp_nn_im2col(const void* X, void* Xc, int32_t C, int32_t B, int32_t T, int32_t kw, int32_t pad, void* stream) {

@@ -36,8 +36,8 @@ def test_min_nodes(lib):
     assert L.sbp_min_nodes(2) == 6 and L.sbp_min_nodes(4) == 11 and L.sbp_min_nodes(6) == 16
     for order in range(2, 8):
         assert L.sbp_min_nodes(order) == min_nodes(order)
-    for order in (2, 4, 6):
-        assert L.sbp_min_nodes(L.SBP_TRADITIONAL + order) == traditional_min_nodes(order)
+    for order in (2, 4, 6):   # also the bound of the upwind pair that forms the metric terms
+        assert L.sbp_min_nodes(L.SBP_TRADITIONAL + order) == max(traditional_min_nodes(order), min_nodes(order))
     for bad in (1, 8, 9, 100, 103, 105, 107):
         with pytest.raises(L.SbpError) as e:
             L.sbp_min_nodes(bad)
@@ -56,7 +56,7 @@ def test_create_grid_validation(lib):
     _expect(1, L.sbp_create_grid, (20, 20, 20), 8, 32, free)        # order 8: no closure
     _expect(1, L.sbp_create_grid, (20, 20, 20), 103, 32, free)      # no odd traditional operator
     _expect(1, L.sbp_create_grid, (15, 15, 15), 7, 32, free)        # order 7 needs 16 nodes
-    _expect(1, L.sbp_create_grid, (14, 15, 15), 106, 32, free)      # traditional 6 needs 15
+    _expect(1, L.sbp_create_grid, (15, 16, 16), 106, 32, free)      # traditional 6 needs 16 (metric terms)
     # the odd upwind orders and the traditional operators (codes 100 + 2, 4, 6) are accepted
     for order in (3, 5, 7, 102, 104, 106):
         L.sbp_destroy(L.sbp_create_grid((20, 20, 20), order, 32, free))

@@ -218,3 +218,67 @@ def test_tiled_adjoint_matches_general_path(order, nodes, prec):
     for f in range(3):
         sc = np.abs(grads[1][f]).max()
         assert np.abs(grads[0][f] - grads[1][f]).max() < (1e-11 if prec == 64 else 1e-4) * sc, f
+
+
+def _batched_problem(c, sources, prec=64, path=0):
+    from paper_2011_02600_gb300 import ElasticSolver
+    from paper_2011_02600_gb300.adjoint import MisfitProblem
+    s = ElasticSolver(c["nodes"], c["order"], prec, c["bc"], batch=len(sources))
+    s.setup(torch.from_numpy(np.stack(c["X"])), torch.from_numpy(np.stack(c["mat"])), keep_metrics=True)
+    s.set_kernel_path(path)
+    rng = np.random.default_rng(21)
+    data = rng.normal(scale=1e-4, size=(len(sources), len(c["rec"]), 3, c["nsteps"]))
+    return MisfitProblem(s, c["rec"], torch.from_numpy(data), c["dt"], c["nsteps"], sources=sources, f0=c["f0"]), data
+
+
+def _three_sources():
+    return [dict(ref=(0.5, 0.45, 0.55), moment=list(moment_tensor(0.4, 1.0, 0.3, 1.0e12))),
+            dict(ref=(0.35, 0.6, 0.7), moment=list(moment_tensor(1.3, 0.6, -0.9, 2.0e12))),
+            dict(ref=(0.62, 0.4, 0.45), moment=list(moment_tensor(2.2, 1.2, 1.4, 0.5e12)))]
+
+
+@pytest.mark.parametrize("path", [0, 1])
+def test_batched_adjoint_is_the_sum_of_single_source_gradients(path):
+    """Three sources as one batch (one launch per adjoint kernel, every member adding into one
+    gradient): the misfit and the gradient equal the sums of the three single-source problems
+    (FP64, tiled and general kernels)."""
+    from paper_2011_02600_gb300.adjoint import MisfitProblem
+    c = _misfit_case(nsteps=20)
+    srcs = _three_sources()
+    pb, data = _batched_problem(c, srcs, path=path)
+    _set(pb, c["mat"])
+    phi_b = pb.forward()
+    g_b = pb.gradient().cpu().numpy()
+    phi_s, g_s = 0.0, 0.0
+    for m, sc in enumerate(srcs):
+        s = _solver(c["nodes"], c["order"], 64, c["bc"], c["X"], c["mat"], keep=True)
+        s.set_kernel_path(path)
+        p = MisfitProblem(s, c["rec"], torch.from_numpy(data[m]), c["dt"], c["nsteps"],
+                          source=dict(ref=sc["ref"], moment=sc["moment"], stf="ricker", f0=c["f0"]))
+        _set(p, c["mat"])
+        phi_s += p.forward()
+        g_s = g_s + p.gradient().cpu().numpy()
+    assert abs(phi_b - phi_s) < 1e-13 * abs(phi_s)
+    for f in range(3):
+        assert np.abs(g_b[f] - g_s[f]).max() < 1e-12 * np.abs(g_s[f]).max(), f
+
+
+def test_batched_gradient_against_finite_differences():
+    """The batched problem's gradient against central differences of its summed misfit in
+    20 seeded directions (FP64, 1e-5)."""
+    c = _misfit_case(nsteps=20)
+    pb, _ = _batched_problem(c, _three_sources())
+    _set(pb, c["mat"])
+    pb.forward()
+    g = pb.gradient().cpu().numpy()
+    h = 1e-6
+    worst = 0.0
+    for dm in _directions(c, 20, seed=9):
+        _set(pb, tuple(m + h * d for m, d in zip(c["mat"], dm)))
+        fp = pb.forward()
+        _set(pb, tuple(m - h * d for m, d in zip(c["mat"], dm)))
+        fm = pb.forward()
+        fd = (fp - fm) / (2 * h)
+        got = float(sum(np.sum(g[f] * dm[f]) for f in range(3)))
+        worst = max(worst, abs(got - fd) / abs(fd))
+    assert worst < 1e-5, worst

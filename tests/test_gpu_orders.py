@@ -36,7 +36,9 @@ def built():
 
 
 def _nmin(order, operator):
-    return min_nodes(order) if operator == "upwind" else traditional_min_nodes(order)
+    """Fewest nodes per axis: the operator's own bound and, for a traditional operator, that of
+    the upwind pair of the same order, which forms the metric terms."""
+    return min_nodes(order) if operator == "upwind" else max(traditional_min_nodes(order), min_nodes(order))
 
 
 def _problem(nodes, order, operator, ext=(1000.0, 1100.0, 900.0)):

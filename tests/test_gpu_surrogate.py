@@ -65,6 +65,43 @@ def test_gemm_tensor_cores_vs_numpy(M, N, K, ta, tb):
     assert np.abs(Cb.float().cpu().numpy() - want).max() < 1e-2 * np.abs(want).max()
 
 
+@pytest.mark.parametrize("path", [1, 2])
+@pytest.mark.parametrize("M,N,K", [(128, 256, 64), (256, 512, 128), (200, 300, 100), (136, 200, 96), (40, 64, 1000),
+                                   (1152, 2048, 640), (384, 640, 4096)])
+@pytest.mark.parametrize("ta,tb", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_gemm_kernel_paths_vs_numpy(path, M, N, K, ta, tb):
+    """Each GEMM kernel forced in turn: 1 the mma.sync kernels, 2 the tcgen05 kernel (TMA
+    operand tiles in both orientations, FP32 accumulator in tensor memory, ragged M, N, K
+    edges, split K for FP32 outputs that leave SMs idle).  Same tolerances as above; the
+    tcgen05 kernel's status word stays clear."""
+    from paper_2011_02600_gb300 import _lib as L
+    from paper_2011_02600_gb300.solver import _stream
+    rng = np.random.default_rng(M + 3 * N + 7 * K + 11 * ta + 13 * tb)
+    A = _bf(rng.normal(size=(K, M) if ta else (M, K)))
+    B = _bf(rng.normal(size=(N, K) if tb else (K, N)))
+    bias = torch.as_tensor(rng.normal(size=M), dtype=torch.float32)
+    An = A.float().numpy().astype(np.float64)
+    Bn = B.float().numpy().astype(np.float64)
+    ref = (An.T if ta else An) @ (Bn.T if tb else Bn) + bias.numpy()[:, None]
+    Ad, Bd, bd = A.cuda(), B.cuda(), bias.cuda()
+    tol = 1e-5 * max(1.0, (K / 1024) ** 0.5)
+    L.sbp_nn_set_gemm_path(path)
+    try:
+        C = torch.empty(M, N, device="cuda")
+        L.sbp_nn_gemm(M, N, K, Ad, A.shape[1], ta, Bd, B.shape[1], tb, C, N, 0, bd, 0, 0.0, _stream())
+        assert np.abs(C.cpu().numpy() - ref).max() < tol * np.abs(ref).max()
+        L.sbp_nn_gemm(M, N, K, Ad, A.shape[1], ta, Bd, B.shape[1], tb, C, N, 0, bd, 1, 1.0, _stream())
+        want = np.maximum(2 * ref, 0)
+        assert np.abs(C.cpu().numpy() - want).max() < tol * np.abs(want).max()
+        Cb = torch.empty(M, N, device="cuda", dtype=torch.bfloat16)
+        L.sbp_nn_gemm(M, N, K, Ad, A.shape[1], ta, Bd, B.shape[1], tb, Cb, N, 1, bd, 1, 0.0, _stream())
+        want = np.maximum(ref, 0)
+        assert np.abs(Cb.float().cpu().numpy() - want).max() < 1e-2 * np.abs(want).max()
+        assert L.sbp_nn_status() == 0
+    finally:
+        L.sbp_nn_set_gemm_path(0)
+
+
 @pytest.mark.parametrize("n_mom", [0, 6])
 def test_network_forward_and_gradients_vs_oracle(n_mom):
     from oracle import surrogate_net as sn
