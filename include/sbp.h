@@ -119,6 +119,26 @@ int sbp_layout(const SbpGrid* grid, int64_t* ldq, int64_t* fs, int64_t* elem_byt
  * Call before sbp_bind; default 1.  B in 1..1024. */
 int sbp_set_batch(SbpGrid* grid, int32_t nb);
 
+/* Make the grid one slab of a block decomposed along s (the multi-device layout:
+ * each device owns a range of s-planes; prior art is the paper's MPI ghost-node
+ * exchange, Section 7.2).  The grid's ns (SbpGridDesc, at least sbp_min_nodes
+ * like every axis) counts its local planes:
+ * ghost_lo ghost planes, the owned planes, ghost_hi ghost planes; local plane k
+ * is plane k + k_offset of the block of ns_global planes.  A ghost count of 0
+ * marks a face of the block (k_offset = 0 at the low face, k_offset + ns =
+ * ns_global at the high face); otherwise it must be at least the interior
+ * stencil's reach max(r, q).  The stages compute the owned planes only, with the
+ * block's spacing and with closures and penalties at the block's faces alone, so
+ * that, with the ghost planes of the state filled from the neighbours before
+ * every stage (the caller's halo exchange), the owned planes evolve exactly as in
+ * the undivided block.  sbp_energy sums the owned planes with the block's
+ * weights.  jmet given to sbp_set_material must be the block's metrics at the
+ * local planes (sbp_metrics refuses slab grids: its closures would be the local
+ * array's).  Point sources, the adjoint and the general kernel path return
+ * UNSUPPORTED on slab grids.  Call before sbp_bind; ghost_lo = ghost_hi = 0
+ * restores the whole block. */
+int sbp_set_slab(SbpGrid* grid, int32_t ns_global, int32_t k_offset, int32_t ghost_lo, int32_t ghost_hi);
+
 /* Bind the caller's device buffers (solver precision, layout of sbp_layout):
  * q0, q1: 9 B fields each (ping-pong state; state b occupies fields 9b..9b+8;
  * q0 holds the states after binding), dq: 9 B fields (Runge-Kutta register),

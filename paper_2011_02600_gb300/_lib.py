@@ -25,7 +25,7 @@ EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sb
             "sbp_nn_upsample2", "sbp_nn_relu_backward", "sbp_nn_bias_grad", "sbp_nn_mse", "sbp_nn_adam",
             "sbp_nn_mlp_to_conv", "sbp_nn_cast_bf16", "sbp_nn_moment_combine", "sbp_selftest_wait_timeout", "sbp_last_error",
             "sbp_set_receivers_xyz", "sbp_record_receivers", "sbp_set_state", "sbp_get_state",
-            "sbp_nn_set_gemm_path", "sbp_nn_status")
+            "sbp_nn_set_gemm_path", "sbp_nn_status", "sbp_set_slab")
 
 
 class SbpError(RuntimeError):
@@ -106,6 +106,7 @@ def lib(path=None):
         "sbp_get_state": [P, P, i32, P],
         "sbp_nn_set_gemm_path": [i32],
         "sbp_nn_status": [ctypes.POINTER(ctypes.c_uint32)],
+        "sbp_set_slab": [P, i32, i32, i32, i32],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -298,6 +299,10 @@ def sbp_adjoint_stage(h, stage, dt, u_stage, ubar, wbar, scratch, rlmj, grad, st
 
 def sbp_misfit(h, q, data, weight, acc, ubar, stream):
     _check(lib().sbp_misfit(h, _ptr(q), _ptr(data), weight, _ptr(acc), _ptr(ubar), stream))
+
+
+def sbp_set_slab(h, ns_global, k_offset, ghost_lo, ghost_hi):
+    _check(lib().sbp_set_slab(h, ns_global, k_offset, ghost_lo, ghost_hi))
 
 
 def sbp_set_batch(h, nb):

@@ -159,6 +159,7 @@ struct SbpGrid {
   bool traces_owned = false;  // traces allocated by the library (sbp_set_receivers with traces = NULL)
   int n_t = 0;
   bool use_tiled = true;
+  sbp::SlabS slab;         // s-slab of a decomposed block (sbp_set_slab); default: the whole block
   void* sclose = nullptr;  // tiled kernel scratch (s-closure sums), owned by the library
   // tensor maps of the tiled stage kernel, per state buffer (q0, q1)
   bool tma_ok[2] = {false, false};
@@ -211,7 +212,9 @@ sbp::StageArgs<T> make_args(const SbpGrid* g, const void* q, void* qout, int mod
   A.status = g->status;
   A.sclose = (T*)g->sclose;
   A.sc_bstride = sclose_elems(g);
-  const int N[3] = {g->desc.nq, g->desc.nr, g->desc.ns};
+  A.slab = g->slab;
+  // spacing along s: that of the whole block when the grid is one of its slabs
+  const int N[3] = {g->desc.nq, g->desc.nr, g->slab.ns_global > 0 ? g->slab.ns_global : g->desc.ns};
   for (int f = 0; f < 6; ++f) {
     A.bc_kind[f] = g->desc.bc_kind[f];
     A.bc_gamma[f] = (T)g->desc.bc_gamma[f];
@@ -306,6 +309,8 @@ int cached_maps(SbpGrid* g, const void* p, const sbp::TmaSet** out) {
 template <typename T>
 int run_stage_kernels(SbpGrid* g, const void* q, void* qout, int mode, double a, double bcoef, double dt,
                       cudaStream_t st, int nb = 1) {
+  if (g->slab.ns_global > 0 && !g->use_tiled)
+    return fail(SBP_ERR_UNSUPPORTED, "a slab grid runs the tiled kernel only (sbp_set_kernel_path(0))");
   sbp::StageArgs<T> A = make_args<T>(g, q, qout, mode, a, bcoef, dt, nb);
   if (g->use_tiled) {
     sbp::TmaSet local;
@@ -582,6 +587,8 @@ int sbp_bind(SbpGrid* g, void* q0, void* q1, void* dq, void* met, void* mat) {
 
 int sbp_metrics(SbpGrid* g, const double* xyz, double* jmet, void* stream) {
   if (int rc = check_ready(g)) return rc;
+  if (g->slab.ns_global > 0)
+    return fail(SBP_ERR_UNSUPPORTED, "a slab grid takes the block's metrics restricted to its planes (see sbp_set_slab)");
   if (!xyz || !jmet) return fail(SBP_ERR_ARG, "null coordinate or metric buffer");
   cudaError_t e =
       sbp::launch_metrics(xyz, jmet, g->dims, op_info(g->desc.order).metric_order, g->status, (cudaStream_t)stream);
@@ -708,10 +715,10 @@ int sbp_energy(SbpGrid* g, double* out, void* stream) {
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = g->elem == 4 ? sbp::launch_energy<float>((const float*)g->q[g->cur], (const float*)g->mat,
                                                            g->dims, g->desc.order, g->partial, sbp::energy_blocks(),
-                                                           g->eout, g->status, st)
+                                                           g->eout, g->status, st, g->slab)
                                : sbp::launch_energy<double>((const double*)g->q[g->cur], (const double*)g->mat,
                                                             g->dims, g->desc.order, g->partial,
-                                                            sbp::energy_blocks(), g->eout, g->status, st);
+                                                            sbp::energy_blocks(), g->eout, g->status, st, g->slab);
   if (e != cudaSuccess) return cuda_fail(e, "energy");
   double v = 0.0;
   e = cudaMemcpyAsync(&v, g->eout, sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -724,6 +731,7 @@ int sbp_energy(SbpGrid* g, double* out, void* stream) {
 
 int sbp_set_sources(SbpGrid* g, int32_t n, const SbpSource* srcs, const double* jmet, void* stream) {
   if (int rc = check_ready(g)) return rc;
+  if (g->slab.ns_global > 0 && n > 0) return fail(SBP_ERR_UNSUPPORTED, "point sources on slab grids are not built");
   if (n == 0 || !srcs) {
     g->src_n = 0;
     return SBP_OK;
@@ -788,6 +796,34 @@ int sbp_set_sources(SbpGrid* g, int32_t n, const SbpSource* srcs, const double* 
 
 int sbp_set_source(SbpGrid* g, const SbpSource* src, const double* jmet, void* stream) {
   return sbp_set_sources(g, src ? 1 : 0, src, jmet, stream);
+}
+
+int sbp_set_slab(SbpGrid* g, int32_t ns_global, int32_t k_offset, int32_t ghost_lo, int32_t ghost_hi) {
+  if (!g) return fail(SBP_ERR_ARG, "null grid");
+  if (g->bound) return fail(SBP_ERR_STATE, "sbp_set_slab must come before sbp_bind");
+  const OpInfo I = op_info(g->desc.order);
+  const int L = g->desc.ns;
+  int32_t nmin = 0;
+  sbp_min_nodes(g->desc.order, &nmin);
+  if (ns_global < nmin) return fail(SBP_ERR_ARG, "the block needs at least %d planes", nmin);
+  if (ghost_lo < 0 || ghost_hi < 0 || (ghost_lo > 0 && ghost_lo < I.reach) || (ghost_hi > 0 && ghost_hi < I.reach))
+    return fail(SBP_ERR_ARG, "ghost planes: 0 (a face of the block) or at least %d", I.reach);
+  if (L - ghost_lo - ghost_hi < 1) return fail(SBP_ERR_ARG, "the slab owns no plane");
+  if (k_offset < 0 || k_offset + L > ns_global) return fail(SBP_ERR_ARG, "slab planes outside the block");
+  if ((ghost_lo == 0) != (k_offset == 0) || (ghost_hi == 0) != (k_offset + L == ns_global))
+    return fail(SBP_ERR_ARG, "ghost planes must be 0 exactly at the block's faces");
+  const int cw = 2 * I.b + I.reach;  // closure rows reach at most this many planes from a face
+  if ((ghost_lo == 0 || ghost_hi == 0) && L < cw)
+    return fail(SBP_ERR_ARG, "a slab at a face of the block needs at least %d local planes", cw);
+  if (ghost_lo == 0 && ghost_hi == 0) {  // the whole block: no decomposition
+    g->slab = sbp::SlabS{};
+    return SBP_OK;
+  }
+  g->slab.ghost_lo = ghost_lo;
+  g->slab.ghost_hi = ghost_hi;
+  g->slab.k_offset = k_offset;
+  g->slab.ns_global = ns_global;
+  return SBP_OK;
 }
 
 int sbp_set_batch(SbpGrid* g, int32_t nb) {
@@ -907,6 +943,7 @@ int sbp_get_state(SbpGrid* g, void* dst, int32_t flags, void* stream) {
 
 int sbp_rhs_adjoint(SbpGrid* g, const void* w, void* out, void* scratch, void* stream) {
   if (int rc = check_ready(g)) return rc;
+  if (g->slab.ns_global > 0) return fail(SBP_ERR_UNSUPPORTED, "the adjoint on slab grids is not built");
   if (!op_info(g->desc.order).adjoint) return fail(SBP_ERR_UNSUPPORTED, "the adjoint is built for orders 2, 4, 6");
   if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
   if (!w || !out || !scratch || w == out || w == scratch || out == scratch)
@@ -921,6 +958,7 @@ int sbp_adjoint_stage(SbpGrid* g, int32_t stage, double dt, const void* u_stage,
                       void* scratch, const double* rlmj, double* grad, void* stream) {
   if (int rc = check_ready(g)) return rc;
   if (!op_info(g->desc.order).adjoint) return fail(SBP_ERR_UNSUPPORTED, "the adjoint is built for orders 2, 4, 6");
+  if (g->slab.ns_global > 0) return fail(SBP_ERR_UNSUPPORTED, "the adjoint on slab grids is not built");
   if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
   if (stage < 0 || stage > 4) return fail(SBP_ERR_ARG, "stage must be 0..4");
   if (!(dt > 0) || !isfinite(dt)) return fail(SBP_ERR_ARG, "dt must be positive and finite");

@@ -23,6 +23,16 @@ struct Dims {
   long long fs;  // field stride in elements
 };
 
+// A slab of a block decomposed along s: the local arrays hold the planes one device owns
+// plus ghost planes copied from its neighbours (halo exchange).  ghost_lo/ghost_hi = 0 mean
+// that the local end is a face of the whole block (closures and penalties apply there);
+// k_offset is the block's index of local plane 0; ns_global = 0 means no decomposition.
+struct SlabS {
+  int ghost_lo = 0, ghost_hi = 0;
+  int k_offset = 0;
+  int ns_global = 0;
+};
+
 enum StageMode : int {
   kModeRhs = 0,     // write dQ/dt to qout
   kModeStage = 1,   // dq <- A dq + dt L; qout <- q + B dq
@@ -56,6 +66,7 @@ struct StageArgs {
   const T* yhat;        // H^-1 P~ Wb_k (the gradient pass reads it at faces)
   const double* rlmj;   // rho, lambda, mu, J (FP64)
   double* grad;         // gradient accumulators (FP64, 3 fields)
+  SlabS slab;           // s-slab of a decomposed block (default: the whole block)
 };
 
 // Closure rows of D+ and D- (unit spacing), one private copy per translation unit; orders

@@ -86,20 +86,23 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // One warp per (r, s) row of nodes (q contiguous, coalesced); rows strided over the grid.
+// A slab of a decomposed block sums its own planes only, with the block's weights along s.
 template <typename T, int O>
 __global__ void __launch_bounds__(kEnergyThreads) energy_kernel(const T* __restrict__ q, const T* __restrict__ mat,
-                                                                Dims d, double* __restrict__ partial,
+                                                                Dims d, SlabS sl, double* __restrict__ partial,
                                                                 unsigned* status) {
   const int warps = kEnergyThreads / 32;
   const int lane = threadIdx.x & 31;
-  const int rows = d.nr * d.ns;
-  const double hq = 1.0 / (d.nq - 1), hr = 1.0 / (d.nr - 1), hs = 1.0 / (d.ns - 1);
+  const int k0 = sl.ghost_lo, nown = d.ns - sl.ghost_lo - sl.ghost_hi;
+  const int nsg = sl.ns_global > 0 ? sl.ns_global : d.ns;
+  const int rows = d.nr * nown;
+  const double hq = 1.0 / (d.nq - 1), hr = 1.0 / (d.nr - 1), hs = 1.0 / (nsg - 1);
   const long long fs = d.fs;
   double acc = 0.0;
   bool bad = false;
   for (int row = blockIdx.x * warps + (threadIdx.x >> 5); row < rows; row += gridDim.x * warps) {
-    const int j = row % d.nr, k = row / d.nr;
-    const double wjk = hr * norm_weight<O>(j, d.nr) * hs * norm_weight<O>(k, d.ns);
+    const int j = row % d.nr, k = k0 + row / d.nr;
+    const double wjk = hr * norm_weight<O>(j, d.nr) * hs * norm_weight<O>(k + sl.k_offset, nsg);
     const long long base = (long long)k * d.plane + (long long)j * d.ldq;
     double racc = 0.0;
     for (int i = lane; i < d.nq; i += 32) {
@@ -143,22 +146,22 @@ __global__ void sum_partials_kernel(const double* __restrict__ partial, int n, d
 
 template <typename T>
 cudaError_t launch_energy(const T* q, const T* mat, const Dims& d, int order, double* partial, int nblocks,
-                          double* out, unsigned* status, cudaStream_t st) {
+                          double* out, unsigned* status, cudaStream_t st, SlabS sl) {
   switch (order) {
-    case 2: energy_kernel<T, 2><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
-    case 4: energy_kernel<T, 4><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
-    case 6: energy_kernel<T, 6><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
-    case 3: energy_kernel<T, 3><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
-    case 5: energy_kernel<T, 5><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
-    case 7: energy_kernel<T, 7><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status); break;
+    case 2: energy_kernel<T, 2><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, sl, partial, status); break;
+    case 4: energy_kernel<T, 4><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, sl, partial, status); break;
+    case 6: energy_kernel<T, 6><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, sl, partial, status); break;
+    case 3: energy_kernel<T, 3><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, sl, partial, status); break;
+    case 5: energy_kernel<T, 5><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, sl, partial, status); break;
+    case 7: energy_kernel<T, 7><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, sl, partial, status); break;
     case kTraditional + 2:
-      energy_kernel<T, kTraditional + 2><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status);
+      energy_kernel<T, kTraditional + 2><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, sl, partial, status);
       break;
     case kTraditional + 4:
-      energy_kernel<T, kTraditional + 4><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status);
+      energy_kernel<T, kTraditional + 4><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, sl, partial, status);
       break;
     case kTraditional + 6:
-      energy_kernel<T, kTraditional + 6><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, partial, status);
+      energy_kernel<T, kTraditional + 6><<<nblocks, kEnergyThreads, 0, st>>>(q, mat, d, sl, partial, status);
       break;
     default: return cudaErrorInvalidValue;
   }
@@ -168,9 +171,9 @@ cudaError_t launch_energy(const T* q, const T* mat, const Dims& d, int order, do
   return cudaGetLastError();
 }
 template cudaError_t launch_energy<float>(const float*, const float*, const Dims&, int, double*, int, double*,
-                                          unsigned*, cudaStream_t);
+                                          unsigned*, cudaStream_t, SlabS);
 template cudaError_t launch_energy<double>(const double*, const double*, const Dims&, int, double*, int,
-                                           double*, unsigned*, cudaStream_t);
+                                           double*, unsigned*, cudaStream_t, SlabS);
 
 // ---------------------------------------------------------------------------
 // Point source: wsrc[n*6 + c] = -M_c delta_h at source node n; in a stage the

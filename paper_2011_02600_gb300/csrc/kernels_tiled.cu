@@ -104,11 +104,14 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
   const TileAxis ay = tile_axis(by, gridDim.y, d.nr, TY, 1);
   const int i0 = ax.origin, j0 = ay.origin;
   const int i = i0 + tx, j = j0 + ty;
-  // blockIdx.z = chunk + nchunks * member (a batch of independent states)
+  // blockIdx.z = chunk + nchunks * member (a batch of independent states).  The computed
+  // planes are [klo, khi): the whole local array but a slab's ghost planes.
+  const int klo = A.slab.ghost_lo, khi = d.ns - A.slab.ghost_hi;
+  const bool face_lo = A.slab.ghost_lo == 0, face_hi = A.slab.ghost_hi == 0;
   const int nchunks = gridDim.z / A.nb;
   const int member = blockIdx.z / nchunks;
-  const int kb = (blockIdx.z % nchunks) * chunk;
-  const int ke = min(d.ns, kb + chunk);
+  const int kb = klo + (blockIdx.z % nchunks) * chunk;
+  const int ke = min(khi, kb + chunk);
   const bool active = i >= ax.own0 && i < ax.own1 && j >= ay.own0 && j < ay.own1;
   // a tile owning nodes within b of a q face takes its q rows from a per-thread table
   const bool q_edge = ax.own0 < BC || ax.own1 > d.nq - BC;
@@ -137,8 +140,8 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
   __syncthreads();
   if (tid == 0) issue_plane(S, 0, tm, i0, j0, kb, member);
   // closure-row sums of the s closure planes this chunk reaches (while the first copy flies)
-  if (active && kb < BC) s_closure_sums<T, O, false>(q, met, d, col, scl);
-  if (active && ke > d.ns - BC) s_closure_sums<T, O, true>(q, met, d, col, scl);
+  if (active && face_lo && kb < BC) s_closure_sums<T, O, false>(q, met, d, col, scl);
+  if (active && face_hi && ke > d.ns - BC) s_closure_sums<T, O, true>(q, met, d, col, scl);
 
   auto ld = [&](const T* p, long long off) -> T { return active ? __ldg(p + off) : T(0); };
   // plane kk of field offset fo at this thread's column; zero outside the grid
@@ -326,8 +329,8 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
       const T a[3] = {st.ar[0][HX + ty][tx], st.ar[1][HX + ty][tx], st.ar[2][HX + ty][tx]};
       add_strain(a, dv, e);
     }
-    // s
-    if (k >= BC && k <= d.ns - 1 - BC) {
+    // s (closure rows only within b of a face of the whole block)
+    if ((k >= BC || !face_lo) && (k <= d.ns - 1 - BC || !face_hi)) {
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
         T sf = T(0), sv = T(0);
@@ -476,7 +479,7 @@ constexpr int NVQ() { return OpCoef<O>::r + OpCoef<O>::q; }
 
 template <typename T, int O, int KIND>
 cudaError_t launch_tiled_order(const StageArgs<T>& A, const TmaSet& tm, cudaStream_t st) {
-  const int ni = A.d.nq, nj = A.d.nr, nk = A.d.ns;
+  const int ni = A.d.nq, nj = A.d.nr, nk = A.d.ns - A.slab.ghost_lo - A.slab.ghost_hi;  // computed planes
   // s chunks: at most 96 planes; when that leaves SM slots idle (few tiles), more chunks
   // (at least 16 planes each), the count that minimises waves x (chunk + queue warm-up)
   int dev = 0, sms = 0;

@@ -50,7 +50,7 @@ cudaError_t launch_material(const double* jmet, const double* rlm, T* met, T* ma
 // block sums them in a fixed order into *out (device).
 template <typename T>
 cudaError_t launch_energy(const T* q, const T* mat, const Dims& d, int order, double* partial,
-                          int nblocks, double* out, unsigned* status, cudaStream_t st);
+                          int nblocks, double* out, unsigned* status, cudaStream_t st, SlabS sl = SlabS{});
 int energy_blocks();
 
 template <typename T>

@@ -11,8 +11,9 @@
 //    descriptors, FP32 accumulator of 128 lanes x 256 columns in tensor memory), four per slice
 //    (K = 16 each), and frees each stage with tcgen05.commit on the stage's "empty" mbarrier;
 //  * after the last slice a commit on the accumulator barrier releases the epilogue: each warp
-//    reads its 32 accumulator rows with tcgen05.ld, adds the bias, applies ReLU and stores FP32
-//    or BF16 (FP32 atomics when K is split over CTAs).
+//    reads its 32 accumulator rows with tcgen05.ld, transposes them through shared memory so
+//    that a store instruction covers 32 consecutive columns of one row, adds the bias, applies
+//    ReLU and stores FP32 or BF16 (FP32 atomics when K is split over CTAs).
 // Every mbarrier wait is bounded: on a timeout the CTA records it in a device status word
 // (sbp_nn_status), skips its stores, and still frees its tensor memory before it exits.
 #include <cuda.h>
@@ -182,44 +183,42 @@ __global__ void __launch_bounds__(THREADS, 1)
   const bool ok = *fail == 0 && nk > 0;
   if (!ok && threadIdx.x == 0 && *fail) atomicOr(&g_tc_status, 1u);
   if (ok) {
-    const int m = m0 + warp * 32 + lane;
-    const bool row_ok = m < M;
-    const float bv = (bias && blockIdx.z == 0 && row_ok) ? bias[m] : 0.f;
+    // Each warp moves its 32 accumulator rows out 32 columns at a time: tcgen05.ld gives one row
+    // per thread; the warp transposes the 32 x 32 block through its own padded shared-memory
+    // tile (the stage buffers are free once the accumulator barrier has passed) and then writes
+    // one row per instruction, 32 consecutive columns across the lanes (128-byte segments).
+    float* tile = reinterpret_cast<float*>(base) + warp * (32 * 33);
     const bool split = gridDim.z > 1;
 #pragma unroll 1
     for (int c = 0; c < BN / 32; ++c) {
-      if (n0 + 32 * c >= N) break;  // uniform over the CTA
+      const int nb = n0 + 32 * c;
+      if (nb >= N) break;  // uniform over the CTA
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * c), v);
-      if (!row_ok) continue;
-      const int nb = n0 + 32 * c;
-      const int nn = min(32, N - nb);
-      const long long row = (long long)m * ldc + nb;
-      // fully unrolled over the 32 columns (masked) so that v stays in registers
-      if (split) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (j < nn) atomicAdd((float*)C + row + j, v[j] + bv);
-      } else if (c_bf16) {
-        __nv_bfloat16* out = (__nv_bfloat16*)C + row;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          float x = v[j] + bv;
-          if (relu) x = fmaxf(x, 0.f);
-          if (j < nn) out[j] = __float2bfloat16(x);
-        }
-      } else {
-        float* out = (float*)C + row;
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          if (j < nn) {
-            float x = v[j] + bv;
-            if (beta != 0.f) x += beta * out[j];
+      for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = v[j];
+      __syncwarp();
+      const int n = nb + lane;
+#pragma unroll 4
+      for (int r = 0; r < 32; ++r) {
+        const int m = m0 + warp * 32 + r;
+        if (m >= M) break;  // uniform over the warp
+        float x = tile[r * 33 + lane] + ((bias && blockIdx.z == 0) ? bias[m] : 0.f);
+        if (n < N) {
+          const long long idx = (long long)m * ldc + n;
+          if (split) {
+            atomicAdd((float*)C + idx, x);
+          } else if (c_bf16) {
             if (relu) x = fmaxf(x, 0.f);
-            out[j] = x;
+            ((__nv_bfloat16*)C)[idx] = __float2bfloat16(x);
+          } else {
+            if (beta != 0.f) x += beta * ((const float*)C)[idx];
+            if (relu) x = fmaxf(x, 0.f);
+            ((float*)C)[idx] = x;
           }
         }
       }
+      __syncwarp();
     }
   }
   fence_before_sync();

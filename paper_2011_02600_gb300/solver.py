@@ -28,10 +28,11 @@ class ElasticSolver:
 
     nodes = (nq, nr, ns); order: 2..7 for the upwind pairs of Table 1, 2, 4 or 6 with
     operator="traditional" for the central operators of Table 2; precision in {32, 64};
-    bc: six face conditions ("free",) / ("char", gamma).
+    bc: six face conditions ("free",) / ("char", gamma); slab: (ns of the whole block,
+    k_offset, ghost_lo, ghost_hi) when the grid is one s-slab of a decomposed block (slab.py).
     """
 
-    def __init__(self, nodes, order, precision=32, bc=None, device="cuda", batch=1, operator="upwind"):
+    def __init__(self, nodes, order, precision=32, bc=None, device="cuda", batch=1, operator="upwind", slab=None):
         if bc is None:
             bc = [("char", 0.0)] * 5 + [("free",)]
         if operator not in ("upwind", "traditional"):
@@ -48,6 +49,8 @@ class ElasticSolver:
         self.batch = int(batch)
         if self.batch != 1:
             L.sbp_set_batch(self.h, self.batch)
+        if slab is not None:   # (ns of the block, k_offset, ghost_lo, ghost_hi): see slab.py
+            L.sbp_set_slab(self.h, *slab)
         self.ldq, self.fs, self.elem = L.sbp_layout(self.h)
         kw = dict(dtype=self.dtype, device=self.device)
         nst = 9 * self.batch

@@ -157,3 +157,19 @@ def test_generated_traditional_coefficients_match_oracle():
             for j in range(len(dp[i])):
                 assert dp[i][j] == D[i][j]
         assert alpha == op.traditional_stencil(order)
+
+
+def test_set_slab_validation(lib):
+    """sbp_set_slab (an s-slab of a decomposed block): ghost counts of 0 exactly at the block's
+    faces and at least the stencil's reach elsewhere, planes inside the block, a face slab big
+    enough for its closures, and only before sbp_bind."""
+    free = [("free",)] * 6
+    h = L.sbp_create_grid((20, 20, 24), 4, 64, free)
+    for bad in [(60, 10, 2, 3), (60, 0, 3, 3), (60, 40, 3, 0), (60, 50, 3, 3), (8, 0, 0, 3), (60, 10, 3, 3 - 3),
+                (24, 0, 0, 0 + 1)]:
+        _expect(1, L.sbp_set_slab, h, *bad)
+    L.sbp_set_slab(h, 60, 10, 3, 3)       # interior slab: planes 10..33 of 60
+    L.sbp_set_slab(h, 60, 0, 0, 3)        # low face slab
+    L.sbp_set_slab(h, 60, 36, 3, 0)       # high face slab
+    L.sbp_set_slab(h, 24, 0, 0, 0)        # the whole block again
+    L.sbp_destroy(h)
