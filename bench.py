@@ -40,9 +40,11 @@ WORKLOAD = "topo1025_o6_fp32"
 BYTES_PER_NODE_STAGE = 192        # 48 FP32 values per node per stage (algorithmic)
 BYTES_PER_NODE_STAGE0 = 156       # first stage: A_0 = 0, the RK register is not read
 NOMINAL_HBM_GBS = 7900.0          # HBM3e nominal, for the second fraction
-FLOP_PER_NODE_STAGE = 420         # order 6: 18 one-axis derivatives x 7 taps x 2, flux 45, strain 54,
-                                  # Hooke 12, Runge-Kutta 36, scaling 20
-FP64_PEAK_TFLOPS = 1.25           # GB300 FP64 nominal (the FP64 path is bound by it, not by HBM)
+FLOP_PER_NODE_STAGE = 444         # order 6, interior node, counted from the tiled kernel's arithmetic (an FMA
+                                  # is 2): fluxes F_q, F_r on the tile and halo (1.19 + 1.75 per node) and F_s,
+                                  # 15 each: 59; D- and D+ on 3 axes x 3 components, 7 taps and a scaling: 270;
+                                  # strain rows 54; P~ 16; Runge-Kutta update 45
+FP64_NOMINAL_TFLOPS = 1.25        # GB300 FP64 nominal; the roofline uses the rate measured on the device
 
 
 def _peaks():
@@ -358,13 +360,20 @@ def run_surrogate_kernels(args, local):
     B_ = torch.randn(K, N, generator=g).to(torch.bfloat16).cuda()
     C_ = torch.empty(M, N, device="cuda")
     def time_gemm(path, reps=20):
+        """Device time of one GEMM: `reps` launches captured in a CUDA graph and replayed, so that
+        the host's per-call work (argument marshalling) stays out of the measurement."""
         L.sbp_nn_set_gemm_path(path)
-        for _ in range(3):
+        for _ in range(3):   # warm-up: attributes set and operand tensor maps encoded
             L.sbp_nn_gemm(M, N, K, A_, K, 0, B_, N, 0, C_, N, 0, None, 0, 0.0, _stream())
         torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(reps):
+                L.sbp_nn_gemm(M, N, K, A_, K, 0, B_, N, 0, C_, N, 0, None, 0, 0.0, _stream())
+        graph.replay()
+        torch.cuda.synchronize()
         ev[0].record(stream)
-        for _ in range(reps):
-            L.sbp_nn_gemm(M, N, K, A_, K, 0, B_, N, 0, C_, N, 0, None, 0, 0.0, _stream())
+        graph.replay()
         ev[1].record(stream)
         torch.cuda.synchronize()
         L.sbp_nn_set_gemm_path(0)
@@ -527,13 +536,15 @@ def main():
             "launches": launches, "peak_source": "measured" if peaks else "fallback",
             "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
     if elem == 8:
-        # FP64 is bound by the FP64 pipe, not by HBM
+        # FP64 is bound by the FP64 pipe, not by HBM: its peak is measured here by an FMA-chain probe
+        fp64_peak = L.sbp_probe_fp64_rate(2000000, _stream())
         tflops = FLOP_PER_NODE_STAGE * knodes / (avg_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tflops / FP64_PEAK_TFLOPS, "traffic": None, "kernel": kind,
+        roof = {"bound": "alu", "achieved": tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": tflops / fp64_peak, "traffic": None, "kernel": kind,
                 "algorithmic_flop_per_launch": FLOP_PER_NODE_STAGE * knodes, "avg_launch_ms": avg_ms,
-                "launches": launches, "peak_source": "nominal FP64 rate",
-                "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak}
+                "launches": launches,
+                "peak_source": "measured: FP64 FMA-chain probe (sbp_probe_fp64_rate) on this device",
+                "nominal_peak": FP64_NOMINAL_TFLOPS, "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak}
 
     # end to end through the C ABI: per step, the state uploaded from pinned host memory
     # (sbp_set_state), one RK step (sbp_step_n), the state downloaded to pinned host memory

@@ -68,6 +68,7 @@ extern "C" {
 
 #define SBP_BC_FREE 0  /* free surface, Eq. SAT_free_surface */
 #define SBP_BC_CHAR 1  /* general condition with gamma, Eq. BC_General2 / Eq. SAT_General */
+#define SBP_BC_INTERFACE 2  /* shared face with another block (sbp_set_interface) */
 
 /* Status bits reported by sbp_status (device-side findings). */
 #define SBP_STATUS_NONFINITE 1u
@@ -79,7 +80,7 @@ typedef struct SbpGridDesc {
   int32_t nq, nr, ns;     /* nodes per axis; each >= sbp_min_nodes(order) */
   int32_t order;          /* operator code: upwind order 2..7, or SBP_TRADITIONAL + 2, 4, 6 */
   int32_t precision;      /* 32 or 64 */
-  int32_t bc_kind[6];     /* SBP_BC_FREE or SBP_BC_CHAR per face */
+  int32_t bc_kind[6];     /* SBP_BC_FREE, SBP_BC_CHAR or SBP_BC_INTERFACE per face */
   double bc_gamma[6];     /* gamma in [-1, 1] for SBP_BC_CHAR faces (Eq. BC_General2) */
 } SbpGridDesc;
 
@@ -132,11 +133,13 @@ int sbp_set_batch(SbpGrid* grid, int32_t nb);
  * that, with the ghost planes of the state filled from the neighbours before
  * every stage (the caller's halo exchange), the owned planes evolve exactly as in
  * the undivided block.  sbp_energy sums the owned planes with the block's
- * weights.  jmet given to sbp_set_material must be the block's metrics at the
- * local planes (sbp_metrics refuses slab grids: its closures would be the local
- * array's).  Point sources, the adjoint and the general kernel path return
- * UNSUPPORTED on slab grids.  Call before sbp_bind; ghost_lo = ghost_hi = 0
- * restores the whole block. */
+ * weights, and sbp_metrics fills the owned planes of jmet with the block's
+ * metrics (the block's spacing and closures, the coordinates of the ghost planes
+ * as stencil taps); jmet given to sbp_set_material must hold the block's metrics
+ * at every local plane, ghost planes included, e.g. from sbp_metrics on a slab
+ * grid whose owned planes are these local planes.  Point sources, the adjoint and
+ * the general kernel path return UNSUPPORTED on slab grids.  Call before
+ * sbp_bind; ghost_lo = ghost_hi = 0 restores the whole block. */
 int sbp_set_slab(SbpGrid* grid, int32_t ns_global, int32_t k_offset, int32_t ghost_lo, int32_t ghost_hi);
 
 /* Bind the caller's device buffers (solver precision, layout of sbp_layout):
@@ -233,6 +236,30 @@ int sbp_set_receivers(SbpGrid* grid, int32_t n, const int32_t* ijk, void* traces
 int sbp_set_receivers_xyz(SbpGrid* grid, int32_t n, const double* xyz, const double* coords, int32_t face,
                           void* traces, int32_t n_t, int32_t* ijk_out);
 
+/* Two blocks coupled at a shared face (Section 7.1 splits the LOH1 domain into
+ * two blocks at its material interface and couples them weakly with penalties).
+ * A face of kind SBP_BC_INTERFACE receives the penalty of Eq. penalty_terms with
+ * the hat variables of a locked interface: velocity and traction (T = sigma n,
+ * n = a_xi/|a_xi|) continuous, the outgoing characteristic of each side kept
+ * (Appendix A's construction with the interface conditions in place of Eq.
+ * BC_General2).  Block "-" has the shared face at xi = 1, block "+" at xi = 0 of
+ * the same axis xi; the two faces must hold the same nodes in the same order
+ * (same node counts on the face's two axes, same orientation) and the same
+ * operator.
+ * sbp_interface_trace writes, for face `face` of this grid and the state q (9 B
+ * fields; NULL: the current state), the face trace the other block's penalty
+ * needs: 8 B face arrays of the solver precision, member b's field c (v_x, v_y,
+ * v_z, T_x, T_y, T_z, Z_p, Z_s) at trace[(8 b + c) n_face + idx], idx = k nr + j
+ * on q faces, k nq + i on r faces, j nq + i on s faces.  sbp_set_interface tells
+ * this grid where the other block's trace of the shared face lies (device
+ * memory, read by every later stage or sbp_rhs; the caller refreshes it from the
+ * other block's stage input before each stage, e.g. trace both blocks, then run
+ * the stage on both).  A stage on a grid with an interface face lacking a trace
+ * returns STATE; sbp_step_n returns UNSUPPORTED for such grids (their traces
+ * must be refreshed between the stages), as do the adjoint calls. */
+int sbp_interface_trace(SbpGrid* grid, int32_t face, const void* q, void* trace, void* stream);
+int sbp_set_interface(SbpGrid* grid, int32_t face, const void* other_trace);
+
 /* Memory and layout flags of the copy calls below. */
 #define SBP_MEM_HOST 1      /* the caller's buffer is host memory (pageable or pinned); else device */
 #define SBP_LAYOUT_DENSE 2  /* fields packed [field][s][r][q] without padding; else the grid layout */
@@ -294,6 +321,14 @@ int sbp_misfit(SbpGrid* grid, const void* q, const double* data, double weight, 
  * status word; the context stays usable.  SBP_ERR_ARG for polls outside
  * that range. */
 int sbp_selftest_wait_timeout(SbpGrid* grid, uint32_t polls, void* stream);
+
+/* Measured FP64 arithmetic rate of the current device (no paper counterpart; the
+ * denominator of the FP64 solver's roofline, which is bound by the FP64 pipe, not
+ * by HBM): 8 independent fused multiply-add chains of `iters` steps (1000..1e8) in
+ * each of 2048 threads per SM, timed with CUDA events on the stream after a
+ * warm-up launch; *tflops = 2 x FMAs / time.  Changes no device setting; the
+ * clocks are whatever the device runs at.  Synchronises the stream. */
+int sbp_probe_fp64_rate(int32_t iters, double* tflops, void* stream);
 
 /* Copy the device status word into *bits and clear it (synchronises). */
 int sbp_status(SbpGrid* grid, uint32_t* bits, void* stream);

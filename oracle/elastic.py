@@ -231,6 +231,8 @@ def rhs_raw(Q, scheme, a, mat, bc, data=None, with_sat=True, diag=None):
             e[c] += B[c]
     if with_sat:
         for face in range(6):
+            if bc[face][0] == "interface":      # coupled to another block: multiblock.py adds it
+                continue
             xi, side = divmod(face, 2)
             sl = face_slice(xi, side, scheme.nodes[xi])
             vs, Ts = (None, None)

@@ -11,6 +11,7 @@ from . import build as _build
 
 SBP_BC_FREE = 0
 SBP_BC_CHAR = 1
+SBP_BC_INTERFACE = 2
 SBP_TRADITIONAL = 100
 SBP_MEM_HOST = 1
 SBP_LAYOUT_DENSE = 2
@@ -25,7 +26,8 @@ EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sb
             "sbp_nn_upsample2", "sbp_nn_relu_backward", "sbp_nn_bias_grad", "sbp_nn_mse", "sbp_nn_adam",
             "sbp_nn_mlp_to_conv", "sbp_nn_cast_bf16", "sbp_nn_moment_combine", "sbp_selftest_wait_timeout", "sbp_last_error",
             "sbp_set_receivers_xyz", "sbp_record_receivers", "sbp_set_state", "sbp_get_state",
-            "sbp_nn_set_gemm_path", "sbp_nn_status", "sbp_set_slab")
+            "sbp_nn_set_gemm_path", "sbp_nn_status", "sbp_set_slab", "sbp_interface_trace", "sbp_set_interface",
+            "sbp_probe_fp64_rate")
 
 
 class SbpError(RuntimeError):
@@ -107,6 +109,9 @@ def lib(path=None):
         "sbp_nn_set_gemm_path": [i32],
         "sbp_nn_status": [ctypes.POINTER(ctypes.c_uint32)],
         "sbp_set_slab": [P, i32, i32, i32, i32],
+        "sbp_interface_trace": [P, i32, P, P, P],
+        "sbp_set_interface": [P, i32, P],
+        "sbp_probe_fp64_rate": [i32, ctypes.POINTER(dbl), P],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -144,8 +149,8 @@ def sbp_create_grid(nodes, order, precision, bc):
     d.nq, d.nr, d.ns = nodes
     d.order, d.precision = order, precision
     for f, c in enumerate(bc):
-        d.bc_kind[f] = SBP_BC_FREE if c[0] == "free" else SBP_BC_CHAR
-        d.bc_gamma[f] = 0.0 if c[0] == "free" else float(c[1])
+        d.bc_kind[f] = {"free": SBP_BC_FREE, "char": SBP_BC_CHAR, "interface": SBP_BC_INTERFACE}[c[0]]
+        d.bc_gamma[f] = float(c[1]) if c[0] == "char" else 0.0
     h = P()
     _check(lib().sbp_create_grid(ctypes.byref(d), ctypes.byref(h)))
     return h
@@ -303,6 +308,20 @@ def sbp_misfit(h, q, data, weight, acc, ubar, stream):
 
 def sbp_set_slab(h, ns_global, k_offset, ghost_lo, ghost_hi):
     _check(lib().sbp_set_slab(h, ns_global, k_offset, ghost_lo, ghost_hi))
+
+
+def sbp_interface_trace(h, face, q, trace, stream):
+    _check(lib().sbp_interface_trace(h, face, _ptr(q), _ptr(trace), stream))
+
+
+def sbp_set_interface(h, face, other_trace):
+    _check(lib().sbp_set_interface(h, face, _ptr(other_trace)))
+
+
+def sbp_probe_fp64_rate(iters, stream):
+    out = ctypes.c_double()
+    _check(lib().sbp_probe_fp64_rate(iters, ctypes.byref(out), stream))
+    return out.value
 
 
 def sbp_set_batch(h, nb):

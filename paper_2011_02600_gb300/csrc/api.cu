@@ -160,6 +160,7 @@ struct SbpGrid {
   int n_t = 0;
   bool use_tiled = true;
   sbp::SlabS slab;         // s-slab of a decomposed block (sbp_set_slab); default: the whole block
+  const void* iface[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // other blocks' traces
   void* sclose = nullptr;  // tiled kernel scratch (s-closure sums), owned by the library
   // tensor maps of the tiled stage kernel, per state buffer (q0, q1)
   bool tma_ok[2] = {false, false};
@@ -179,6 +180,27 @@ struct NvtxRange {
   explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
   ~NvtxRange() { nvtxRangePop(); }
 };
+
+// Nodes of face f (0..5) of the grid.
+long long face_nodes(const SbpGrid* g, int f) {
+  const int xi = f / 2;
+  return xi == 0 ? (long long)g->desc.nr * g->desc.ns
+                 : xi == 1 ? (long long)g->desc.nq * g->desc.ns : (long long)g->desc.nq * g->desc.nr;
+}
+
+bool has_interface(const SbpGrid* g) {
+  for (int f = 0; f < 6; ++f)
+    if (g->desc.bc_kind[f] == SBP_BC_INTERFACE) return true;
+  return false;
+}
+
+// Every interface face needs the other block's trace before a stage can run.
+int check_interfaces(const SbpGrid* g) {
+  for (int f = 0; f < 6; ++f)
+    if (g->desc.bc_kind[f] == SBP_BC_INTERFACE && !g->iface[f])
+      return fail(SBP_ERR_STATE, "face %d is an interface without the other block's trace (sbp_set_interface)", f);
+  return SBP_OK;
+}
 
 // Elements of the tiled kernel's s-closure scratch per state: 2 ends x b rows x 6 planes.
 long long sclose_elems(const SbpGrid* g) { return 2LL * closure_b(g->desc.order) * 6 * g->dims.plane; }
@@ -218,6 +240,8 @@ sbp::StageArgs<T> make_args(const SbpGrid* g, const void* q, void* qout, int mod
   for (int f = 0; f < 6; ++f) {
     A.bc_kind[f] = g->desc.bc_kind[f];
     A.bc_gamma[f] = (T)g->desc.bc_gamma[f];
+    A.ifc.other[f] = (const T*)g->iface[f];
+    A.ifc.n_face[f] = face_nodes(g, f);
   }
   const double w0 = op_info(g->desc.order).w0;
   for (int x = 0; x < 3; ++x) {
@@ -311,6 +335,7 @@ int run_stage_kernels(SbpGrid* g, const void* q, void* qout, int mode, double a,
                       cudaStream_t st, int nb = 1) {
   if (g->slab.ns_global > 0 && !g->use_tiled)
     return fail(SBP_ERR_UNSUPPORTED, "a slab grid runs the tiled kernel only (sbp_set_kernel_path(0))");
+  if (int rc = check_interfaces(g)) return rc;
   sbp::StageArgs<T> A = make_args<T>(g, q, qout, mode, a, bcoef, dt, nb);
   if (g->use_tiled) {
     sbp::TmaSet local;
@@ -503,7 +528,7 @@ int sbp_create_grid(const SbpGridDesc* desc, SbpGrid** out) {
                 desc->nq, desc->nr, desc->ns);
   if (desc->precision != 32 && desc->precision != 64) return fail(SBP_ERR_ARG, "precision must be 32 or 64");
   for (int f = 0; f < 6; ++f) {
-    if (desc->bc_kind[f] != SBP_BC_FREE && desc->bc_kind[f] != SBP_BC_CHAR)
+    if (desc->bc_kind[f] != SBP_BC_FREE && desc->bc_kind[f] != SBP_BC_CHAR && desc->bc_kind[f] != SBP_BC_INTERFACE)
       return fail(SBP_ERR_ARG, "face %d: unknown boundary kind %d", f, desc->bc_kind[f]);
     if (desc->bc_kind[f] == SBP_BC_CHAR && !(fabs(desc->bc_gamma[f]) <= 1.0))
       return fail(SBP_ERR_ARG, "face %d: gamma must lie in [-1, 1]", f);
@@ -587,11 +612,9 @@ int sbp_bind(SbpGrid* g, void* q0, void* q1, void* dq, void* met, void* mat) {
 
 int sbp_metrics(SbpGrid* g, const double* xyz, double* jmet, void* stream) {
   if (int rc = check_ready(g)) return rc;
-  if (g->slab.ns_global > 0)
-    return fail(SBP_ERR_UNSUPPORTED, "a slab grid takes the block's metrics restricted to its planes (see sbp_set_slab)");
   if (!xyz || !jmet) return fail(SBP_ERR_ARG, "null coordinate or metric buffer");
-  cudaError_t e =
-      sbp::launch_metrics(xyz, jmet, g->dims, op_info(g->desc.order).metric_order, g->status, (cudaStream_t)stream);
+  cudaError_t e = sbp::launch_metrics(xyz, jmet, g->dims, op_info(g->desc.order).metric_order, g->status,
+                                      (cudaStream_t)stream, g->slab);
   return e == cudaSuccess ? SBP_OK : cuda_fail(e, "metrics");
 }
 
@@ -631,6 +654,9 @@ int sbp_step_n(SbpGrid* g, int32_t n, double dt, void* stream) {
   if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
   if (n < 0) return fail(SBP_ERR_ARG, "negative step count");
   if (!(dt > 0) || !isfinite(dt)) return fail(SBP_ERR_ARG, "dt must be positive and finite");
+  if (has_interface(g))
+    return fail(SBP_ERR_UNSUPPORTED, "a grid with interface faces steps stage by stage (sbp_rk_stage), its "
+                                     "traces refreshed before every stage");
   cudaStream_t st = (cudaStream_t)stream;
   for (int s = 0; s < n; ++s) {
     for (int k = 0; k < 5; ++k) {
@@ -826,6 +852,47 @@ int sbp_set_slab(SbpGrid* g, int32_t ns_global, int32_t k_offset, int32_t ghost_
   return SBP_OK;
 }
 
+int sbp_set_interface(SbpGrid* g, int32_t face, const void* other_trace) {
+  if (!g) return fail(SBP_ERR_ARG, "null grid");
+  if (face < 0 || face > 5) return fail(SBP_ERR_ARG, "face must be 0..5");
+  if (g->desc.bc_kind[face] != SBP_BC_INTERFACE) return fail(SBP_ERR_ARG, "face %d is not an interface face", face);
+  g->iface[face] = other_trace;
+  return SBP_OK;
+}
+
+int sbp_interface_trace(SbpGrid* g, int32_t face, const void* q, void* trace, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
+  if (face < 0 || face > 5) return fail(SBP_ERR_ARG, "face must be 0..5");
+  if (!trace) return fail(SBP_ERR_ARG, "null trace buffer");
+  const void* src = q ? q : g->q[g->cur];
+  const long long bs = 9 * g->dims.fs;
+  cudaError_t e = g->elem == 4 ? sbp::launch_interface_trace<float>((const float*)src, (const float*)g->met,
+                                                                    (const float*)g->mat, g->dims, face, g->nb, bs,
+                                                                    (float*)trace, (cudaStream_t)stream)
+                               : sbp::launch_interface_trace<double>((const double*)src, (const double*)g->met,
+                                                                     (const double*)g->mat, g->dims, face, g->nb, bs,
+                                                                     (double*)trace, (cudaStream_t)stream);
+  return e == cudaSuccess ? SBP_OK : cuda_fail(e, "interface trace");
+}
+
+int sbp_probe_fp64_rate(int32_t iters, double* tflops, void* stream) {
+  if (!tflops || iters < 1000 || iters > 100000000) return fail(SBP_ERR_ARG, "iters must lie in 1000..1e8");
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "device query");
+  const int blocks = sms * 8;  // 2048 threads per SM: full occupancy
+  double* sink = nullptr;
+  e = cudaMalloc(&sink, sizeof(double) * blocks);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = sbp::probe_fp64_fma(iters, blocks, sink, &ms, (cudaStream_t)stream);
+  cudaFree(sink);
+  if (e != cudaSuccess) return cuda_fail(e, "FP64 rate probe");
+  *tflops = 16.0 * iters * blocks * 256.0 / (ms * 1e-3) / 1e12;
+  return SBP_OK;
+}
+
 int sbp_set_batch(SbpGrid* g, int32_t nb) {
   if (!g) return fail(SBP_ERR_ARG, "null grid");
   if (g->bound) return fail(SBP_ERR_STATE, "sbp_set_batch must come before sbp_bind");
@@ -943,6 +1010,7 @@ int sbp_get_state(SbpGrid* g, void* dst, int32_t flags, void* stream) {
 
 int sbp_rhs_adjoint(SbpGrid* g, const void* w, void* out, void* scratch, void* stream) {
   if (int rc = check_ready(g)) return rc;
+  if (has_interface(g)) return fail(SBP_ERR_UNSUPPORTED, "the adjoint with interface faces is not built");
   if (g->slab.ns_global > 0) return fail(SBP_ERR_UNSUPPORTED, "the adjoint on slab grids is not built");
   if (!op_info(g->desc.order).adjoint) return fail(SBP_ERR_UNSUPPORTED, "the adjoint is built for orders 2, 4, 6");
   if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
@@ -959,6 +1027,7 @@ int sbp_adjoint_stage(SbpGrid* g, int32_t stage, double dt, const void* u_stage,
   if (int rc = check_ready(g)) return rc;
   if (!op_info(g->desc.order).adjoint) return fail(SBP_ERR_UNSUPPORTED, "the adjoint is built for orders 2, 4, 6");
   if (g->slab.ns_global > 0) return fail(SBP_ERR_UNSUPPORTED, "the adjoint on slab grids is not built");
+  if (has_interface(g)) return fail(SBP_ERR_UNSUPPORTED, "the adjoint with interface faces is not built");
   if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
   if (stage < 0 || stage > 4) return fail(SBP_ERR_ARG, "stage must be 0..4");
   if (!(dt > 0) || !isfinite(dt)) return fail(SBP_ERR_ARG, "dt must be positive and finite");

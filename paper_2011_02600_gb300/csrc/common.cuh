@@ -33,6 +33,23 @@ struct SlabS {
   int ns_global = 0;
 };
 
+// Face kind of an interface between two blocks (the host's SBP_BC_INTERFACE).
+constexpr int kBcInterface = 2;
+
+// The other block's trace at an interface face (one per face; null when the face is no
+// interface): 8 fields of the face's nodes, v (3), T = sigma n (3), Z_p, Z_s, each field a face
+// array in the order of face_index; member b of a batch at other + b * 8 * n_face.
+template <typename T>
+struct IfaceArgs {
+  const T* other[6];
+  long long n_face[6];
+};
+
+// Index of a node on face xi (0: q faces, [k][j]; 1: r faces, [k][i]; 2: s faces, [j][i]).
+__host__ __device__ __forceinline__ long long face_index(int xi, int i, int j, int k, int nq, int nr) {
+  return xi == 0 ? (long long)k * nr + j : xi == 1 ? (long long)k * nq + i : (long long)j * nq + i;
+}
+
 enum StageMode : int {
   kModeRhs = 0,     // write dQ/dt to qout
   kModeStage = 1,   // dq <- A dq + dt L; qout <- q + B dq
@@ -67,6 +84,7 @@ struct StageArgs {
   const double* rlmj;   // rho, lambda, mu, J (FP64)
   double* grad;         // gradient accumulators (FP64, 3 fields)
   SlabS slab;           // s-slab of a decomposed block (default: the whole block)
+  IfaceArgs<T> ifc;     // the other blocks' traces at interface faces (none by default)
 };
 
 // Closure rows of D+ and D- (unit spacing), one private copy per translation unit; orders
@@ -246,6 +264,58 @@ __device__ __forceinline__ void add_penalty(int side, int kind, T gamma, T inv_h
   e[5] += fs * (n[2] * Gt[1] + n[1] * Gt[2]);
 }
 
+// Interface penalty of one face node (Section 7.1's two blocks coupled weakly; the penalty of
+// Eq. penalty_terms with the hat variables of a locked interface, velocity and traction
+// continuous, both outgoing characteristics kept).  side 1: this block's face is at xi = 1
+// (block "-"), side 0: at xi = 0 (block "+"); o: the other block's v, T, Z_p, Z_s at the node.
+// With vhat from the two characteristics, G = Z (v - vhat) per part, G~ = G / Z = v - vhat:
+//    vhat_n = (Z-_p v-_n - T-_n + Z+_p v+_n + T+_n) / (Z-_p + Z+_p), likewise tangential with Z_s,
+//    rv -= |a| G / H0,  e -= |a| (-+)(n (x) G~)_sym / H0   (the signs of add_penalty).
+template <typename T>
+__device__ __forceinline__ void add_interface_penalty(int side, T inv_h0, const T v[3], const T s[6], const T a[3],
+                                                      T irhoJ, T lamJ, T muJ, const T o[8], T rv[3], T e[6]) {
+  const T an = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  const T ian = T(1) / an;
+  const T n[3] = {a[0] * ian, a[1] * ian, a[2] * ian};
+  T Tr[3];
+  flux(n, s, Tr);
+  const T Zp = sqrt((lamJ + T(2) * muJ) / irhoJ);
+  const T Zs = sqrt(muJ / irhoJ);
+  // (this side, other side) as ("-", "+")
+  const T* vm = side == 1 ? v : o;
+  const T* Tm = side == 1 ? Tr : o + 3;
+  const T* vp = side == 1 ? o : v;
+  const T* Tp = side == 1 ? o + 3 : Tr;
+  const T Zpm = side == 1 ? Zp : o[6], Zsm = side == 1 ? Zs : o[7];
+  const T Zpp = side == 1 ? o[6] : Zp, Zsp = side == 1 ? o[7] : Zs;
+  const T vmn = vm[0] * n[0] + vm[1] * n[1] + vm[2] * n[2], Tmn = Tm[0] * n[0] + Tm[1] * n[1] + Tm[2] * n[2];
+  const T vpn = vp[0] * n[0] + vp[1] * n[1] + vp[2] * n[2], Tpn = Tp[0] * n[0] + Tp[1] * n[1] + Tp[2] * n[2];
+  const T vhn = (Zpm * vmn - Tmn + Zpp * vpn + Tpn) / (Zpm + Zpp);
+  const T vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  const T isz = T(1) / (Zsm + Zsp);
+  T G[3], Gt[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const T vht = (Zsm * (vm[c] - vmn * n[c]) - (Tm[c] - Tmn * n[c]) + Zsp * (vp[c] - vpn * n[c]) +
+                   (Tp[c] - Tpn * n[c])) * isz;
+    const T dt_ = (v[c] - vn * n[c]) - vht;   // tangential part of v - vhat
+    const T dn = vn - vhn;                     // normal part
+    Gt[c] = dn * n[c] + dt_;
+    G[c] = Zp * dn * n[c] + Zs * dt_;
+  }
+  const T f = an * inv_h0;
+  rv[0] -= f * G[0];
+  rv[1] -= f * G[1];
+  rv[2] -= f * G[2];
+  const T fs = side == 0 ? f : -f;
+  e[0] += fs * n[0] * Gt[0];
+  e[1] += fs * n[1] * Gt[1];
+  e[2] += fs * n[2] * Gt[2];
+  e[3] += fs * (n[1] * Gt[0] + n[0] * Gt[1]);
+  e[4] += fs * (n[2] * Gt[0] + n[0] * Gt[2]);
+  e[5] += fs * (n[2] * Gt[1] + n[1] * Gt[2]);
+}
+
 // dQ/dt = P~ (rv, e): velocity rows / (rho J); stress rows C e / J.
 template <typename T>
 __device__ __forceinline__ void apply_P(const T rv[3], const T e[6], T irhoJ, T lamJ, T muJ, T d[9]) {
@@ -266,14 +336,17 @@ __device__ __forceinline__ void apply_P(const T rv[3], const T e[6], T irhoJ, T 
 // coordinates xyz (3 FP64 fields), into jmet (J, then the 9 metrics; FP64).  Coordinate
 // derivatives use D_c = (D+ + D-)/2 along each axis.  Returns false where J <= 0.
 template <int O>
+// On a slab of a decomposed block (sl) node t enumerates the owned planes, and the s position and
+// node count are the block's: the rows of D_c along s are the block's, their taps reaching into
+// the ghost planes.
 __device__ __forceinline__ bool metrics_at(const double* __restrict__ xyz, double* __restrict__ jmet, const Dims& d,
-                                           long long t) {
+                                           long long t, SlabS sl = SlabS{}) {
   const int i = (int)(t % d.nq);
   const int j = (int)((t / d.nq) % d.nr);
-  const int k = (int)(t / ((long long)d.nq * d.nr));
+  const int k = sl.ghost_lo + (int)(t / ((long long)d.nq * d.nr));
   const long long n0 = (long long)k * d.plane + (long long)j * d.ldq + i;
-  const int pos[3] = {i, j, k};
-  const int N[3] = {d.nq, d.nr, d.ns};
+  const int pos[3] = {i, j, k + sl.k_offset};
+  const int N[3] = {d.nq, d.nr, sl.ns_global > 0 ? sl.ns_global : d.ns};
   const long long stride[3] = {1, d.ldq, d.plane};
   double der[3][3];  // der[xi][c] = d x_c / d xi
 #pragma unroll
@@ -384,19 +457,40 @@ __device__ __forceinline__ void axis_operator_global(const T* __restrict__ q, co
   add_strain(a0, dv, e);
 }
 
+// Penalty of face (xi, side) at one node: the boundary penalties of add_penalty, or the interface
+// penalty with the other block's trace at the node (ifc; member b of a batch).
+template <typename T>
+__device__ __forceinline__ void face_penalty_at(int xi, int side, const int pos[3], const int N[3], const T a[3],
+                                                const T qc[9], T irhoJ, T lamJ, T muJ, const int bc_kind[6],
+                                                const T bc_gamma[6], const T inv_h0[3], T rv[3], T e[6],
+                                                const IfaceArgs<T>* ifc, int member) {
+  const int face = 2 * xi + side;
+  if (bc_kind[face] == kBcInterface) {
+    if (!ifc || !ifc->other[face]) return;  // refused on the host before any launch
+    const long long nf = ifc->n_face[face];
+    const T* src = ifc->other[face] + (long long)member * 8 * nf + face_index(xi, pos[0], pos[1], pos[2], N[0], N[1]);
+    T o[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) o[c] = src[c * nf];
+    add_interface_penalty<T>(side, inv_h0[xi], qc, qc + 3, a, irhoJ, lamJ, muJ, o, rv, e);
+    return;
+  }
+  add_penalty<T>(side, bc_kind[face], bc_gamma[face], inv_h0[xi], qc, qc + 3, a, irhoJ, lamJ, muJ, rv, e);
+}
+
 // Penalties of every face the node lies on (positions pos, sizes N), in the order
 // q = 0, q = 1, r = 0, r = 1, s = 0, s = 1.  a[xi] is a^xi at the node, qc its state.
 template <typename T>
 __device__ __forceinline__ void add_face_penalties(const int pos[3], const int N[3], const T a[3][3],
                                                    const T qc[9], T irhoJ, T lamJ, T muJ, const int bc_kind[6],
-                                                   const T bc_gamma[6], const T inv_h0[3], T rv[3], T e[6]) {
+                                                   const T bc_gamma[6], const T inv_h0[3], T rv[3], T e[6],
+                                                   const IfaceArgs<T>* ifc = nullptr, int member = 0) {
 #pragma unroll
   for (int xi = 0; xi < 3; ++xi) {
     if (pos[xi] == 0)
-      add_penalty<T>(0, bc_kind[2 * xi], bc_gamma[2 * xi], inv_h0[xi], qc, qc + 3, a[xi], irhoJ, lamJ, muJ, rv, e);
+      face_penalty_at<T>(xi, 0, pos, N, a[xi], qc, irhoJ, lamJ, muJ, bc_kind, bc_gamma, inv_h0, rv, e, ifc, member);
     if (pos[xi] == N[xi] - 1)
-      add_penalty<T>(1, bc_kind[2 * xi + 1], bc_gamma[2 * xi + 1], inv_h0[xi], qc, qc + 3, a[xi], irhoJ, lamJ,
-                     muJ, rv, e);
+      face_penalty_at<T>(xi, 1, pos, N, a[xi], qc, irhoJ, lamJ, muJ, bc_kind, bc_gamma, inv_h0, rv, e, ifc, member);
   }
 }
 
@@ -408,7 +502,7 @@ __device__ __forceinline__ void raw_operator_at(const T* __restrict__ q, const T
                                                 const T* __restrict__ mat, const Dims& d, long long n0,
                                                 const int pos[3], const T inv_h[3], const T inv_h0[3],
                                                 const int bc_kind[6], const T bc_gamma[6], T rv[3], T e[6],
-                                                T qc[9]) {
+                                                T qc[9], const IfaceArgs<T>* ifc = nullptr, int member = 0) {
   const long long fs = d.fs;
   const int N[3] = {d.nq, d.nr, d.ns};
   const long long stride[3] = {1, d.ldq, d.plane};
@@ -429,7 +523,8 @@ __device__ __forceinline__ void raw_operator_at(const T* __restrict__ q, const T
     for (int xi = 0; xi < 3; ++xi)
 #pragma unroll
       for (int c = 0; c < 3; ++c) a[xi][c] = met[(3 * xi + c) * fs + n0];
-    add_face_penalties(pos, N, a, qc, mat[n0], mat[fs + n0], mat[2 * fs + n0], bc_kind, bc_gamma, inv_h0, rv, e);
+    add_face_penalties(pos, N, a, qc, mat[n0], mat[fs + n0], mat[2 * fs + n0], bc_kind, bc_gamma, inv_h0, rv, e,
+                       ifc, member);
   }
 }
 

@@ -11,24 +11,24 @@ namespace sbp {
 // Section 2.2: J and a[xi][eta] = J xi_eta from node coordinates, FP64, one thread per node
 // (metrics_at in common.cuh).
 template <int O>
-__global__ void metrics_kernel(const double* __restrict__ xyz, double* __restrict__ jmet, Dims d,
+__global__ void metrics_kernel(const double* __restrict__ xyz, double* __restrict__ jmet, Dims d, SlabS sl,
                                unsigned* status) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)d.nq * d.nr * d.ns) return;
-  if (!metrics_at<O>(xyz, jmet, d, t)) atomicOr(status, 2u);
+  if (t >= (long long)d.nq * d.nr * (d.ns - sl.ghost_lo - sl.ghost_hi)) return;
+  if (!metrics_at<O>(xyz, jmet, d, t, sl)) atomicOr(status, 2u);
 }
 
 cudaError_t launch_metrics(const double* xyz, double* jmet, const Dims& d, int order, unsigned* status,
-                           cudaStream_t st) {
-  const long long total = (long long)d.nq * d.nr * d.ns;
+                           cudaStream_t st, SlabS sl) {
+  const long long total = (long long)d.nq * d.nr * (d.ns - sl.ghost_lo - sl.ghost_hi);
   const unsigned blocks = (unsigned)((total + 255) / 256);
   switch (order) {
-    case 2: metrics_kernel<2><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
-    case 4: metrics_kernel<4><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
-    case 6: metrics_kernel<6><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
-    case 3: metrics_kernel<3><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
-    case 5: metrics_kernel<5><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
-    case 7: metrics_kernel<7><<<blocks, 256, 0, st>>>(xyz, jmet, d, status); break;
+    case 2: metrics_kernel<2><<<blocks, 256, 0, st>>>(xyz, jmet, d, sl, status); break;
+    case 4: metrics_kernel<4><<<blocks, 256, 0, st>>>(xyz, jmet, d, sl, status); break;
+    case 6: metrics_kernel<6><<<blocks, 256, 0, st>>>(xyz, jmet, d, sl, status); break;
+    case 3: metrics_kernel<3><<<blocks, 256, 0, st>>>(xyz, jmet, d, sl, status); break;
+    case 5: metrics_kernel<5><<<blocks, 256, 0, st>>>(xyz, jmet, d, sl, status); break;
+    case 7: metrics_kernel<7><<<blocks, 256, 0, st>>>(xyz, jmet, d, sl, status); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -208,6 +208,58 @@ template cudaError_t launch_source<double>(double*, double*, const Dims&, const 
                                            double, double, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
+// Interface trace of face `face` (xi = face / 2): at every node of the face and member b,
+// trace[(8 b + c) n_face + face_index] = v (c = 0..2), T = sigma n (3..5) with n = a_xi / |a_xi|,
+// Z_p, Z_s (6, 7) from the stored coefficients, for the other block's interface penalty.
+template <typename T>
+__global__ void interface_trace_kernel(const T* __restrict__ q, const T* __restrict__ met, const T* __restrict__ mat,
+                                       Dims d, int face, int nb, long long bstride, T* __restrict__ trace) {
+  const int xi = face / 2, side = face % 2;
+  const long long nf = xi == 0 ? (long long)d.nr * d.ns : xi == 1 ? (long long)d.nq * d.ns : (long long)d.nq * d.nr;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nf * nb) return;
+  const int b = (int)(t / nf);
+  const long long f = t % nf;
+  const int na = xi == 0 ? d.nr : d.nq;   // the face's first (fastest) axis
+  const int u = (int)(f % na), w = (int)(f / na);
+  const int i = xi == 0 ? (side ? d.nq - 1 : 0) : u;
+  const int j = xi == 0 ? u : xi == 1 ? (side ? d.nr - 1 : 0) : w;
+  const int k = xi == 2 ? (side ? d.ns - 1 : 0) : w;
+  const long long n0 = (long long)k * d.plane + (long long)j * d.ldq + i;
+  const long long fs = d.fs;
+  const T* qb = q + (long long)b * bstride;
+  const T a[3] = {met[(3 * xi) * fs + n0], met[(3 * xi + 1) * fs + n0], met[(3 * xi + 2) * fs + n0]};
+  const T ian = T(1) / sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+  const T n[3] = {a[0] * ian, a[1] * ian, a[2] * ian};
+  T sg[6], Tr[3];
+#pragma unroll
+  for (int c = 0; c < 6; ++c) sg[c] = qb[(3 + c) * fs + n0];
+  flux(n, sg, Tr);
+  const T irhoJ = mat[n0], lamJ = mat[fs + n0], muJ = mat[2 * fs + n0];
+  T* out = trace + (long long)b * 8 * nf + f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[c * nf] = qb[c * fs + n0];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[(3 + c) * nf] = Tr[c];
+  out[6 * nf] = sqrt((lamJ + T(2) * muJ) / irhoJ);
+  out[7 * nf] = sqrt(muJ / irhoJ);
+}
+
+template <typename T>
+cudaError_t launch_interface_trace(const T* q, const T* met, const T* mat, const Dims& d, int face, int nb,
+                                   long long bstride, T* trace, cudaStream_t st) {
+  const int xi = face / 2;
+  const long long nf = xi == 0 ? (long long)d.nr * d.ns : xi == 1 ? (long long)d.nq * d.ns : (long long)d.nq * d.nr;
+  const long long total = nf * nb;
+  interface_trace_kernel<T><<<(unsigned)((total + 255) / 256), 256, 0, st>>>(q, met, mat, d, face, nb, bstride, trace);
+  return cudaGetLastError();
+}
+template cudaError_t launch_interface_trace<float>(const float*, const float*, const float*, const Dims&, int, int,
+                                                   long long, float*, cudaStream_t);
+template cudaError_t launch_interface_trace<double>(const double*, const double*, const double*, const Dims&, int,
+                                                    int, long long, double*, cudaStream_t);
+
+// ---------------------------------------------------------------------------
 // Receivers: trace[b][r][c][step] = v_c of state b at the receiver node.
 template <typename T>
 __global__ void receivers_kernel(const T* __restrict__ q, Dims d, const int32_t* __restrict__ off, int n, int nb,
@@ -300,5 +352,44 @@ template cudaError_t launch_receivers<float>(const float*, const Dims&, const in
                                              int, long long, cudaStream_t);
 template cudaError_t launch_receivers<double>(const double*, const Dims&, const int32_t*, int, int, long long,
                                               double*, int, long long, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// FP64 arithmetic rate probe: 8 independent fused multiply-add chains per thread (enough to
+// cover the FP64 pipe's latency), no memory traffic; the result is written only if it takes an
+// impossible value, so that the chains are not removed.
+__global__ void __launch_bounds__(256) fma_probe_kernel(int iters, double seed, double* sink) {
+  double a[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) a[c] = seed + 1e-3 * (threadIdx.x + 7 * c);
+  const double b = 0.9999999, d = 1e-9;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) a[c] = fma(a[c], b, d);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) s += a[c];
+  if (s == -1.0) sink[blockIdx.x] = s;
+}
+
+cudaError_t probe_fp64_fma(int iters, int blocks, double* sink, float* ms, cudaStream_t st) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    fma_probe_kernel<<<blocks, 256, 0, st>>>(iters / 10 + 1, 1.0, sink);  // warm-up
+    e = cudaEventRecord(e0, st);
+  }
+  if (e == cudaSuccess) {
+    fma_probe_kernel<<<blocks, 256, 0, st>>>(iters, 1.0, sink);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return e;
+}
 
 }  // namespace sbp

@@ -31,7 +31,8 @@ __global__ void __launch_bounds__(256) stage_general_kernel(StageArgs<T> A, BoxL
   const long long n0 = (long long)k * d.plane + (long long)j * d.ldq + i;
   const int pos[3] = {i, j, k};
   T rv[3], e[6], qc[9];
-  raw_operator_at<T, O>(A.q, A.met, A.mat, d, n0, pos, A.inv_h, A.inv_h0, A.bc_kind, A.bc_gamma, rv, e, qc);
+  raw_operator_at<T, O>(A.q, A.met, A.mat, d, n0, pos, A.inv_h, A.inv_h0, A.bc_kind, A.bc_gamma, rv, e, qc, &A.ifc,
+                        (int)blockIdx.y);
   const T irhoJ = A.mat[n0], lamJ = A.mat[d.fs + n0], muJ = A.mat[2 * d.fs + n0];
   T dd[9];
   apply_P(rv, e, irhoJ, lamJ, muJ, dd);

@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
                            {st.ar[0][HX + ty][tx], st.ar[1][HX + ty][tx], st.ar[2][HX + ty][tx]},
                            {st.as[0][ty][tx], st.as[1][ty][tx], st.as[2][ty][tx]}};
         add_face_penalties(pos, N, a, qc, st.mat[0][ty][tx], st.mat[1][ty][tx], st.mat[2][ty][tx], A.bc_kind,
-                           A.bc_gamma, A.inv_h0, rv, e);
+                           A.bc_gamma, A.inv_h0, rv, e, &A.ifc, member);
       }
       T dd[9];
       apply_P(rv, e, st.mat[0][ty][tx], st.mat[1][ty][tx], st.mat[2][ty][tx], dd);

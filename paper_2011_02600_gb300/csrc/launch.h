@@ -40,7 +40,7 @@ cudaError_t launch_adjoint_tiled(const StageArgs<T>& A, int order, int pass, con
 cudaError_t launch_wait_selftest(unsigned polls, unsigned* status, cudaStream_t st);
 
 cudaError_t launch_metrics(const double* xyz, double* jmet, const Dims& d, int order, unsigned* status,
-                           cudaStream_t st);
+                           cudaStream_t st, SlabS sl = SlabS{});
 
 template <typename T>
 cudaError_t launch_material(const double* jmet, const double* rlm, T* met, T* mat, const Dims& d,
@@ -60,6 +60,16 @@ cudaError_t launch_source(T* qout, T* dq, const Dims& d, const long long* off, c
 template <typename T>
 cudaError_t launch_receivers(const T* q, const Dims& d, const int32_t* off, int n, int nb, long long bstride,
                              T* traces, int n_t, long long step, cudaStream_t st);
+
+// The interface trace of one face (v, sigma n, Z_p, Z_s at each face node and member), 8 nb face
+// arrays in trace (see interface_trace_kernel).
+template <typename T>
+cudaError_t launch_interface_trace(const T* q, const T* met, const T* mat, const Dims& d, int face, int nb,
+                                   long long bstride, T* trace, cudaStream_t st);
+
+// FP64 fused multiply-add rate probe: one warm-up and one timed launch of `blocks` x 256 threads,
+// 16 iters flops per thread; the timed launch's milliseconds in *ms.
+cudaError_t probe_fp64_fma(int iters, int blocks, double* sink, float* ms, cudaStream_t st);
 
 // Nearest node to each of n target points (3 FP64 values each, device) among the nodes of
 // face `face` (0..5) or of the whole grid (face < 0), from the node coordinates xyz (3 FP64

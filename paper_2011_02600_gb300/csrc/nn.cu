@@ -12,6 +12,7 @@
 // mma.sync.m16n8k16 (BF16 in, FP32 accumulate) through ldmatrix.
 #include <cuda_bf16.h>
 #include <algorithm>
+#include <mutex>
 #include <stdint.h>
 
 #include "nn_elem.cuh"
@@ -544,9 +545,20 @@ int sbp_nn_gemm(int32_t M, int32_t N, int32_t K, const void* A, int64_t lda, int
                  : cudaMemset2DAsync(C, sizeof(float) * (size_t)ldc, 0, sizeof(float) * (size_t)N, (size_t)M, st);
     if (e != cudaSuccess) return nn_status(e);
   }
-  // per launch: the attribute belongs to the current device
-  e = cudaFuncSetAttribute(gemm_bf16_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PSMEM);
-  if (e != cudaSuccess) return nn_status(e);
+  // the attribute belongs to the device: set once per device
+  {
+    static std::mutex m;
+    static bool set[64] = {};
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return nn_status(e);
+    std::lock_guard<std::mutex> lock(m);
+    if (dev >= 64 || !set[dev]) {
+      e = cudaFuncSetAttribute(gemm_bf16_pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, PSMEM);
+      if (e != cudaSuccess) return nn_status(e);
+      if (dev < 64) set[dev] = true;
+    }
+  }
   gemm_bf16_pipe_kernel<<<grid, 256, PSMEM, st>>>(M, N, K, k_per, (const __nv_bfloat16*)A, lda, transA,
                                                   (const __nv_bfloat16*)B, ldb, transB, C, ldc, c_bf16, bias, relu,
                                                   beta);

@@ -3,19 +3,21 @@
 // with the conventions of sbp_nn_gemm (row-major storage; op(A) = A stored M x K, or A^T with A
 // stored K x M; op(B) = B stored K x N, or B^T with B stored N x K).
 //
-// One CTA of 128 threads computes a 128 x 256 tile of C:
-//  * thread 0 streams 64-deep K slices of both operands into a ring of shared-memory stages
-//    with 2D TMA loads (128-byte swizzle), in each operand's own orientation: K-major when k is
-//    the contiguous index, MN-major otherwise; an mbarrier per stage counts the bytes;
-//  * thread 32 issues tcgen05.mma (kind::f16, BF16 operands from shared memory through matrix
-//    descriptors, FP32 accumulator of 128 lanes x 256 columns in tensor memory), four per slice
-//    (K = 16 each), and frees each stage with tcgen05.commit on the stage's "empty" mbarrier;
-//  * after the last slice a commit on the accumulator barrier releases the epilogue: each warp
-//    reads its 32 accumulator rows with tcgen05.ld, transposes them through shared memory so
-//    that a store instruction covers 32 consecutive columns of one row, adds the bias, applies
-//    ReLU and stores FP32 or BF16 (FP32 atomics when K is split over CTAs).
+// A persistent kernel, one CTA of six warps per SM, takes 128 x 256 tiles of C in turn:
+//  * warp 0 (one thread) streams 64-deep K slices of both operands into a ring of four
+//    shared-memory stages with 2D TMA loads (128-byte swizzle), in each operand's own
+//    orientation: K-major when k is the contiguous index, MN-major otherwise; an mbarrier per
+//    stage counts the bytes, another frees the stage;
+//  * warp 1 (one thread) issues tcgen05.mma (kind::f16, BF16 operands from shared memory
+//    through matrix descriptors), four per slice (K = 16 each), into one of two FP32
+//    accumulators of 128 lanes x 256 columns in tensor memory (all 512 columns), and frees each
+//    stage with tcgen05.commit; a commit on the accumulator's barrier hands it to the epilogue;
+//  * warps 2-5 drain the other accumulator meanwhile: tcgen05.ld of their 32 lanes, a transpose
+//    through shared memory so that each store covers 32 consecutive columns of one row, bias,
+//    ReLU, FP32 or BF16 stores (FP32 atomics when K is split over work items), then an arrival
+//    that gives the accumulator back to the MMA warp.
 // Every mbarrier wait is bounded: on a timeout the CTA records it in a device status word
-// (sbp_nn_status), skips its stores, and still frees its tensor memory before it exits.
+// (sbp_nn_status), its roles stop, and it still waits for its MMAs and frees its tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -29,12 +31,15 @@
 
 namespace sbp_tc {
 
-constexpr int BM = 128, BN = 256, BK = 64, STAGES = 2, THREADS = 128;
+constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
+constexpr int WARPS = 6, THREADS = 32 * WARPS;     // producer, MMA issuer, four epilogue warps
 constexpr int A_BYTES = BM * BK * 2;              // 16 KB
 constexpr int B_BYTES = BN * BK * 2;              // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;    // 48 KB, a multiple of the 1 KB swizzle atom
-constexpr int TMEM_COLS = BN;                     // FP32 accumulator: one column per n
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /* alignment slack */ + 256 /* barriers */;
+constexpr int ACC_COLS = BN;                      // FP32 accumulator: one column per n
+constexpr int TMEM_COLS = 2 * ACC_COLS;           // two accumulators: the whole tensor memory
+constexpr int EPI_TILE = 32 * 33;                 // floats of one epilogue warp's transpose tile
+constexpr int SMEM_BYTES = 1024 /* alignment slack */ + STAGES * STAGE_BYTES + 4 * EPI_TILE * 4 + 256;
 constexpr unsigned kWaitLimit = 1u << 24;         // polls of about 64 ns: roughly a second
 
 __device__ unsigned g_tc_status;  // bit 1: a wait timed out
@@ -68,6 +73,14 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sbp::smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool wait(uint64_t* bar, unsigned parity) {
+  return sbp::mbar_wait_bounded(reinterpret_cast<unsigned long long*>(bar), parity, kWaitLimit);
+}
+
 __device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -87,32 +100,52 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// A_MN / B_MN: operand stored MN-major (the m or n index contiguous) rather than K-major.
+// Work item w (of tm x tn x splits): m tiles fastest, so that the CTAs running at the same time
+// share their B tiles (the larger operand) through L2.
+struct Item {
+  int m0, n0, kb, ke;
+};
+__device__ __forceinline__ Item item(int w, int tm, int tn, int k_per, int K) {
+  Item it;
+  const int per = tm * tn;
+  const int z = w / per, r = w % per;
+  it.m0 = (r % tm) * BM;
+  it.n0 = (r / tm) * BN;
+  it.kb = z * k_per;
+  it.ke = min(K, it.kb + k_per);
+  return it;
+}
+
+// Persistent kernel: CTA b takes work items b, b + gridDim.x, ...  A_MN / B_MN: operand stored
+// MN-major (the m or n index contiguous) rather than K-major.
 template <bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(THREADS, 1)
-    gemm_tc_kernel(const __grid_constant__ Maps maps, int M, int N, int K, int k_per, void* C, long long ldc,
-                   int c_bf16, const float* __restrict__ bias, int relu, float beta) {
+    gemm_tc_kernel(const __grid_constant__ Maps maps, int M, int N, int K, int k_per, int tm, int tn, int items,
+                   void* C, long long ldc, int c_bf16, const float* __restrict__ bias, int relu, float beta) {
   extern __shared__ unsigned char smem_raw[];
-  // stages at the first 1 KB boundary (the swizzle pattern repeats every 1 KB), barriers after
+  // stages at the first 1 KB boundary (the swizzle pattern repeats every 1 KB), then the
+  // epilogue warps' transpose tiles, then the barriers
   unsigned char* base = smem_raw + ((1024u - (sbp::smem_u32(smem_raw) & 1023u)) & 1023u);
-  uint64_t* full = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+  float* epi = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);
+  uint64_t* full = reinterpret_cast<uint64_t*>(epi + 4 * EPI_TILE);
   uint64_t* empty = full + STAGES;
-  uint64_t* accum = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accum + 1);
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* done = acc_empty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   int* fail = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-  const int kb = blockIdx.z * k_per;
-  const int ke = min(K, kb + k_per);
-  const int nk = (ke - kb + BK - 1) / BK;
-
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       sbp::mbar_init(reinterpret_cast<unsigned long long*>(&full[s]), 1);
       sbp::mbar_init(reinterpret_cast<unsigned long long*>(&empty[s]), 1);
     }
-    sbp::mbar_init(reinterpret_cast<unsigned long long*>(accum), 1);
+    for (int b = 0; b < 2; ++b) {
+      sbp::mbar_init(reinterpret_cast<unsigned long long*>(&acc_full[b]), 1);
+      sbp::mbar_init(reinterpret_cast<unsigned long long*>(&acc_empty[b]), 128);  // the epilogue threads
+    }
+    sbp::mbar_init(reinterpret_cast<unsigned long long*>(done), 1);
     *fail = 0;
     sbp::fence_mbar_init();
   }
@@ -127,102 +160,135 @@ __global__ void __launch_bounds__(THREADS, 1)
   fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
-  if (threadIdx.x == 0) {
-    // producer: TMA loads of the K slices
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % STAGES, use = kt / STAGES;
-      if (use > 0 && !sbp::mbar_wait_bounded(reinterpret_cast<unsigned long long*>(&empty[s]), (use - 1) & 1,
-                                            kWaitLimit)) {
-        atomicOr(fail, 1);
-        break;
-      }
-      unsigned char* st = base + s * STAGE_BYTES;
-      sbp::mbar_expect_tx(reinterpret_cast<unsigned long long*>(&full[s]), STAGE_BYTES);
-      const int k0 = kb + kt * BK;
-      if (A_MN) {
-        tma_load_2d(st, &maps.a, m0, k0, &full[s]);
-        tma_load_2d(st + sbp_umma::kMnBoxBytes, &maps.a, m0 + 64, k0, &full[s]);
-      } else {
-        tma_load_2d(st, &maps.a, k0, m0, &full[s]);
-      }
-      unsigned char* sb = st + A_BYTES;
-      if (B_MN) {
-#pragma unroll
-        for (int c = 0; c < BN / 64; ++c) tma_load_2d(sb + c * sbp_umma::kMnBoxBytes, &maps.b, n0 + 64 * c, k0, &full[s]);
-      } else {
-        tma_load_2d(sb, &maps.b, k0, n0, &full[s]);
-      }
-    }
-  } else if (threadIdx.x == 32) {
-    // MMA issuer
-    constexpr uint32_t idesc = sbp_umma::instr_desc_bf16_f32(BM, BN, A_MN, B_MN);
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % STAGES, use = kt / STAGES;
-      if (!sbp::mbar_wait_bounded(reinterpret_cast<unsigned long long*>(&full[s]), use & 1, kWaitLimit)) {
-        atomicOr(fail, 1);
-        break;
-      }
-      fence_after_sync();
-      const uint32_t sa = sbp::smem_u32(base + s * STAGE_BYTES);
-      const uint32_t sb = sa + A_BYTES;
-#pragma unroll
-      for (int k16 = 0; k16 < BK / 16; ++k16) {
-        const uint64_t ad = A_MN ? sbp_umma::mnmajor_desc(sa, k16) : sbp_umma::kmajor_desc(sa, k16);
-        const uint64_t bd = B_MN ? sbp_umma::mnmajor_desc(sb, k16) : sbp_umma::kmajor_desc(sb, k16);
-        mma_bf16(tmem, ad, bd, idesc, (kt > 0 || k16 > 0) ? 1u : 0u);
-      }
-      mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
-    }
-    mma_commit(accum);  // arrives when every MMA issued above has completed
-  }
-
-  // epilogue: all four warps, 32 accumulator rows each
-  if (!sbp::mbar_wait_bounded(reinterpret_cast<unsigned long long*>(accum), 0, kWaitLimit)) atomicOr(fail, 1);
-  fence_after_sync();
-  __syncthreads();
-  const bool ok = *fail == 0 && nk > 0;
-  if (!ok && threadIdx.x == 0 && *fail) atomicOr(&g_tc_status, 1u);
-  if (ok) {
-    // Each warp moves its 32 accumulator rows out 32 columns at a time: tcgen05.ld gives one row
-    // per thread; the warp transposes the 32 x 32 block through its own padded shared-memory
-    // tile (the stage buffers are free once the accumulator barrier has passed) and then writes
-    // one row per instruction, 32 consecutive columns across the lanes (128-byte segments).
-    float* tile = reinterpret_cast<float*>(base) + warp * (32 * 33);
-    const bool split = gridDim.z > 1;
-#pragma unroll 1
-    for (int c = 0; c < BN / 32; ++c) {
-      const int nb = n0 + 32 * c;
-      if (nb >= N) break;  // uniform over the CTA
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(32 * c), v);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = v[j];
-      __syncwarp();
-      const int n = nb + lane;
-#pragma unroll 4
-      for (int r = 0; r < 32; ++r) {
-        const int m = m0 + warp * 32 + r;
-        if (m >= M) break;  // uniform over the warp
-        float x = tile[r * 33 + lane] + ((bias && blockIdx.z == 0) ? bias[m] : 0.f);
-        if (n < N) {
-          const long long idx = (long long)m * ldc + n;
-          if (split) {
-            atomicAdd((float*)C + idx, x);
-          } else if (c_bf16) {
-            if (relu) x = fmaxf(x, 0.f);
-            ((__nv_bfloat16*)C)[idx] = __float2bfloat16(x);
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: TMA loads of every K slice of every item, through the ring of stages
+      int it = 0;
+      for (int w = blockIdx.x; w < items && !*(volatile int*)fail; w += gridDim.x) {
+        const Item I = item(w, tm, tn, k_per, K);
+        const int nk = (I.ke - I.kb + BK - 1) / BK;
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = it % STAGES, use = it / STAGES;
+          if (use > 0 && !wait(&empty[s], (use - 1) & 1)) {
+            atomicOr(fail, 1);
+            break;
+          }
+          unsigned char* st = base + s * STAGE_BYTES;
+          sbp::mbar_expect_tx(reinterpret_cast<unsigned long long*>(&full[s]), STAGE_BYTES);
+          const int k0 = I.kb + kt * BK;
+          if (A_MN) {
+            tma_load_2d(st, &maps.a, I.m0, k0, &full[s]);
+            tma_load_2d(st + sbp_umma::kMnBoxBytes, &maps.a, I.m0 + 64, k0, &full[s]);
           } else {
-            if (beta != 0.f) x += beta * ((const float*)C)[idx];
-            if (relu) x = fmaxf(x, 0.f);
-            ((float*)C)[idx] = x;
+            tma_load_2d(st, &maps.a, k0, I.m0, &full[s]);
+          }
+          unsigned char* sb = st + A_BYTES;
+          if (B_MN) {
+#pragma unroll
+            for (int c = 0; c < BN / 64; ++c)
+              tma_load_2d(sb + c * sbp_umma::kMnBoxBytes, &maps.b, I.n0 + 64 * c, k0, &full[s]);
+          } else {
+            tma_load_2d(sb, &maps.b, k0, I.n0, &full[s]);
           }
         }
       }
-      __syncwarp();
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: accumulator t & 1 of the two in tensor memory for the t-th item
+      constexpr uint32_t idesc = sbp_umma::instr_desc_bf16_f32(BM, BN, A_MN, B_MN);
+      int it = 0, t = 0;
+      for (int w = blockIdx.x; w < items && !*(volatile int*)fail; w += gridDim.x, ++t) {
+        const Item I = item(w, tm, tn, k_per, K);
+        const int nk = (I.ke - I.kb + BK - 1) / BK;
+        const int buf = t & 1, ause = t >> 1;
+        if (ause > 0 && !wait(&acc_empty[buf], (ause - 1) & 1)) {
+          atomicOr(fail, 1);
+          break;
+        }
+        fence_after_sync();
+        const uint32_t acc = tmem + (uint32_t)(buf * ACC_COLS);
+        bool ok = true;
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = it % STAGES, use = it / STAGES;
+          if (!wait(&full[s], use & 1)) {
+            atomicOr(fail, 1);
+            ok = false;
+            break;
+          }
+          fence_after_sync();
+          const uint32_t sa = sbp::smem_u32(base + s * STAGE_BYTES);
+          const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+          for (int k16 = 0; k16 < BK / 16; ++k16) {
+            const uint64_t ad = A_MN ? sbp_umma::mnmajor_desc(sa, k16) : sbp_umma::kmajor_desc(sa, k16);
+            const uint64_t bd = B_MN ? sbp_umma::mnmajor_desc(sb, k16) : sbp_umma::kmajor_desc(sb, k16);
+            mma_bf16(acc, ad, bd, idesc, (kt > 0 || k16 > 0) ? 1u : 0u);
+          }
+          mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+        }
+        if (!ok) break;
+        mma_commit(&acc_full[buf]);  // the accumulator is complete once every MMA above is
+      }
+      // before the tensor memory is freed, every MMA issued here has to have completed
+      mma_commit(done);
+      if (!wait(done, 0)) atomicOr(fail, 1);
+    }
+  } else {
+    // epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31, i.e. those rows of the tile
+    const int lg = warp & 3;
+    float* tile = epi + (warp - 2) * EPI_TILE;
+    const bool split = k_per < K;
+    int t = 0;
+    for (int w = blockIdx.x; w < items; w += gridDim.x, ++t) {
+      const Item I = item(w, tm, tn, k_per, K);
+      const int buf = t & 1, use = t >> 1;
+      const bool got = wait(&acc_full[buf], use & 1);
+      if (!__all_sync(0xffffffffu, got)) {
+        if (lane == 0) atomicOr(fail, 1);
+        break;
+      }
+      fence_after_sync();
+      const uint32_t acc = tmem + (uint32_t)(buf * ACC_COLS) + ((uint32_t)(lg * 32) << 16);
+#pragma unroll 1
+      for (int c = 0; c < BN / 32; ++c) {
+        const int nb = I.n0 + 32 * c;
+        if (nb >= N) break;  // uniform over the warp
+        float v[32];
+        tmem_ld32(acc + (uint32_t)(32 * c), v);
+        // transpose through the warp's tile so that a store covers 32 consecutive columns
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = v[j];
+        __syncwarp();
+        const int n = nb + lane;
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+          const int m = I.m0 + lg * 32 + r;
+          if (m >= M) break;  // uniform over the warp
+          float x = tile[r * 33 + lane] + ((bias && I.kb == 0) ? bias[m] : 0.f);
+          if (n < N) {
+            const long long idx = (long long)m * ldc + n;
+            if (split) {
+              atomicAdd((float*)C + idx, x);
+            } else if (c_bf16) {
+              if (relu) x = fmaxf(x, 0.f);
+              ((__nv_bfloat16*)C)[idx] = __float2bfloat16(x);
+            } else {
+              if (beta != 0.f) x += beta * ((const float*)C)[idx];
+              if (relu) x = fmaxf(x, 0.f);
+              ((float*)C)[idx] = x;
+            }
+          }
+        }
+        __syncwarp();
+      }
+      fence_before_sync();
+      mbar_arrive(&acc_empty[buf]);  // this thread has read its part of the accumulator
     }
   }
   fence_before_sync();
   __syncthreads();
+  if (threadIdx.x == 0 && *(volatile int*)fail) atomicOr(&g_tc_status, 1u);
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
 
@@ -239,10 +305,51 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
   return fn;
 }
 
+// Encoded tensor maps, reused for repeated calls on the same operands (a network's GEMMs see
+// the same buffers every iteration): a small table with round-robin replacement.
+struct MapKey {
+  const void* base;
+  long long rows, cols, ld;
+  int box_cols, box_rows, dev;
+};
+struct MapEntry {
+  MapKey key;
+  CUtensorMap map;
+  bool used = false;
+};
+constexpr int kMapCache = 64;
+std::mutex g_map_mutex;
+MapEntry g_maps[kMapCache];
+int g_map_next = 0;
+
+bool encode_uncached(CUtensorMap* m, const void* base, long long rows, long long cols, long long ld, int box_cols,
+                     int box_rows);
+
 // 2D tensor map of a row-major bf16 matrix with `rows` rows of `cols` elements (row pitch ld),
 // box of box_cols x box_rows, 128-byte swizzle, zero fill outside the matrix.
 bool encode(CUtensorMap* m, const void* base, long long rows, long long cols, long long ld, int box_cols,
             int box_rows) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  const MapKey k{base, rows, cols, ld, box_cols, box_rows, dev};
+  std::lock_guard<std::mutex> lock(g_map_mutex);
+  for (auto& e : g_maps)
+    if (e.used && e.key.base == k.base && e.key.rows == k.rows && e.key.cols == k.cols && e.key.ld == k.ld &&
+        e.key.box_cols == k.box_cols && e.key.box_rows == k.box_rows && e.key.dev == k.dev) {
+      *m = e.map;
+      return true;
+    }
+  if (!encode_uncached(m, base, rows, cols, ld, box_cols, box_rows)) return false;
+  MapEntry& slot = g_maps[g_map_next];
+  g_map_next = (g_map_next + 1) % kMapCache;
+  slot.key = k;
+  slot.map = *m;
+  slot.used = true;
+  return true;
+}
+
+bool encode_uncached(CUtensorMap* m, const void* base, long long rows, long long cols, long long ld, int box_cols,
+                     int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
   if (!enc) return false;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
@@ -270,36 +377,49 @@ cudaError_t launch_gemm_tc(int M, int N, int K, const void* A, long long lda, in
   // B: op(B) = B (stored K x N, MN-major) or B^T (B stored N x K, K-major)
   const bool okB = tb ? encode(&maps.b, B, N, K, ldb, BK, BN) : encode(&maps.b, B, K, N, ldb, 64, BK);
   if (!okA || !okB) return cudaErrorInvalidValue;
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, 1);
-  if (grid.y > 65535) return cudaErrorInvalidValue;
+  const int tn = (N + BN - 1) / BN, tm = (M + BM - 1) / BM;
   int k_per = K;
-  const long long tiles = (long long)grid.x * grid.y;
-  const long long slots = 2LL * sms;  // two CTAs per SM (smem and tensor memory allow two)
-  if (!c_bf16 && !relu && beta == 0.f && tiles < slots && K >= 8 * BK) {
-    long long splits = (slots + tiles - 1) / tiles;
+  const long long tiles = (long long)tm * tn;
+  // split K when the output tiles alone would leave SMs idle (FP32 output, plain sum)
+  if (!c_bf16 && !relu && beta == 0.f && tiles < sms && K >= 8 * BK) {
+    long long splits = (sms + tiles - 1) / tiles;
     splits = splits < K / (4 * BK) ? splits : K / (4 * BK);
-    if (splits > 1) {
-      k_per = (int)(((K + splits - 1) / splits + BK - 1) / BK * BK);
-      grid.z = (unsigned)((K + k_per - 1) / k_per);
-    }
+    if (splits > 1) k_per = (int)(((K + splits - 1) / splits + BK - 1) / BK * BK);
   }
+  const long long items = tiles * ((K + k_per - 1) / k_per);
+  if (items > (1LL << 30)) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
-  if (grid.z > 1) {
+  if (k_per < K) {
     e = ldc == N ? cudaMemsetAsync(C, 0, sizeof(float) * (size_t)M * N, st)
                  : cudaMemset2DAsync(C, sizeof(float) * (size_t)ldc, 0, sizeof(float) * (size_t)N, (size_t)M, st);
     if (e != cudaSuccess) return e;
   }
-  auto launch = [&](auto kern) -> cudaError_t {
-    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (r != cudaSuccess) return r;
-    kern<<<grid, THREADS, SMEM_BYTES, st>>>(maps, M, N, K, k_per, C, ldc, c_bf16, bias, relu, beta);
+  // persistent: one CTA per SM (its shared memory and tensor memory fill the SM)
+  const unsigned grid = (unsigned)(items < sms ? items : sms);
+  // the shared-memory attribute belongs to the device: set once per device and kernel variant
+  static std::mutex attr_mutex;
+  static bool attr_set[64][4] = {};
+  int dev = 0;
+  e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  auto launch = [&](auto kern, int variant) -> cudaError_t {
+    {
+      std::lock_guard<std::mutex> lock(attr_mutex);
+      if (dev >= 64 || !attr_set[dev][variant]) {
+        cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (r != cudaSuccess) return r;
+        if (dev < 64) attr_set[dev][variant] = true;
+      }
+    }
+    kern<<<grid, THREADS, SMEM_BYTES, st>>>(maps, M, N, K, k_per, tm, tn, (int)items, C, ldc, c_bf16, bias, relu,
+                                           beta);
     return cudaGetLastError();
   };
   const bool a_mn = ta != 0, b_mn = tb == 0;
-  if (a_mn && b_mn) return launch(gemm_tc_kernel<true, true>);
-  if (a_mn) return launch(gemm_tc_kernel<true, false>);
-  if (b_mn) return launch(gemm_tc_kernel<false, true>);
-  return launch(gemm_tc_kernel<false, false>);
+  if (a_mn && b_mn) return launch(gemm_tc_kernel<true, true>, 3);
+  if (a_mn) return launch(gemm_tc_kernel<true, false>, 2);
+  if (b_mn) return launch(gemm_tc_kernel<false, true>, 1);
+  return launch(gemm_tc_kernel<false, false>, 0);
 }
 
 // Read and clear the tcgen05 GEMM's status word (synchronises the device).

@@ -150,18 +150,21 @@ class SlabSolver:
         self.g = reach(order, operator)
         self.s = ElasticSolver((nq, nr, slab.planes), order, precision, bc, device=device, operator=operator,
                                slab=(ns, slab.lo, slab.ghost_lo, slab.ghost_hi))
-        # metrics: computed on a window of the block around the slab, wide enough that the kept
-        # planes see the block's own rows of D_c, then restricted to the slab's planes
-        m = sbp_min_nodes_py(order, operator)
-        w0, w1 = max(0, slab.lo - m), min(ns, slab.hi + m)
-        win = ElasticSolver((nq, nr, w1 - w0), order, 64, bc, device=device, operator=operator)
+        # metrics at every local plane, ghost planes included: sbp_metrics on a window slab whose
+        # owned planes are this slab's local planes, with reach more planes of coordinates on each
+        # inner side (the rows of D_c are the block's)
+        g = self.g
+        glo, ghi = (g if slab.lo > 0 else 0), (g if slab.hi < ns else 0)
+        w0, w1 = slab.lo - glo, slab.hi + ghi
+        win = ElasticSolver((nq, nr, w1 - w0), order, 64, bc, device=device, operator=operator,
+                            slab=(ns, w0, glo, ghi) if (glo or ghi) else None)
         xyz = win.to_layout(torch.as_tensor(coords(w0, w1)), torch.float64)
         jwin = win.new_fields(10, torch.float64)
         L.sbp_metrics(win.h, xyz, jwin, _stream())
         if L.sbp_status(win.h, _stream()) & 2:
             raise L.SbpError(6, "non-positive Jacobian")
         jmet = self.s.new_fields(10, torch.float64)
-        self.s.view(jmet, 10).copy_(win.view(jwin, 10)[:, slab.lo - w0:slab.hi - w0])
+        self.s.view(jmet, 10).copy_(win.view(jwin, 10)[:, glo:glo + slab.planes])
         del win, xyz, jwin
         rlm_b = self.s.to_layout(torch.as_tensor(rlm(slab.lo, slab.hi)), torch.float64)
         L.sbp_set_material(self.s.h, jmet, rlm_b, _stream())

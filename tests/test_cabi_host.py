@@ -173,3 +173,15 @@ def test_set_slab_validation(lib):
     L.sbp_set_slab(h, 60, 36, 3, 0)       # high face slab
     L.sbp_set_slab(h, 24, 0, 0, 0)        # the whole block again
     L.sbp_destroy(h)
+
+
+def test_interface_face_validation(lib):
+    """Interface faces (SBP_BC_INTERFACE): accepted by sbp_create_grid; sbp_set_interface only on
+    such a face and a face index in 0..5; the interface trace needs a bound grid with material."""
+    bc = [("free",), ("interface",), ("free",), ("free",), ("free",), ("char", 0.0)]
+    h = L.sbp_create_grid((20, 20, 20), 4, 32, bc)
+    L.sbp_set_interface(h, 1, None)
+    _expect(1, L.sbp_set_interface, h, 0, None)       # not an interface face
+    _expect(1, L.sbp_set_interface, h, 6, None)
+    _expect(5, L.sbp_interface_trace, h, 1, None, 0x1000, None)   # not bound
+    L.sbp_destroy(h)

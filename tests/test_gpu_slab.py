@@ -62,7 +62,8 @@ def test_slab_refusals():
     from paper_2011_02600_gb300 import _lib as L
     nodes = (20, 20, 24)
     s = ElasticSolver(nodes, 4, 64, BC, slab=(60, 10, 3, 3))
-    for fn, args in [(L.sbp_metrics, (s.new_fields(3, torch.float64), s.new_fields(10, torch.float64), 0)),
+    src = dict(ref=(0.5, 0.5, 0.5), moment=[1.0] * 6, stf=0, f0=1.0, t0=1.0)
+    for fn, args in [(L.sbp_set_sources, ([src], s.new_fields(10, torch.float64), 0)),
                      (L.sbp_rhs_adjoint, (s.new_fields(9), s.new_fields(9), s.new_fields(9), 0))]:
         with pytest.raises(L.SbpError) as e:
             fn(s.h, *args)
