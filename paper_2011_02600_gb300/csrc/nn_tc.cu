@@ -3,7 +3,7 @@
 // with the conventions of sbp_nn_gemm (row-major storage; op(A) = A stored M x K, or A^T with A
 // stored K x M; op(B) = B stored K x N, or B^T with B stored N x K).
 //
-// A persistent kernel, one CTA of six warps per SM, takes 128 x 256 tiles of C in turn:
+// A persistent kernel, one CTA of ten warps per SM, takes 128 x 256 tiles of C in turn:
 //  * warp 0 (one thread) streams 64-deep K slices of both operands into a ring of four
 //    shared-memory stages with 2D TMA loads (128-byte swizzle), in each operand's own
 //    orientation: K-major when k is the contiguous index, MN-major otherwise; an mbarrier per
@@ -12,10 +12,12 @@
 //    through matrix descriptors), four per slice (K = 16 each), into one of two FP32
 //    accumulators of 128 lanes x 256 columns in tensor memory (all 512 columns), and frees each
 //    stage with tcgen05.commit; a commit on the accumulator's barrier hands it to the epilogue;
-//  * warps 2-5 drain the other accumulator meanwhile: tcgen05.ld of their 32 lanes, a transpose
-//    through shared memory so that each store covers 32 consecutive columns of one row, bias,
-//    ReLU, FP32 or BF16 stores (FP32 atomics when K is split over work items), then an arrival
-//    that gives the accumulator back to the MMA warp.
+//  * warps 2-9 drain the other accumulator meanwhile, two warps per group of 32 accumulator lanes
+//    (half of the columns each): tcgen05.ld, bias and ReLU in registers, then for FP32 outputs a
+//    32 x 32 box into swizzled shared memory and a TMA store (a TMA reduce-add when K is split
+//    over work items), otherwise a transpose through shared memory and stores that cover 32
+//    consecutive columns of a row; then an arrival that gives the accumulator back to the MMA
+//    warp.
 // Every mbarrier wait is bounded: on a timeout the CTA records it in a device status word
 // (sbp_nn_status), its roles stop, and it still waits for its MMAs and frees its tensor memory.
 #include <cuda.h>
@@ -32,21 +34,43 @@
 namespace sbp_tc {
 
 constexpr int BM = 128, BN = 256, BK = 64, STAGES = 4;
-constexpr int WARPS = 6, THREADS = 32 * WARPS;     // producer, MMA issuer, four epilogue warps
+constexpr int EPI_WARPS = 8;                      // two per accumulator lane group, half the columns each
+constexpr int WARPS = 2 + EPI_WARPS, THREADS = 32 * WARPS;  // producer, MMA issuer, epilogue warps
 constexpr int A_BYTES = BM * BK * 2;              // 16 KB
 constexpr int B_BYTES = BN * BK * 2;              // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;    // 48 KB, a multiple of the 1 KB swizzle atom
 constexpr int ACC_COLS = BN;                      // FP32 accumulator: one column per n
 constexpr int TMEM_COLS = 2 * ACC_COLS;           // two accumulators: the whole tensor memory
-constexpr int EPI_TILE = 32 * 33;                 // floats of one epilogue warp's transpose tile
-constexpr int SMEM_BYTES = 1024 /* alignment slack */ + STAGES * STAGE_BYTES + 4 * EPI_TILE * 4 + 256;
+constexpr int EPI_WARP_BYTES = 4096;              // per epilogue warp: one 32 x 32 FP32 buffer
+constexpr int SMEM_BYTES = 1024 /* alignment slack */ + STAGES * STAGE_BYTES + EPI_WARPS * EPI_WARP_BYTES + 256;
+static_assert(SMEM_BYTES <= 232448, "shared memory per block");
+
+// How the epilogue writes C: through the warp's transpose tile with plain stores (BF16 output or
+// accumulation into C), or from swizzled shared-memory buffers by TMA (store, or reduce-add
+// when K is split over work items).
+enum EpiMode : int { kEpiDirect = 0, kEpiTmaStore = 1, kEpiTmaAdd = 2 };
 constexpr unsigned kWaitLimit = 1u << 24;         // polls of about 64 ns: roughly a second
 
 __device__ unsigned g_tc_status;  // bit 1: a wait timed out
 
 struct Maps {
-  CUtensorMap a, b;
+  CUtensorMap a, b, c;  // c: FP32 C with 32 x 32 boxes and 128-byte swizzle (TMA epilogue modes)
 };
+
+// TMA store (or reduce-add) of a 32 x 32 FP32 box from shared memory at C[y][x], as a bulk group.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src, bool add) {
+  if (add)
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(sbp::smem_u32(src))
+                 : "memory");
+  else
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(sbp::smem_u32(src))
+                 : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
   asm volatile(
@@ -121,13 +145,14 @@ __device__ __forceinline__ Item item(int w, int tm, int tn, int k_per, int K) {
 template <bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ Maps maps, int M, int N, int K, int k_per, int tm, int tn, int items,
-                   void* C, long long ldc, int c_bf16, const float* __restrict__ bias, int relu, float beta) {
+                   void* C, long long ldc, int c_bf16, const float* __restrict__ bias, int relu, float beta,
+                   int epi_mode) {
   extern __shared__ unsigned char smem_raw[];
   // stages at the first 1 KB boundary (the swizzle pattern repeats every 1 KB), then the
   // epilogue warps' transpose tiles, then the barriers
   unsigned char* base = smem_raw + ((1024u - (sbp::smem_u32(smem_raw) & 1023u)) & 1023u);
-  float* epi = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);
-  uint64_t* full = reinterpret_cast<uint64_t*>(epi + 4 * EPI_TILE);
+  unsigned char* epi = base + STAGES * STAGE_BYTES;   // 1 KB aligned: the swizzled store buffers need it
+  uint64_t* full = reinterpret_cast<uint64_t*>(epi + EPI_WARPS * EPI_WARP_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* acc_full = empty + STAGES;
   uint64_t* acc_empty = acc_full + 2;
@@ -143,7 +168,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       sbp::mbar_init(reinterpret_cast<unsigned long long*>(&acc_full[b]), 1);
-      sbp::mbar_init(reinterpret_cast<unsigned long long*>(&acc_empty[b]), 128);  // the epilogue threads
+      sbp::mbar_init(reinterpret_cast<unsigned long long*>(&acc_empty[b]), 32 * EPI_WARPS);  // epilogue threads
     }
     sbp::mbar_init(reinterpret_cast<unsigned long long*>(done), 1);
     *fail = 0;
@@ -235,11 +260,15 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (!wait(done, 0)) atomicOr(fail, 1);
     }
   } else {
-    // epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31, i.e. those rows of the tile
+    // epilogue: warp w reads accumulator lanes 32 (w % 4) .. + 31, i.e. those rows of the tile, and
+    // the column chunks of its half of the tile
     const int lg = warp & 3;
-    float* tile = epi + (warp - 2) * EPI_TILE;
+    const int c0 = ((warp - 2) >> 2) * (BN / 64);
+    unsigned char* wbuf = epi + (warp - 2) * EPI_WARP_BYTES;
+    float* tile = reinterpret_cast<float*>(wbuf);
     const bool split = k_per < K;
-    int t = 0;
+    const bool tma = epi_mode != kEpiDirect;
+    int t = 0, chunks_stored = 0;
     for (int w = blockIdx.x; w < items; w += gridDim.x, ++t) {
       const Item I = item(w, tm, tn, k_per, K);
       const int buf = t & 1, use = t >> 1;
@@ -250,22 +279,48 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       fence_after_sync();
       const uint32_t acc = tmem + (uint32_t)(buf * ACC_COLS) + ((uint32_t)(lg * 32) << 16);
+      const int my_m = I.m0 + lg * 32 + lane;
+      const float my_bias = (bias && I.kb == 0 && my_m < M) ? bias[my_m] : 0.f;
 #pragma unroll 1
-      for (int c = 0; c < BN / 32; ++c) {
+      for (int c = c0; c < c0 + BN / 64; ++c) {
         const int nb = I.n0 + 32 * c;
         if (nb >= N) break;  // uniform over the warp
         float v[32];
         tmem_ld32(acc + (uint32_t)(32 * c), v);
-        // transpose through the warp's tile so that a store covers 32 consecutive columns
+        if (tma) {
+          // bias and ReLU in registers (this thread holds row my_m), then the 32 x 32 box into the
+          // warp's buffer in the 128-byte swizzled layout the store map reads, and a TMA store (or
+          // reduce-add) of the box; rows and columns beyond C are clipped by TMA
 #pragma unroll
-        for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = v[j];
+          for (int j = 0; j < 32; ++j) {
+            v[j] += my_bias;
+            if (relu) v[j] = fmaxf(v[j], 0.f);
+          }
+          unsigned char* sb = wbuf;
+          if (lane == 0 && chunks_stored >= 1)
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the last store has read the buffer
+          __syncwarp();
+          float4* row = reinterpret_cast<float4*>(sb + lane * 128);
+#pragma unroll
+          for (int j4 = 0; j4 < 8; ++j4)
+            row[j4 ^ (lane & 7)] = make_float4(v[4 * j4], v[4 * j4 + 1], v[4 * j4 + 2], v[4 * j4 + 3]);
+          sbp::fence_proxy_async_smem();
+          __syncwarp();
+          if (lane == 0) tma_store_2d(&maps.c, nb, I.m0 + lg * 32, sb, epi_mode == kEpiTmaAdd);
+          ++chunks_stored;
+          continue;
+        }
+        // transpose through the warp's tile so that a store covers 32 consecutive columns (columns
+        // rotated by the row: conflict-free writes of a row and reads of a column)
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tile[lane * 32 + ((j + lane) & 31)] = v[j];
         __syncwarp();
         const int n = nb + lane;
 #pragma unroll 4
         for (int r = 0; r < 32; ++r) {
           const int m = I.m0 + lg * 32 + r;
           if (m >= M) break;  // uniform over the warp
-          float x = tile[r * 33 + lane] + ((bias && I.kb == 0) ? bias[m] : 0.f);
+          float x = tile[r * 32 + ((lane + r) & 31)] + ((bias && I.kb == 0) ? bias[m] : 0.f);
           if (n < N) {
             const long long idx = (long long)m * ldc + n;
             if (split) {
@@ -285,6 +340,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       fence_before_sync();
       mbar_arrive(&acc_empty[buf]);  // this thread has read its part of the accumulator
     }
+    // the stores read their buffers after this CTA's last instruction unless it waits for them
+    if (lane == 0 && tma) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
   fence_before_sync();
   __syncthreads();
@@ -310,7 +367,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 struct MapKey {
   const void* base;
   long long rows, cols, ld;
-  int box_cols, box_rows, dev;
+  int box_cols, box_rows, dev, fp32;
 };
 struct MapEntry {
   MapKey key;
@@ -323,23 +380,23 @@ MapEntry g_maps[kMapCache];
 int g_map_next = 0;
 
 bool encode_uncached(CUtensorMap* m, const void* base, long long rows, long long cols, long long ld, int box_cols,
-                     int box_rows);
+                     int box_rows, bool fp32);
 
-// 2D tensor map of a row-major bf16 matrix with `rows` rows of `cols` elements (row pitch ld),
-// box of box_cols x box_rows, 128-byte swizzle, zero fill outside the matrix.
+// 2D tensor map of a row-major bf16 (or FP32) matrix with `rows` rows of `cols` elements (row
+// pitch ld elements), box of box_cols x box_rows, 128-byte swizzle, zero fill outside the matrix.
 bool encode(CUtensorMap* m, const void* base, long long rows, long long cols, long long ld, int box_cols,
-            int box_rows) {
+            int box_rows, bool fp32 = false) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
-  const MapKey k{base, rows, cols, ld, box_cols, box_rows, dev};
+  const MapKey k{base, rows, cols, ld, box_cols, box_rows, dev, fp32 ? 1 : 0};
   std::lock_guard<std::mutex> lock(g_map_mutex);
   for (auto& e : g_maps)
     if (e.used && e.key.base == k.base && e.key.rows == k.rows && e.key.cols == k.cols && e.key.ld == k.ld &&
-        e.key.box_cols == k.box_cols && e.key.box_rows == k.box_rows && e.key.dev == k.dev) {
+        e.key.box_cols == k.box_cols && e.key.box_rows == k.box_rows && e.key.dev == k.dev && e.key.fp32 == k.fp32) {
       *m = e.map;
       return true;
     }
-  if (!encode_uncached(m, base, rows, cols, ld, box_cols, box_rows)) return false;
+  if (!encode_uncached(m, base, rows, cols, ld, box_cols, box_rows, fp32)) return false;
   MapEntry& slot = g_maps[g_map_next];
   g_map_next = (g_map_next + 1) % kMapCache;
   slot.key = k;
@@ -349,14 +406,16 @@ bool encode(CUtensorMap* m, const void* base, long long rows, long long cols, lo
 }
 
 bool encode_uncached(CUtensorMap* m, const void* base, long long rows, long long cols, long long ld, int box_cols,
-                     int box_rows) {
+                     int box_rows, bool fp32) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
   if (!enc) return false;
+  const int es_bytes = fp32 ? 4 : 2;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  const cuuint64_t strides[1] = {(cuuint64_t)ld * es_bytes};
   const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   const cuuint32_t es[2] = {1, 1};
-  return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+  return enc(m, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+             dims, strides, box, es,
              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -387,6 +446,12 @@ cudaError_t launch_gemm_tc(int M, int N, int K, const void* A, long long lda, in
     if (splits > 1) k_per = (int)(((K + splits - 1) / splits + BK - 1) / BK * BK);
   }
   const long long items = tiles * ((K + k_per - 1) / k_per);
+  // TMA epilogue for FP32 outputs without accumulation (store, or reduce-add of split K) when C
+  // suits TMA (16-byte aligned base, rows a multiple of 16 bytes); the direct path otherwise
+  int epi_mode = kEpiDirect;
+  if (!c_bf16 && beta == 0.f && ldc % 4 == 0 && (uintptr_t)C % 16 == 0 &&
+      encode(&maps.c, C, M, N, ldc, 32, 32, true))
+    epi_mode = k_per < K ? kEpiTmaAdd : kEpiTmaStore;
   if (items > (1LL << 30)) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   if (k_per < K) {
@@ -412,7 +477,7 @@ cudaError_t launch_gemm_tc(int M, int N, int K, const void* A, long long lda, in
       }
     }
     kern<<<grid, THREADS, SMEM_BYTES, st>>>(maps, M, N, K, k_per, tm, tn, (int)items, C, ldc, c_bf16, bias, relu,
-                                           beta);
+                                           beta, epi_mode);
     return cudaGetLastError();
   };
   const bool a_mn = ta != 0, b_mn = tb == 0;
