@@ -154,7 +154,10 @@ int sbp_bind(SbpGrid* grid, void* q0, void* q1, void* dq, void* met, void* mat);
  * compute J and a[xi][eta] = J xi_eta (Cramer's rule, derivatives with
  * D_c = (D+ + D-)/2 of the upwind pair of the grid's order, also for the
  * traditional operators) into jmet (10 FP64 fields: J, then
- * the 9 metrics; device, caller-owned).  Flags SBP_STATUS_BAD_MESH where J <= 0. */
+ * the 9 metrics; device, caller-owned).  Flags SBP_STATUS_BAD_MESH where J <= 0.
+ * On a slab grid every inner end needs at least the reach of that D_c in ghost
+ * planes (for the traditional operators one more than sbp_set_slab asks):
+ * SBP_ERR_ARG otherwise. */
 int sbp_metrics(SbpGrid* grid, const double* xyz, double* jmet, void* stream);
 
 /* Fill the bound met (a[xi][eta] cast to the solver precision) and mat

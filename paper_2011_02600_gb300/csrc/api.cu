@@ -613,6 +613,11 @@ int sbp_bind(SbpGrid* g, void* q0, void* q1, void* dq, void* met, void* mat) {
 int sbp_metrics(SbpGrid* g, const double* xyz, double* jmet, void* stream) {
   if (int rc = check_ready(g)) return rc;
   if (!xyz || !jmet) return fail(SBP_ERR_ARG, "null coordinate or metric buffer");
+  // D_c of the metric operator reaches further than the central operators it serves: a slab's
+  // inner ends must hold that many planes of coordinates
+  const int mreach = op_info(op_info(g->desc.order).metric_order).reach;
+  if ((g->slab.ghost_lo > 0 && g->slab.ghost_lo < mreach) || (g->slab.ghost_hi > 0 && g->slab.ghost_hi < mreach))
+    return fail(SBP_ERR_ARG, "metrics on a slab need at least %d ghost planes at an inner end", mreach);
   cudaError_t e = sbp::launch_metrics(xyz, jmet, g->dims, op_info(g->desc.order).metric_order, g->status,
                                       (cudaStream_t)stream, g->slab);
   return e == cudaSuccess ? SBP_OK : cuda_fail(e, "metrics");

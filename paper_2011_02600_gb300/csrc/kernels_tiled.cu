@@ -130,6 +130,10 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
   T* wbm = A.wbar ? A.wbar + boff : nullptr;
   const T* yhm = A.yhat ? A.yhat + boff : nullptr;
   const int col = j * d.ldq + i;
+  // node offsets within a field as 32-bit indices from per-field base pointers (a field holds
+  // fewer than 2^31 elements: the host refuses larger grids)
+  auto fld = [&](const T* p, int c) -> const T* { return p + c * fs; };
+  auto fldw = [&](T* p, int c) -> T* { return p + c * fs; };
 
   if (tid == 0) {
     mbar_init(&S.bar[0], 1);
@@ -143,25 +147,28 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
   if (active && face_lo && kb < BC) s_closure_sums<T, O, false>(q, met, d, col, scl);
   if (active && face_hi && ke > d.ns - BC) s_closure_sums<T, O, true>(q, met, d, col, scl);
 
-  auto ld = [&](const T* p, long long off) -> T { return active ? __ldg(p + off) : T(0); };
-  // plane kk of field offset fo at this thread's column; zero outside the grid
-  auto ldk = [&](const T* p, long long fo, int kk) -> T {
-    return active && kk >= 0 && kk < d.ns ? __ldg(p + fo + (long long)kk * d.plane + col) : T(0);
+  auto ld = [&](const T* p, unsigned off) -> T { return active ? __ldg(p + off) : T(0); };
+  // streamed once per launch (the RK register): evict-first in the caches
+  auto ld_stream = [&](const T* p, unsigned off) -> T { return active ? __ldcs(p + off) : T(0); };
+  // plane kk of field c of p at this thread's column; zero outside the grid
+  auto ldk = [&](const T* p, int c, int kk) -> T {
+    return active && kk >= 0 && kk < d.ns ? __ldg(fld(p, c) + ((unsigned)kk * (unsigned)d.plane + (unsigned)col))
+                                          : T(0);
   };
   T vq[NV][3];  // v at planes k-R .. k+Q
   T fq[NV][3];  // F_s at planes k-Q .. k+R
 #pragma unroll
   for (int m = 0; m < NV - 1; ++m) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) vq[m][c] = ldk(q, c * fs, kb - R + m);
+    for (int c = 0; c < 3; ++c) vq[m][c] = ldk(q, c, kb - R + m);
   }
 #pragma unroll
   for (int m = 0; m < NV - 1; ++m) {
     T s[6], a[3];
 #pragma unroll
-    for (int c = 0; c < 6; ++c) s[c] = ldk(q, (3 + c) * fs, kb - Q + m);
+    for (int c = 0; c < 6; ++c) s[c] = ldk(q, 3 + c, kb - Q + m);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) a[c] = ldk(met, (6 + c) * fs, kb - Q + m);
+    for (int c = 0; c < 3; ++c) a[c] = ldk(met, 6 + c, kb - Q + m);
     flux(a, s, fq[m]);
   }
 
@@ -169,23 +176,18 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
   T lv[3], ls[6], la[3];
   auto load_lead = [&](int k) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) lv[c] = ldk(q, c * fs, k + Q);
+    for (int c = 0; c < 3; ++c) lv[c] = ldk(q, c, k + Q);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) ls[c] = ldk(q, (3 + c) * fs, k + R);
+    for (int c = 0; c < 6; ++c) ls[c] = ldk(q, 3 + c, k + R);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) la[c] = ldk(met, (6 + c) * fs, k + R);
+    for (int c = 0; c < 3; ++c) la[c] = ldk(met, 6 + c, k + R);
   };
   load_lead(kb);
 
   for (int it = 0, k = kb; k < ke; ++it, ++k) {
     const int sidx = it & 1;
     const unsigned phase = (it >> 1) & 1;
-    const long long pk = (long long)k * d.plane;
-    // push this plane's lead values (loaded during the previous plane), then fetch the next ones
-#pragma unroll
-    for (int c = 0; c < 3; ++c) vq[NV - 1][c] = lv[c];
-    flux(la, ls, fq[NV - 1]);
-    const long long off = pk + col;
+    const unsigned off = (unsigned)k * (unsigned)d.plane + (unsigned)col;
     // the epilogue's own inputs at this node, fetched before the tile wait so that their
     // latency overlaps the plane's derivatives: the RK register (forward stage), Ub_{k+1} and
     // Wb_k (L^T pass), Wb_k, rho and J (gradient pass)
@@ -193,18 +195,18 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
     double rj[2];
     if (KIND == 0 && A.mode == kModeStage) {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) dqi[c] = ld(dqm, c * fs + off);
+      for (int c = 0; c < 9; ++c) dqi[c] = ld_stream(fld(dqm, c), off);
     }
     if (KIND == 1 && A.mode != kModeRhs) {
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        dqi[c] = ub_next ? ld(ub_next, c * fs + off) : T(0);
-        pre[c] = ld(wbm, c * fs + off);
+        dqi[c] = ub_next ? ld(fld(ub_next, c), off) : T(0);
+        pre[c] = ld(fld(wbm, c), off);
       }
     }
     if (KIND == 2) {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) pre[c] = ld(wbm, c * fs + off);
+      for (int c = 0; c < 9; ++c) pre[c] = ld(fld(wbm, c), off);
       rj[0] = active ? __ldg(A.rlmj + off) : 0.0;
       rj[1] = active ? __ldg(A.rlmj + 3 * fs + off) : 0.0;
     }
@@ -329,6 +331,13 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
       const T a[3] = {st.ar[0][HX + ty][tx], st.ar[1][HX + ty][tx], st.ar[2][HX + ty][tx]};
       add_strain(a, dv, e);
     }
+    // push this plane's lead values (loaded one plane earlier), then fetch the next plane's, so
+    // that their latency overlaps the s derivatives, the epilogue and the next plane's q and r
+    // derivatives
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vq[NV - 1][c] = lv[c];
+    flux(la, ls, fq[NV - 1]);
+    if (k + 1 < ke) load_lead(k + 1);
     // s (closure rows only within b of a face of the whole block)
     if ((k >= BC || !face_lo) && (k <= d.ns - 1 - BC || !face_hi)) {
 #pragma unroll
@@ -354,8 +363,6 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
       const T a[3] = {st.as[0][ty][tx], st.as[1][ty][tx], st.as[2][ty][tx]};
       add_strain(a, dv, e);
     }
-    // lead values of the next plane (in flight during the epilogue and the next barrier)
-    if (k + 1 < ke) load_lead(k + 1);
 
     if (active && KIND == 0) {
       T qc[9];
@@ -374,14 +381,14 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
       apply_P(rv, e, st.mat[0][ty][tx], st.mat[1][ty][tx], st.mat[2][ty][tx], dd);
       if (A.mode == kModeRhs) {
 #pragma unroll
-        for (int f = 0; f < 9; ++f) qout[f * fs + off] = dd[f];
+        for (int f = 0; f < 9; ++f) fldw(qout, f)[off] = dd[f];
       } else {
 #pragma unroll
         for (int f = 0; f < 9; ++f) {
           T dn = A.dt * dd[f];
           if (A.mode == kModeStage) dn += A.rk_a * dqi[f];
-          dqm[f * fs + off] = dn;
-          qout[f * fs + off] = qc[f] + A.rk_b * dn;
+          __stcs(fldw(dqm, f) + off, dn);                    // read again one stage later
+          __stcs(fldw(qout, f) + off, qc[f] + A.rk_b * dn);
         }
       }
     } else if (active) {
@@ -421,12 +428,12 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
         const T m9[9] = {vb[0], vb[1], vb[2], sb[0], sb[1], sb[2], sb[3], sb[4], sb[5]};
         if (A.mode == kModeRhs) {
 #pragma unroll
-          for (int f = 0; f < 9; ++f) ub_out[f * fs + off] = m9[f];
+          for (int f = 0; f < 9; ++f) fldw(ub_out, f)[off] = m9[f];
         } else {
 #pragma unroll
           for (int f = 0; f < 9; ++f) {
-            ub_out[f * fs + off] = dqi[f] + A.dt * m9[f];
-            wbm[f * fs + off] = A.rk_a * pre[f];
+            fldw(ub_out, f)[off] = dqi[f] + A.dt * m9[f];
+            fldw(wbm, f)[off] = A.rk_a * pre[f];
           }
         }
       } else {
@@ -436,7 +443,7 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
           const T H = norm_weight_t<T, O>(i, d.nq) * A.h[0] * norm_weight_t<T, O>(j, d.nr) * A.h[1] *
                       norm_weight_t<T, O>(k, d.ns) * A.h[2];
 #pragma unroll
-          for (int f = 0; f < 9; ++f) y[f] = H * yhm[f * fs + off];
+          for (int f = 0; f < 9; ++f) y[f] = H * fld(yhm, f)[off];
         }
         double g[3];
         gradient_terms(rv, e, qc, pre, y, pos, N, a, irhoJ, lamJ, muJ, rj[0], rj[1], A.bc_kind, A.bc_gamma,

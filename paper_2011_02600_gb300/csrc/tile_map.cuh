@@ -36,7 +36,7 @@ __device__ __forceinline__ TileAxis tile_axis(int t, int nt, int n, int w, int a
 // each other) run close together in time and the second reads the halo from L2; in plain
 // row order r neighbours start a whole row of tiles apart, and on wide grids the halo has
 // left L2 by then.
-constexpr int kSwizzle = 8;
+constexpr int kSwizzle = 12;
 __device__ __forceinline__ void swizzle_tiles(int lin, int nbx, int nby, int& bx, int& by) {
   const int full = nbx / kSwizzle;                 // complete groups
   const int group = lin / (kSwizzle * nby);

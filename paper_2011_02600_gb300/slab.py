@@ -50,6 +50,12 @@ def reach(order, operator="upwind"):
     return r[code]
 
 
+def metric_reach(order):
+    """Planes of coordinates D_c of the metric operator reaches on each side: the metrics of
+    every operator of a given order come from the upwind pair of that order."""
+    return reach(order, "upwind")
+
+
 def partition(ns, world, order, operator="upwind", min_face_planes=None):
     """Owned plane ranges of `world` slabs of a block of ns planes, as equal as the constraints
     allow: every slab owns at least `reach` planes (what it sends to a neighbour) and holds at
@@ -151,11 +157,13 @@ class SlabSolver:
         self.s = ElasticSolver((nq, nr, slab.planes), order, precision, bc, device=device, operator=operator,
                                slab=(ns, slab.lo, slab.ghost_lo, slab.ghost_hi))
         # metrics at every local plane, ghost planes included: sbp_metrics on a window slab whose
-        # owned planes are this slab's local planes, with reach more planes of coordinates on each
-        # inner side (the rows of D_c are the block's)
-        g = self.g
-        glo, ghi = (g if slab.lo > 0 else 0), (g if slab.hi < ns else 0)
-        w0, w1 = slab.lo - glo, slab.hi + ghi
+        # owned planes cover this slab's local planes, with as many more planes of coordinates on
+        # each inner side as D_c of the metric operator reaches (the rows of D_c are the block's;
+        # the central operators' metric operator is the upwind pair of their order, which reaches
+        # one plane further than they do)
+        gm = max(self.g, metric_reach(order))
+        w0, w1 = max(0, slab.lo - gm), min(ns, slab.hi + gm)
+        glo, ghi = (slab.lo - w0 if w0 > 0 else 0), (w1 - slab.hi if w1 < ns else 0)
         win = ElasticSolver((nq, nr, w1 - w0), order, 64, bc, device=device, operator=operator,
                             slab=(ns, w0, glo, ghi) if (glo or ghi) else None)
         xyz = win.to_layout(torch.as_tensor(coords(w0, w1)), torch.float64)
@@ -164,7 +172,7 @@ class SlabSolver:
         if L.sbp_status(win.h, _stream()) & 2:
             raise L.SbpError(6, "non-positive Jacobian")
         jmet = self.s.new_fields(10, torch.float64)
-        self.s.view(jmet, 10).copy_(win.view(jwin, 10)[:, glo:glo + slab.planes])
+        self.s.view(jmet, 10).copy_(win.view(jwin, 10)[:, slab.lo - w0:slab.lo - w0 + slab.planes])
         del win, xyz, jwin
         rlm_b = self.s.to_layout(torch.as_tensor(rlm(slab.lo, slab.hi)), torch.float64)
         L.sbp_set_material(self.s.h, jmet, rlm_b, _stream())

@@ -68,6 +68,12 @@ def test_slab_refusals():
         with pytest.raises(L.SbpError) as e:
             fn(s.h, *args)
         assert e.value.code == 2
+    # the central operator of order 6 reaches 3 planes, its metric operator (the upwind pair of
+    # order 6) 4: metrics on a slab with 3 ghost planes would read past the local planes
+    t = ElasticSolver(nodes, 6, 64, BC, slab=(60, 10, 3, 3), operator="traditional")
+    with pytest.raises(L.SbpError) as e:
+        L.sbp_metrics(t.h, t.new_fields(3, torch.float64), t.new_fields(10, torch.float64), 0)
+    assert e.value.code == 1
     h = L.sbp_create_grid(nodes, 4, 64, BC)
     for bad in [(60, 10, 2, 3), (60, 0, 3, 3), (60, 40, 3, 0), (60, 50, 3, 3), (8, 0, 0, 3)]:
         with pytest.raises(L.SbpError) as e:
