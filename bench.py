@@ -44,6 +44,12 @@ FLOP_PER_NODE_STAGE = 444         # order 6, interior node, counted from the til
                                   # is 2): fluxes F_q, F_r on the tile and halo (1.19 + 1.75 per node) and F_s,
                                   # 15 each: 59; D- and D+ on 3 axes x 3 components, 7 taps and a scaling: 270;
                                   # strain rows 54; P~ 16; Runge-Kutta update 45
+# The topography-map path (x = L_x q, y = L_y r: a_q = (a_q,x, 0, 0), a_r = (0, c a_q,x, 0)) reads 4
+# metric fields instead of 9: 43 values per node and stage, 34 in stage 0; its fluxes F_q, F_r take
+# 3 and 4 flop and the q and r strain rows 6 and 7, so 388 flop per node and stage.
+BYTES_PER_NODE_STAGE_TOPO = 172
+BYTES_PER_NODE_STAGE0_TOPO = 136
+FLOP_PER_NODE_STAGE_TOPO = 388
 FP64_NOMINAL_TFLOPS = 1.25        # GB300 FP64 nominal; the roofline uses the rate measured on the device
 
 
@@ -520,7 +526,11 @@ def main():
     else:
         kind, launches, kms_tot, knodes = "general", kn[1], kms[1], nodes
     # per launch: stage 0 reads no RK register; average over the 5 stages of a step
-    avg_bytes = knodes * (BYTES_PER_NODE_STAGE * 4 + BYTES_PER_NODE_STAGE0) / 5.0 * (elem / 4)
+    topo = kind == "tiled" and s.map_path() == "topography"
+    b14, b0 = (BYTES_PER_NODE_STAGE_TOPO, BYTES_PER_NODE_STAGE0_TOPO) if topo else (BYTES_PER_NODE_STAGE,
+                                                                                   BYTES_PER_NODE_STAGE0)
+    flop_node = FLOP_PER_NODE_STAGE_TOPO if topo else FLOP_PER_NODE_STAGE
+    avg_bytes = knodes * (b14 * 4 + b0) / 5.0 * (elem / 4)
     avg_ms = kms_tot / max(1, launches)
     achieved = avg_bytes / (avg_ms / 1e3) / 1e9
     peaks = _peaks()
@@ -533,22 +543,26 @@ def main():
             if ":" in ln and not ln.startswith("#"):
                 a, b2 = ln.split(":", 1)
                 kv[a.strip()] = b2.strip()
-        if kv.get("kernel_source_digest") == _kernel_digest():
+        if kv.get("kernel_source_digest") == _kernel_digest() and \
+                kv.get("metric_path", "general") == ("topography" if topo else "general"):
             per_node = (float(kv["dram_bytes_per_node_stage0"]) + 4 * float(kv["dram_bytes_per_node_stage1to4"])) / 5
             prof_traffic = per_node * knodes
 
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": prof_traffic if elem == 4 else None, "kernel": kind,
-            "algorithmic_bytes_per_launch": avg_bytes, "avg_launch_ms": avg_ms,
+            "algorithmic_bytes_per_launch": avg_bytes, "algorithmic_bytes_per_node_stage": [b0, b14],
+            "metric_path": "topography (a_q,x and a_s)" if topo else "general (9 metric fields)",
+            "avg_launch_ms": avg_ms,
             "launches": launches, "peak_source": "measured" if peaks else "fallback",
             "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS}
     if elem == 8:
         # FP64 is bound by the FP64 pipe, not by HBM: its peak is measured here by an FMA-chain probe
         fp64_peak = L.sbp_probe_fp64_rate(2000000, _stream())
-        tflops = FLOP_PER_NODE_STAGE * knodes / (avg_ms / 1e3) / 1e12
+        tflops = flop_node * knodes / (avg_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": tflops, "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": tflops / fp64_peak, "traffic": None, "kernel": kind,
-                "algorithmic_flop_per_launch": FLOP_PER_NODE_STAGE * knodes, "avg_launch_ms": avg_ms,
+                "algorithmic_flop_per_launch": flop_node * knodes, "avg_launch_ms": avg_ms,
+                "metric_path": "topography (a_q,x and a_s)" if topo else "general (9 metric fields)",
                 "launches": launches,
                 "peak_source": "measured: FP64 FMA-chain probe (sbp_probe_fp64_rate) on this device",
                 "nominal_peak": FP64_NOMINAL_TFLOPS, "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak}

@@ -163,8 +163,30 @@ int sbp_metrics(SbpGrid* grid, const double* xyz, double* jmet, void* stream);
 /* Fill the bound met (a[xi][eta] cast to the solver precision) and mat
  * (1/(rho J), lambda/J, mu/J) from jmet (as produced by sbp_metrics) and rlm
  * (3 FP64 fields rho, lambda, mu; device).  Flags SBP_STATUS_BAD_MATERIAL where
- * rho <= 0, mu <= 0 or lambda + 2 mu <= 0.  Needs sbp_bind. */
+ * rho <= 0, mu <= 0 or lambda + 2 mu <= 0.  Also finds whether the metrics are
+ * those of a topography map x = L_x q, y = L_y r, z = z(q, r, s) (the configs'
+ * layered and topographic grids): then a_q = (a_q,x, 0, 0) and a_r =
+ * (0, c a_q,x, 0) with the constant c = L_x / L_y at every node, to 1e-11
+ * relative (the vanishing components are rounding noise of D_c on the linear
+ * x and y), and the tiled forward stage of the upwind orders 2, 4, 6 reads 4
+ * metric fields (a_q,x, a_s) instead of 9 (sbp_map_path).  Synchronises the
+ * stream.  Needs sbp_bind. */
 int sbp_set_material(SbpGrid* grid, const double* jmet, const double* rlm, void* stream);
+
+/* Metric path of the tiled forward stage (not part of the paper: its method is
+ * the same on either path; the topography path only skips the metric components
+ * that vanish).  SBP_MAP_AUTO (default): the topography path where
+ * sbp_set_material found a topography map; SBP_MAP_GENERAL: always all nine
+ * metric components.  May be called at any time; the next stage uses it. */
+#define SBP_MAP_AUTO 0
+#define SBP_MAP_GENERAL 1
+#define SBP_MAP_TOPOGRAPHY 2
+int sbp_set_map_path(SbpGrid* grid, int32_t path);
+
+/* The metric path the tiled forward stage uses now: SBP_MAP_TOPOGRAPHY or
+ * SBP_MAP_GENERAL (before sbp_set_material, on the general kernel path, for the
+ * orders without a topography variant, or after SBP_MAP_GENERAL). */
+int sbp_map_path(SbpGrid* grid, int32_t* path);
 
 /* dQ/dt of the semi-discrete scheme with penalties (Eq.
  * gen_hyp_transformed_discrete_SAT multiplied by P~) for the state q (9 fields,

@@ -15,6 +15,7 @@ SBP_BC_INTERFACE = 2
 SBP_TRADITIONAL = 100
 SBP_MEM_HOST = 1
 SBP_LAYOUT_DENSE = 2
+SBP_MAP_AUTO, SBP_MAP_GENERAL, SBP_MAP_TOPOGRAPHY = 0, 1, 2
 ERRORS = {1: "ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "NONFINITE", 5: "STATE", 6: "MESH"}
 
 EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sbp_bind", "sbp_metrics",
@@ -27,7 +28,7 @@ EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sb
             "sbp_nn_mlp_to_conv", "sbp_nn_cast_bf16", "sbp_nn_moment_combine", "sbp_selftest_wait_timeout", "sbp_last_error",
             "sbp_set_receivers_xyz", "sbp_record_receivers", "sbp_set_state", "sbp_get_state",
             "sbp_nn_set_gemm_path", "sbp_nn_status", "sbp_set_slab", "sbp_interface_trace", "sbp_set_interface",
-            "sbp_probe_fp64_rate")
+            "sbp_probe_fp64_rate", "sbp_set_map_path", "sbp_map_path")
 
 
 class SbpError(RuntimeError):
@@ -74,6 +75,8 @@ def lib(path=None):
         "sbp_rk_stage": [P, i32, dbl, P],
         "sbp_step_n": [P, i32, dbl, P],
         "sbp_set_kernel_path": [P, i32],
+        "sbp_set_map_path": [P, i32],
+        "sbp_map_path": [P, ctypes.POINTER(i32)],
         "sbp_current": [P, ctypes.POINTER(i32)],
         "sbp_kernel_timing": [P, i32],
         "sbp_kernel_times": [P, ctypes.POINTER(dbl), ctypes.POINTER(i64)],
@@ -192,6 +195,16 @@ def sbp_step_n(h, n, dt, stream):
 
 def sbp_set_kernel_path(h, path):
     _check(lib().sbp_set_kernel_path(h, path))
+
+
+def sbp_set_map_path(h, path):
+    _check(lib().sbp_set_map_path(h, path))
+
+
+def sbp_map_path(h):
+    v = ctypes.c_int32(0)
+    _check(lib().sbp_map_path(h, ctypes.byref(v)))
+    return v.value
 
 
 def sbp_kernel_timing(h, enable):

@@ -162,6 +162,11 @@ struct SbpGrid {
   sbp::SlabS slab;         // s-slab of a decomposed block (sbp_set_slab); default: the whole block
   const void* iface[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // other blocks' traces
   void* sclose = nullptr;  // tiled kernel scratch (s-closure sums), owned by the library
+  // topography map (found by sbp_set_material): the tiled forward stage reads a_q,x and a_s only
+  unsigned long long* topo_dev = nullptr;  // detection scratch (one word)
+  bool topo = false;
+  double ar_ratio = 0.0;  // a_r,y / a_q,x
+  int map_path = SBP_MAP_AUTO;
   // tensor maps of the tiled stage kernel, per state buffer (q0, q1)
   bool tma_ok[2] = {false, false};
   sbp::TmaSet tma[2];
@@ -215,6 +220,14 @@ sbp::BoxList whole_grid(const SbpGrid* g) {
   return L;
 }
 
+// The tiled forward stage reads the topography map's 4 metric fields where the metrics are
+// those of such a map (sbp_set_material), the path is automatic (sbp_set_map_path) and the
+// variant is built for the operator (upwind orders 2, 4, 6).
+bool uses_topography(const SbpGrid* g) {
+  const int o = g->desc.order;
+  return g->topo && g->map_path == SBP_MAP_AUTO && (o == 2 || o == 4 || o == 6);
+}
+
 template <typename T>
 sbp::StageArgs<T> make_args(const SbpGrid* g, const void* q, void* qout, int mode, double a, double bcoef,
                             double dt, int nb = 1) {
@@ -235,6 +248,8 @@ sbp::StageArgs<T> make_args(const SbpGrid* g, const void* q, void* qout, int mod
   A.sclose = (T*)g->sclose;
   A.sc_bstride = sclose_elems(g);
   A.slab = g->slab;
+  A.map = uses_topography(g) ? 1 : 0;
+  A.ar_ratio = (T)g->ar_ratio;
   // spacing along s: that of the whole block when the grid is one of its slabs
   const int N[3] = {g->desc.nq, g->desc.nr, g->slab.ns_global > 0 ? g->slab.ns_global : g->desc.ns};
   for (int f = 0; f < 6; ++f) {
@@ -309,6 +324,7 @@ int encode_maps(const SbpGrid* g, const void* q, int nb, sbp::TmaSet* out) {
   if (!rc) rc = one(&out->met_r, g->met, 9, 32, 16, 3);
   if (!rc) rc = one(&out->met_s, g->met, 9, 32, 8, 3);
   if (!rc) rc = one(&out->mat, g->mat, 3, 32, 8, 3);
+  if (!rc) rc = one(&out->met_j, g->met, 9, 40, 16, 1);
   return rc;
 }
 
@@ -566,6 +582,7 @@ int sbp_destroy(SbpGrid* g) {
   cudaFree(g->rec_off);
   if (g->traces_owned) cudaFree(g->traces);
   cudaFree(g->sclose);
+  cudaFree(g->topo_dev);
   delete g;
   return SBP_OK;
 }
@@ -600,6 +617,7 @@ int sbp_bind(SbpGrid* g, void* q0, void* q1, void* dq, void* met, void* mat) {
     if (e == cudaSuccess) e = cudaMalloc(&g->eout, sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&g->status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(g->status, 0, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&g->topo_dev, sizeof(unsigned long long));
     if (e != cudaSuccess) return cuda_fail(e, "internal buffers");
   }
   if (!g->sclose) {
@@ -631,7 +649,44 @@ int sbp_set_material(SbpGrid* g, const double* jmet, const double* rlm, void* st
                                : sbp::launch_material<double>(jmet, rlm, (double*)g->met, (double*)g->mat, g->dims,
                                                               g->status, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "material");
+  // topography map?  c = a_r,y / a_q,x at node 0, then every node within 1e-11 (relative) of
+  // a_q = (a_q,x, 0, 0), a_r = (0, c a_q,x, 0).  The components that vanish for such a map come
+  // out of D_c applied to the linear x and y as rounding noise that grows with the node count
+  // (about 1e-13 of a_q,x on 1025 nodes); genuinely curvilinear maps are far above the bound.
+  cudaStream_t st = (cudaStream_t)stream;
+  const sbp::Dims& d = g->dims;
+  double a0[2] = {0.0, 0.0};
+  unsigned long long worst = ~0ull;
+  e = cudaMemcpyAsync(&a0[0], jmet + 1 * d.fs, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&a0[1], jmet + 5 * d.fs, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const double c = a0[1] / a0[0];
+  g->topo = false;
+  if (e == cudaSuccess && isfinite(c) && c > 0.0) {
+    e = cudaMemsetAsync(g->topo_dev, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = sbp::launch_topography_check(jmet, d, c, g->topo_dev, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&worst, g->topo_dev, sizeof(worst), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    double w;
+    memcpy(&w, &worst, sizeof(w));
+    g->topo = e == cudaSuccess && w <= 1.0e-11;
+    g->ar_ratio = c;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "topography check");
   g->material = true;
+  return SBP_OK;
+}
+
+int sbp_set_map_path(SbpGrid* g, int32_t path) {
+  if (!g) return fail(SBP_ERR_ARG, "null grid");
+  if (path != SBP_MAP_AUTO && path != SBP_MAP_GENERAL) return fail(SBP_ERR_ARG, "map path must be 0 (auto) or 1 (general)");
+  g->map_path = path;
+  return SBP_OK;
+}
+
+int sbp_map_path(SbpGrid* g, int32_t* path) {
+  if (!g || !path) return fail(SBP_ERR_ARG, "null argument");
+  *path = uses_topography(g) && g->use_tiled ? SBP_MAP_TOPOGRAPHY : SBP_MAP_GENERAL;
   return SBP_OK;
 }
 

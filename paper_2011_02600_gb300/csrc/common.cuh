@@ -85,6 +85,8 @@ struct StageArgs {
   double* grad;         // gradient accumulators (FP64, 3 fields)
   SlabS slab;           // s-slab of a decomposed block (default: the whole block)
   IfaceArgs<T> ifc;     // the other blocks' traces at interface faces (none by default)
+  int map;              // 1: topography map (a_q = (a_q,x, 0, 0), a_r = (0, ar_ratio a_q,x, 0)); 0: general
+  T ar_ratio;           // a_r,y / a_q,x of a topography map (L_x / L_y)
 };
 
 // Closure rows of D+ and D- (unit spacing), one private copy per translation unit; orders

@@ -38,14 +38,100 @@ namespace sbp {
 
 constexpr unsigned kWaitLimit = 1u << 24;  // polls (with 64 ns sleeps) before giving up: about a second
 
+// Metric storage the kernel reads.  MAP 0: the general curvilinear map, all nine a_xi.
+// MAP 1: a topography map x = L_x q, y = L_y r, z = z(q, r, s), where a_q = (J / L_x, 0, 0) and
+// a_r = (0, J / L_y, 0) = (0, c a_q,x, 0) with the constant c = L_x / L_y: only a_q,x (field 0,
+// with halos on q and r) and a_s are read, 4 metric fields instead of 9.
+template <typename T, int MAP>
+struct Stage;
 template <typename T>
-struct Stage {
+struct Stage<T, 0> {
   T state[9][BYH][BXH];
   T aq[3][TY][BXH];
   T ar[3][BYH][TX];
   T as[3][TY][TX];
   T mat[3][TY][TX];
 };
+template <typename T>
+struct Stage<T, 1> {
+  T state[9][BYH][BXH];
+  T jq[BYH][BXH];  // a_q,x on the tile and both halos
+  T as[3][TY][TX];
+  T mat[3][TY][TX];
+};
+
+// a_q at flux-tile row `row` (0..TY-1), smem column `col` (0..BXH-1); a_r at r-halo row `row`
+// (0..BYH-1), column `col` (0..TX-1).
+template <typename T>
+__device__ __forceinline__ void aq_at(const Stage<T, 0>& st, int row, int col, T c_r, T a[3]) {
+  (void)c_r;
+  a[0] = st.aq[0][row][col];
+  a[1] = st.aq[1][row][col];
+  a[2] = st.aq[2][row][col];
+}
+template <typename T>
+__device__ __forceinline__ void aq_at(const Stage<T, 1>& st, int row, int col, T c_r, T a[3]) {
+  (void)c_r;
+  a[0] = st.jq[HX + row][col];
+  a[1] = T(0);
+  a[2] = T(0);
+}
+template <typename T>
+__device__ __forceinline__ void ar_at(const Stage<T, 0>& st, int row, int col, T c_r, T a[3]) {
+  (void)c_r;
+  a[0] = st.ar[0][row][col];
+  a[1] = st.ar[1][row][col];
+  a[2] = st.ar[2][row][col];
+}
+template <typename T>
+__device__ __forceinline__ void ar_at(const Stage<T, 1>& st, int row, int col, T c_r, T a[3]) {
+  a[0] = T(0);
+  a[1] = c_r * st.jq[row][HX + col];
+  a[2] = T(0);
+}
+
+// Fluxes F_q = sigma a_q, F_r = sigma a_r and the strain rows of one axis; MAP 1 skips the
+// products with the components that vanish.
+template <int MAP, typename T>
+__device__ __forceinline__ void flux_q(const T a[3], const T s[6], T F[3]) {
+  if constexpr (MAP == 1) {
+    F[0] = a[0] * s[0];
+    F[1] = a[0] * s[3];
+    F[2] = a[0] * s[4];
+  } else {
+    flux(a, s, F);
+  }
+}
+template <int MAP, typename T>
+__device__ __forceinline__ void flux_r(const T a[3], const T s[6], T F[3]) {
+  if constexpr (MAP == 1) {
+    F[0] = a[1] * s[3];
+    F[1] = a[1] * s[1];
+    F[2] = a[1] * s[5];
+  } else {
+    flux(a, s, F);
+  }
+}
+template <int MAP, typename T>
+__device__ __forceinline__ void strain_q(const T a[3], const T dv[3], T e[6]) {
+  if constexpr (MAP == 1) {
+    e[0] += a[0] * dv[0];
+    e[3] += a[0] * dv[1];
+    e[4] += a[0] * dv[2];
+  } else {
+    add_strain(a, dv, e);
+  }
+}
+template <int MAP, typename T>
+__device__ __forceinline__ void strain_r(const T a[3], const T dv[3], T e[6]) {
+  if constexpr (MAP == 1) {
+    e[1] += a[1] * dv[1];
+    e[3] += a[1] * dv[0];
+    e[5] += a[1] * dv[2];
+  } else {
+    add_strain(a, dv, e);
+  }
+}
 
 template <typename T>
 struct FluxTiles {
@@ -53,9 +139,9 @@ struct FluxTiles {
   T fr[3][BYH][TX];
 };
 
-template <typename T>
+template <typename T, int MAP>
 struct TiledShared {
-  Stage<T> st[2];
+  Stage<T, MAP> st[2];
   FluxTiles<T> f[2];
   QRows<T> qrows;
   unsigned long long bar[2];
@@ -64,15 +150,19 @@ struct TiledShared {
 template <typename T>
 constexpr int tiled_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
 
-template <typename T>
-__device__ __forceinline__ void issue_plane(TiledShared<T>& S, int stage, const TmaSet& tm, int i0, int j0,
+template <typename T, int MAP>
+__device__ __forceinline__ void issue_plane(TiledShared<T, MAP>& S, int stage, const TmaSet& tm, int i0, int j0,
                                             int k, int member) {
   unsigned long long* bar = &S.bar[stage];
-  mbar_expect_tx(bar, (unsigned)sizeof(Stage<T>));
-  Stage<T>& st = S.st[stage];
+  mbar_expect_tx(bar, (unsigned)sizeof(Stage<T, MAP>));
+  Stage<T, MAP>& st = S.st[stage];
   tma_load_4d(&st.state[0][0][0], &tm.state, i0 - HX, j0 - HX, k, 9 * member, bar);
-  tma_load_4d(&st.aq[0][0][0], &tm.met_q, i0 - HX, j0, k, 0, bar);
-  tma_load_4d(&st.ar[0][0][0], &tm.met_r, i0, j0 - HX, k, 3, bar);
+  if constexpr (MAP == 1) {
+    tma_load_4d(&st.jq[0][0], &tm.met_j, i0 - HX, j0 - HX, k, 0, bar);
+  } else {
+    tma_load_4d(&st.aq[0][0][0], &tm.met_q, i0 - HX, j0, k, 0, bar);
+    tma_load_4d(&st.ar[0][0][0], &tm.met_r, i0, j0 - HX, k, 3, bar);
+  }
   tma_load_4d(&st.as[0][0][0], &tm.met_s, i0, j0, k, 6, bar);
   tma_load_4d(&st.mat[0][0][0], &tm.mat, i0, j0, k, 0, bar);
 }
@@ -80,9 +170,10 @@ __device__ __forceinline__ void issue_plane(TiledShared<T>& S, int stage, const 
 // KIND 0: the forward stage.  KIND 1: the adjoint's L^T pass on q = yhat (-H times the
 // forward rows, face terms of the transposes; Ub and Wb updated).  KIND 2: the material
 // gradient pass on q = U_k (forward rows and penalties contracted with Wb_k).
-template <typename T, int O, int KIND>
+template <typename T, int O, int KIND, int MAP>
 __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
     stage_tiled_kernel(StageArgs<T> A, int chunk, const __grid_constant__ TmaSet tm) {
+  static_assert(MAP == 0 || KIND == 0, "the adjoint passes read the general metrics");
   using C = OpCoef<O>;
   constexpr int R = C::r;    // D+ reaches -R..+Q, D- reaches -Q..+R
   constexpr int Q = C::q;
@@ -92,7 +183,8 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
   static_assert(CW <= TY + R && CW <= TX + R && BC <= TY, "closure rows must fit the first tile");
   static_assert(Q <= HX && R <= HX, "halo too small");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  TiledShared<T>& S = *reinterpret_cast<TiledShared<T>*>(smem_raw);
+  TiledShared<T, MAP>& S = *reinterpret_cast<TiledShared<T, MAP>*>(smem_raw);
+  const T c_r = A.ar_ratio;  // MAP 1: a_r,y / a_q,x
 
   const Dims d = A.d;
   const long long fs = d.fs;
@@ -216,31 +308,31 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
     // every thread leaves.  Until then a thread whose wait gave up only reads shared memory at
     // fixed in-bounds indices.
     const bool landed = mbar_wait_bounded(&S.bar[sidx], phase, kWaitLimit);
-    const Stage<T>& st = S.st[sidx];
+    const Stage<T, MAP>& st = S.st[sidx];
     FluxTiles<T>& F = S.f[sidx];
     // fluxes on the tile and its halo: F_q at columns -QF..TX-1+R, F_r at rows -QF..TY-1+R
     constexpr int QF = flux_halo<O>();
     for (int t = tid; t < TY * (QF + R + TX); t += TX * TY) {
       const int row = t / (QF + R + TX);
       const int cc = HX - QF + t % (QF + R + TX);
-      const T a[3] = {st.aq[0][row][cc], st.aq[1][row][cc], st.aq[2][row][cc]};
-      T s[6];
+      T a[3], s[6];
+      aq_at(st, row, cc, c_r, a);
 #pragma unroll
       for (int c = 0; c < 6; ++c) s[c] = st.state[3 + c][HX + row][cc];
       T Fv[3];
-      flux(a, s, Fv);
+      flux_q<MAP>(a, s, Fv);
 #pragma unroll
       for (int c = 0; c < 3; ++c) F.fq[c][row][cc] = Fv[c];
     }
     for (int t = tid; t < TX * (QF + R + TY); t += TX * TY) {
       const int cl = t % TX;
       const int rr = HX - QF + t / TX;
-      const T a[3] = {st.ar[0][rr][cl], st.ar[1][rr][cl], st.ar[2][rr][cl]};
-      T s[6];
+      T a[3], s[6];
+      ar_at(st, rr, cl, c_r, a);
 #pragma unroll
       for (int c = 0; c < 6; ++c) s[c] = st.state[3 + c][rr][HX + cl];
       T Fv[3];
-      flux(a, s, Fv);
+      flux_r<MAP>(a, s, Fv);
 #pragma unroll
       for (int c = 0; c < 3; ++c) F.fr[c][rr][cl] = Fv[c];
     }
@@ -290,8 +382,9 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
       }
     }
     {
-      const T a[3] = {st.aq[0][ty][HX + tx], st.aq[1][ty][HX + tx], st.aq[2][ty][HX + tx]};
-      add_strain(a, dv, e);
+      T a[3];
+      aq_at(st, ty, HX + tx, c_r, a);
+      strain_q<MAP>(a, dv, e);
     }
     // r
     if (!r_close) {
@@ -305,8 +398,9 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
         rv[c] += ihr * sf;
         dv[c] = ihr * sv;
       }
-      const T a[3] = {st.ar[0][HX + ty][tx], st.ar[1][HX + ty][tx], st.ar[2][HX + ty][tx]};
-      add_strain(a, dv, e);
+      T a[3];
+      ar_at(st, HX + ty, tx, c_r, a);
+      strain_r<MAP>(a, dv, e);
     } else if (active) {
       // closure row of a node within b of an r face (whole warps: the row is uniform)
       const bool lo = j < BC;
@@ -328,8 +422,9 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
         rv[m] += ihr * sf[m];
         dv[m] = ihr * sv[m];
       }
-      const T a[3] = {st.ar[0][HX + ty][tx], st.ar[1][HX + ty][tx], st.ar[2][HX + ty][tx]};
-      add_strain(a, dv, e);
+      T a[3];
+      ar_at(st, HX + ty, tx, c_r, a);
+      strain_r<MAP>(a, dv, e);
     }
     // push this plane's lead values (loaded one plane earlier), then fetch the next plane's, so
     // that their latency overlaps the s derivatives, the epilogue and the next plane's q and r
@@ -371,9 +466,11 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
       if (qr_face || k == 0 || k == d.ns - 1) {
         const int pos[3] = {i, j, k};
         const int N[3] = {d.nq, d.nr, d.ns};
-        const T a[3][3] = {{st.aq[0][ty][HX + tx], st.aq[1][ty][HX + tx], st.aq[2][ty][HX + tx]},
-                           {st.ar[0][HX + ty][tx], st.ar[1][HX + ty][tx], st.ar[2][HX + ty][tx]},
-                           {st.as[0][ty][tx], st.as[1][ty][tx], st.as[2][ty][tx]}};
+        T a[3][3];
+        aq_at(st, ty, HX + tx, c_r, a[0]);
+        ar_at(st, HX + ty, tx, c_r, a[1]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) a[2][c] = st.as[c][ty][tx];
         add_face_penalties(pos, N, a, qc, st.mat[0][ty][tx], st.mat[1][ty][tx], st.mat[2][ty][tx], A.bc_kind,
                            A.bc_gamma, A.inv_h0, rv, e, &A.ifc, member);
       }
@@ -401,12 +498,10 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
       const T irhoJ = st.mat[0][ty][tx], lamJ = st.mat[1][ty][tx], muJ = st.mat[2][ty][tx];
       T a[3][3];
       if (face) {
+        aq_at(st, ty, HX + tx, c_r, a[0]);
+        ar_at(st, HX + ty, tx, c_r, a[1]);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          a[0][c] = st.aq[c][ty][HX + tx];
-          a[1][c] = st.ar[c][HX + ty][tx];
-          a[2][c] = st.as[c][ty][tx];
-        }
+        for (int c = 0; c < 3; ++c) a[2][c] = st.as[c][ty][tx];
       }
       if (KIND == 2 && face)
         add_face_penalties(pos, N, a, qc, irhoJ, lamJ, muJ, A.bc_kind, A.bc_gamma, A.inv_h0, rv, e);
@@ -484,7 +579,7 @@ cudaError_t launch_wait_selftest(unsigned polls, unsigned* status, cudaStream_t 
 template <int O>
 constexpr int NVQ() { return OpCoef<O>::r + OpCoef<O>::q; }
 
-template <typename T, int O, int KIND>
+template <typename T, int O, int KIND, int MAP = 0>
 cudaError_t launch_tiled_order(const StageArgs<T>& A, const TmaSet& tm, cudaStream_t st) {
   const int ni = A.d.nq, nj = A.d.nr, nk = A.d.ns - A.slab.ghost_lo - A.slab.ghost_hi;  // computed planes
   // s chunks: at most 96 planes; when that leaves SM slots idle (few tiles), more chunks
@@ -513,17 +608,28 @@ cudaError_t launch_tiled_order(const StageArgs<T>& A, const TmaSet& tm, cudaStre
   dim3 grid((ni + TX - 1) / TX, (nj + TY - 1) / TY, ((nk + chunk - 1) / chunk) * A.nb);
   if (grid.z > 65535 || grid.y > 65535) return cudaErrorInvalidConfiguration;
   dim3 block(TX, TY);
-  const size_t smem = sizeof(TiledShared<T>);
-  cudaError_t e = cudaFuncSetAttribute(stage_tiled_kernel<T, O, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  const size_t smem = sizeof(TiledShared<T, MAP>);
+  cudaError_t e = cudaFuncSetAttribute(stage_tiled_kernel<T, O, KIND, MAP>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  stage_tiled_kernel<T, O, KIND><<<grid, block, smem, st>>>(A, chunk, tm);
+  stage_tiled_kernel<T, O, KIND, MAP><<<grid, block, smem, st>>>(A, chunk, tm);
   return cudaGetLastError();
 }
 
 template <typename T, int KIND>
 cudaError_t launch_kind(const StageArgs<T>& A, int order, const TmaSet& tm, cudaStream_t st) {
   if (!A.sclose) return cudaErrorInvalidValue;
+  // the forward stage on a topography map: 4 metric fields (upwind orders 2, 4, 6)
+  if constexpr (KIND == 0) {
+    if (A.map == 1) {
+      switch (order) {
+        case 2: return launch_tiled_order<T, 2, 0, 1>(A, tm, st);
+        case 4: return launch_tiled_order<T, 4, 0, 1>(A, tm, st);
+        case 6: return launch_tiled_order<T, 6, 0, 1>(A, tm, st);
+        default: break;
+      }
+    }
+  }
   switch (order) {
     case 2: return launch_tiled_order<T, 2, KIND>(A, tm, st);
     case 4: return launch_tiled_order<T, 4, KIND>(A, tm, st);

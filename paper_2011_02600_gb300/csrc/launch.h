@@ -46,6 +46,13 @@ template <typename T>
 cudaError_t launch_material(const double* jmet, const double* rlm, T* met, T* mat, const Dims& d,
                             unsigned* status, cudaStream_t st);
 
+// Largest relative departure of jmet (FP64 metrics) from a topography map: over all nodes,
+// max(|a_q,y|, |a_q,z|, |a_r,x|, |a_r,z|) / |a_q,x| and |a_r,y - c a_q,x| / |a_r,y|, as the
+// bits of a non-negative double, atomically maximised into *dev (zero it first; NaN counts as
+// infinity).
+cudaError_t launch_topography_check(const double* jmet, const Dims& d, double c, unsigned long long* dev,
+                                    cudaStream_t st);
+
 // Energy: per-block FP64 partial sums into partial[0..nblocks), then a single
 // block sums them in a fixed order into *out (device).
 template <typename T>

@@ -8,13 +8,15 @@
 namespace sbp {
 
 // Tensor maps of one interior-stage launch: the state with a halo on q and r, the
-// three metric vectors (q-halo, r-halo, centre) and the coefficients (centre).
+// three metric vectors (q-halo, r-halo, centre), the coefficients (centre), and a_q,x with
+// halos on q and r (the topography-map variant's only metric read with a halo).
 struct TmaSet {
   CUtensorMap state;
   CUtensorMap met_q;
   CUtensorMap met_r;
   CUtensorMap met_s;
   CUtensorMap mat;
+  CUtensorMap met_j;
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {

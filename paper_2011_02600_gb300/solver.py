@@ -134,6 +134,14 @@ class ElasticSolver:
     def set_kernel_path(self, path):
         L.sbp_set_kernel_path(self.h, path)
 
+    def set_map_path(self, path):
+        """"auto" (the topography path where the metrics allow it) or "general"."""
+        L.sbp_set_map_path(self.h, {"auto": L.SBP_MAP_AUTO, "general": L.SBP_MAP_GENERAL}[path])
+
+    def map_path(self):
+        """The metric path of the tiled forward stage: "topography" or "general"."""
+        return "topography" if L.sbp_map_path(self.h) == L.SBP_MAP_TOPOGRAPHY else "general"
+
     # -- compute ----------------------------------------------------------------
     def rhs(self, Q=None):
         """dQ/dt (9, ns, nr, nq) of the given state (default: the current one)."""
