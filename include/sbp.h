@@ -329,6 +329,19 @@ int sbp_rhs_adjoint(SbpGrid* grid, const void* w, void* out, void* scratch, void
 int sbp_adjoint_stage(SbpGrid* grid, int32_t stage, double dt, const void* u_stage, void* ubar, void* wbar,
                       void* scratch, const double* rlmj, double* grad, void* stream);
 
+/* The adjoint of one whole step: sbp_adjoint_stage for k = 4, 3, 2, 1, 0 in one
+ * call, with the same results.  u_stages: the five forward stage inputs U_0..U_4
+ * back to back (group k, 9 B fields, at element offset k 9 B fs; device; may be
+ * NULL with grad NULL); scratch: 18 B fields (two buffers of H^-1 P~ wbar used in
+ * turn).  On the tiled kernel path the pointwise part of each stage k < 4 (wbar +
+ * B_k ubar and H^-1 P~ of it) is formed in the epilogue of stage k + 1's L^T pass
+ * instead of in a separate pass over the grid.  Between two calls the caller may
+ * add the receivers' adjoint sources to ubar (sbp_misfit); wbar carries A_0 wbar
+ * (zero for this scheme) into the next call.  Other arguments and errors as
+ * sbp_adjoint_stage. */
+int sbp_adjoint_step(SbpGrid* grid, double dt, const void* u_stages, void* ubar, void* wbar, void* scratch,
+                     const double* rlmj, double* grad, void* stream);
+
 /* Receiver misfit of the B states q (9 B fields): for member b, receiver r and
  * velocity component c, diff = v_c - data[(b n + r) 3 + c] (data: FP64 device,
  * 3 n per member); acc[(b n + r) 3 + c] += weight diff^2 / 2 (FP64 device, may

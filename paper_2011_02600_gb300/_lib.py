@@ -28,7 +28,7 @@ EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sb
             "sbp_nn_mlp_to_conv", "sbp_nn_cast_bf16", "sbp_nn_moment_combine", "sbp_selftest_wait_timeout", "sbp_last_error",
             "sbp_set_receivers_xyz", "sbp_record_receivers", "sbp_set_state", "sbp_get_state",
             "sbp_nn_set_gemm_path", "sbp_nn_status", "sbp_set_slab", "sbp_interface_trace", "sbp_set_interface",
-            "sbp_probe_fp64_rate", "sbp_set_map_path", "sbp_map_path")
+            "sbp_probe_fp64_rate", "sbp_set_map_path", "sbp_map_path", "sbp_adjoint_step")
 
 
 class SbpError(RuntimeError):
@@ -90,6 +90,7 @@ def lib(path=None):
         "sbp_energy_noalloc": [P, P, i32, i32, i32, i64, i64, i32, i32, i32, ctypes.POINTER(dbl), P],
         "sbp_rhs_adjoint": [P, P, P, P, P],
         "sbp_adjoint_stage": [P, i32, dbl, P, P, P, P, P, P, P],
+        "sbp_adjoint_step": [P, dbl, P, P, P, P, P, P, P],
         "sbp_misfit": [P, P, P, dbl, P, P, P],
         "sbp_set_batch": [P, i32],
         "sbp_nn_gemm": [i32, i32, i32, P, i64, i32, P, i64, i32, P, i64, i32, P, i32, ctypes.c_float, P],
@@ -308,6 +309,11 @@ def sbp_energy_noalloc(q, mat, nodes, ldq, fs, order, precision, nblocks, stream
 
 def sbp_rhs_adjoint(h, w, out, scratch, stream):
     _check(lib().sbp_rhs_adjoint(h, _ptr(w), _ptr(out), _ptr(scratch), stream))
+
+
+def sbp_adjoint_step(h, dt, u_stages, ubar, wbar, scratch, rlmj, grad, stream):
+    _check(lib().sbp_adjoint_step(h, dt, _ptr(u_stages), _ptr(ubar), _ptr(wbar), _ptr(scratch), _ptr(rlmj),
+                                  _ptr(grad), stream))
 
 
 def sbp_adjoint_stage(h, stage, dt, u_stage, ubar, wbar, scratch, rlmj, grad, stream):

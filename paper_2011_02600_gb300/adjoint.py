@@ -46,6 +46,9 @@ class MisfitProblem:
         elif source is not None:
             s.set_source(**source)
         self.ckpt = {}
+        # one sbp_adjoint_step per step (the stages' pointwise preps fused into the L^T passes);
+        # False: sbp_adjoint_stage five times
+        self.fused = True
 
     def _layout(self, data):
         """[nsteps][B * n_rec * 3] (member-major, as the misfit kernel reads it)."""
@@ -106,9 +109,11 @@ class MisfitProblem:
         nf = 9 * self.B
         ubar = s.new_fields(nf)
         wbar = s.new_fields(nf)
-        scratch = s.new_fields(nf)
+        scratch = s.new_fields(2 * nf)
         grad = s.new_fields(3, torch.float64)
-        stage_in = [s.new_fields(nf) for _ in range(5)]
+        stages = s.new_fields(5 * nf)          # U_0..U_4 back to back
+        g = nf * s.fs
+        stage_in = [stages[k * g:(k + 1) * g] for k in range(5)]
         starts = sorted(self.ckpt)
         for seg in reversed(starts):
             end = min(seg + self.C, self.nsteps)
@@ -124,8 +129,12 @@ class MisfitProblem:
                     stage_in[k].copy_(s.qbuf[s.current])
                     L.sbp_rk_stage(s.h, k, self.dt, st)
                 wbar.zero_()
-                for k in reversed(range(5)):
-                    L.sbp_adjoint_stage(s.h, k, self.dt, stage_in[k], ubar, wbar, scratch, self.rlmj, grad, st)
+                if self.fused:
+                    L.sbp_adjoint_step(s.h, self.dt, stages, ubar, wbar, scratch, self.rlmj, grad, st)
+                else:
+                    for k in reversed(range(5)):
+                        L.sbp_adjoint_stage(s.h, k, self.dt, stage_in[k], ubar, wbar, scratch, self.rlmj, grad,
+                                            st)
             del states
         return s.view(grad, 3).clone()
 

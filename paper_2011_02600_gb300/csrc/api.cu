@@ -476,6 +476,62 @@ int adjoint_impl(SbpGrid* g, int mode, int stage, double dt, const void* u, void
   return SBP_OK;
 }
 
+// One whole adjoint step (stages 4..0) on the tiled kernel, the prep of each stage k < 4 fused
+// into the L^T pass of stage k + 1 (pointwise there); scratch holds two yhat buffers used in turn.
+template <typename T>
+int adjoint_step_impl(SbpGrid* g, double dt, const void* u5, void* ubar, void* wbar, void* scratch,
+                      const double* rlmj, double* grad, cudaStream_t st) {
+  const long long grp = 9LL * g->nb * g->dims.fs;  // elements of one group of B states
+  T* y[2] = {(T*)scratch, (T*)scratch + grp};
+  for (int k = 4; k >= 0; --k) {
+    TimedLaunch ta(g, 2, st);
+    T* yc = y[(4 - k) & 1];
+    if (k == 4) {
+      // the prep of stage 4 on its own: Ub_5 holds the step's receiver sources
+      sbp::AdjArgs<T> A{};
+      A.nb = g->nb;
+      A.bstride = 9 * g->dims.fs;
+      A.ubar_next = (const T*)ubar;
+      A.ubar_out = (T*)ubar;
+      A.wbar_in = (const T*)wbar;
+      A.wbar = (T*)wbar;
+      A.yhat = yc;
+      A.mat = (const T*)g->mat;
+      A.d = g->dims;
+      A.rk_b = (T)kRkB[4];
+      A.mode = 1;
+      sbp::StageArgs<T> S = make_args<T>(g, nullptr, nullptr, 0, 0, 0, 0);
+      for (int x = 0; x < 3; ++x) A.inv_h[x] = S.inv_h[x];
+      cudaError_t e = sbp::launch_adjoint_prep<T>(A, g->desc.order, st);
+      if (e != cudaSuccess) return cuda_fail(e, "adjoint prep");
+    }
+    sbp::StageArgs<T> S2 = make_args<T>(g, nullptr, nullptr, sbp::kModeStage, kRkA[k], 0.0, dt, g->nb);
+    S2.ubar_next = (const T*)ubar;
+    S2.ubar_out = (T*)ubar;
+    S2.wbar = (T*)wbar;
+    S2.yhat = yc;
+    S2.rlmj = rlmj;
+    S2.grad = grad;
+    if (grad) {
+      const T* uk = (const T*)u5 + k * grp;
+      const sbp::TmaSet* tu = nullptr;
+      if (int rc = cached_maps(g, uk, &tu)) return rc;
+      S2.q = uk;
+      cudaError_t e = sbp::launch_adjoint_tiled<T>(S2, g->desc.order, 2, *tu, st);
+      if (e != cudaSuccess) return cuda_fail(e, "adjoint gradient (tiled)");
+    }
+    const sbp::TmaSet* ty = nullptr;
+    if (int rc = cached_maps(g, yc, &ty)) return rc;
+    S2.q = yc;
+    S2.yhat_next = k > 0 ? y[(5 - k) & 1] : nullptr;
+    S2.rk_b_next = k > 0 ? (T)kRkB[k - 1] : T(0);
+    cudaError_t e = sbp::launch_adjoint_tiled<T>(S2, g->desc.order, 1, *ty, st);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint (tiled)");
+    ta.done();
+  }
+  return SBP_OK;
+}
+
 // Copy the 9 B state fields between the bound buffer dev (grid layout) and a caller buffer
 // ext: host or device memory (SBP_MEM_HOST), in the grid layout (9 B fields of fs elements) or
 // packed [field][s][r][q] (SBP_LAYOUT_DENSE).  A copy to host memory synchronises the stream.
@@ -1097,6 +1153,32 @@ int sbp_adjoint_stage(SbpGrid* g, int32_t stage, double dt, const void* u_stage,
                                             (cudaStream_t)stream)
                       : adjoint_impl<double>(g, 1, stage, dt, u_stage, ubar, wbar, wbar, scratch, rlmj, grad,
                                              (cudaStream_t)stream);
+}
+
+int sbp_adjoint_step(SbpGrid* g, double dt, const void* u_stages, void* ubar, void* wbar, void* scratch,
+                     const double* rlmj, double* grad, void* stream) {
+  if (int rc = check_ready(g)) return rc;
+  if (!op_info(g->desc.order).adjoint) return fail(SBP_ERR_UNSUPPORTED, "the adjoint is built for orders 2, 4, 6");
+  if (g->slab.ns_global > 0) return fail(SBP_ERR_UNSUPPORTED, "the adjoint on slab grids is not built");
+  if (has_interface(g)) return fail(SBP_ERR_UNSUPPORTED, "the adjoint with interface faces is not built");
+  if (!g->material) return fail(SBP_ERR_STATE, "material not set (sbp_set_material)");
+  if (!(dt > 0) || !isfinite(dt)) return fail(SBP_ERR_ARG, "dt must be positive and finite");
+  if (!ubar || !wbar || !scratch) return fail(SBP_ERR_ARG, "null adjoint buffer");
+  if (grad && (!u_stages || !rlmj)) return fail(SBP_ERR_ARG, "the gradient needs the stage states and rho, lambda, mu, J");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!g->use_tiled) {
+    // the general kernels: the five stages one by one
+    const long long grp = 9LL * g->nb * g->dims.fs * g->elem;  // bytes of one group of B states
+    for (int k = 4; k >= 0; --k) {
+      const void* uk = u_stages ? (const char*)u_stages + k * grp : nullptr;
+      const int rc = g->elem == 4 ? adjoint_impl<float>(g, 1, k, dt, uk, ubar, wbar, wbar, scratch, rlmj, grad, st)
+                                  : adjoint_impl<double>(g, 1, k, dt, uk, ubar, wbar, wbar, scratch, rlmj, grad, st);
+      if (rc) return rc;
+    }
+    return SBP_OK;
+  }
+  return g->elem == 4 ? adjoint_step_impl<float>(g, dt, u_stages, ubar, wbar, scratch, rlmj, grad, st)
+                      : adjoint_step_impl<double>(g, dt, u_stages, ubar, wbar, scratch, rlmj, grad, st);
 }
 
 int sbp_misfit(SbpGrid* g, const void* q, const double* data, double weight, double* acc, void* ubar, void* stream) {

@@ -85,6 +85,9 @@ struct StageArgs {
   double* grad;         // gradient accumulators (FP64, 3 fields)
   SlabS slab;           // s-slab of a decomposed block (default: the whole block)
   IfaceArgs<T> ifc;     // the other blocks' traces at interface faces (none by default)
+  T* yhat_next;         // L^T pass of stage k > 0 in an adjoint step: where the fused prep of stage
+                        // k - 1 writes yhat_{k-1} (null: no fusion, Wb <- A_k Wb_k)
+  T rk_b_next;          // B_{k-1} of that fused prep
   int map;              // 1: topography map (a_q = (a_q,x, 0, 0), a_r = (0, ar_ratio a_q,x, 0)); 0: general
   T ar_ratio;           // a_r,y / a_q,x of a topography map (L_x / L_y)
 };

@@ -173,7 +173,6 @@ __device__ __forceinline__ void issue_plane(TiledShared<T, MAP>& S, int stage, c
 template <typename T, int O, int KIND, int MAP>
 __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
     stage_tiled_kernel(StageArgs<T> A, int chunk, const __grid_constant__ TmaSet tm) {
-  static_assert(MAP == 0 || KIND == 0, "the adjoint passes read the general metrics");
   using C = OpCoef<O>;
   constexpr int R = C::r;    // D+ reaches -R..+Q, D- reaches -Q..+R
   constexpr int Q = C::q;
@@ -524,12 +523,30 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
         if (A.mode == kModeRhs) {
 #pragma unroll
           for (int f = 0; f < 9; ++f) fldw(ub_out, f)[off] = m9[f];
-        } else {
+        } else if (!A.yhat_next) {
 #pragma unroll
           for (int f = 0; f < 9; ++f) {
             fldw(ub_out, f)[off] = dqi[f] + A.dt * m9[f];
             fldw(wbm, f)[off] = A.rk_a * pre[f];
           }
+        } else {
+          // and the prep of stage k - 1, pointwise at this node: Wb_{k-1} = A_k Wb_k + B_{k-1} Ub_k,
+          // yhat_{k-1} = H^-1 P~ Wb_{k-1} (1/H without a division)
+          T w[9];
+#pragma unroll
+          for (int f = 0; f < 9; ++f) {
+            const T ub = dqi[f] + A.dt * m9[f];
+            fldw(ub_out, f)[off] = ub;
+            w[f] = A.rk_a * pre[f] + A.rk_b_next * ub;
+            fldw(wbm, f)[off] = w[f];
+          }
+          T y[9];
+          apply_P(w, w + 3, irhoJ, lamJ, muJ, y);
+          const T ih = norm_weight_inv_t<T, O>(i, d.nq) * A.inv_h[0] * norm_weight_inv_t<T, O>(j, d.nr) * A.inv_h[1] *
+                       norm_weight_inv_t<T, O>(k, d.ns) * A.inv_h[2];
+          T* yn = A.yhat_next + boff;
+#pragma unroll
+          for (int f = 0; f < 9; ++f) fldw(yn, f)[off] = y[f] * ih;
         }
       } else {
         // dt Wb_k . d(P~ M U_k)/d(rho, lambda, mu) at the node
@@ -619,15 +636,13 @@ cudaError_t launch_tiled_order(const StageArgs<T>& A, const TmaSet& tm, cudaStre
 template <typename T, int KIND>
 cudaError_t launch_kind(const StageArgs<T>& A, int order, const TmaSet& tm, cudaStream_t st) {
   if (!A.sclose) return cudaErrorInvalidValue;
-  // the forward stage on a topography map: 4 metric fields (upwind orders 2, 4, 6)
-  if constexpr (KIND == 0) {
-    if (A.map == 1) {
-      switch (order) {
-        case 2: return launch_tiled_order<T, 2, 0, 1>(A, tm, st);
-        case 4: return launch_tiled_order<T, 4, 0, 1>(A, tm, st);
-        case 6: return launch_tiled_order<T, 6, 0, 1>(A, tm, st);
-        default: break;
-      }
+  // the stage and the adjoint passes on a topography map: 4 metric fields (upwind orders 2, 4, 6)
+  if (A.map == 1) {
+    switch (order) {
+      case 2: return launch_tiled_order<T, 2, KIND, 1>(A, tm, st);
+      case 4: return launch_tiled_order<T, 4, KIND, 1>(A, tm, st);
+      case 6: return launch_tiled_order<T, 6, KIND, 1>(A, tm, st);
+      default: break;
     }
   }
   switch (order) {

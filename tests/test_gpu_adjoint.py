@@ -282,3 +282,22 @@ def test_batched_gradient_against_finite_differences():
         got = float(sum(np.sum(g[f] * dm[f]) for f in range(3)))
         worst = max(worst, abs(got - fd) / abs(fd))
     assert worst < 1e-5, worst
+
+
+@pytest.mark.parametrize("order,nodes", [(2, (21, 18, 16)), (4, (40, 19, 30)), (6, (36, 30, 27))])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_fused_adjoint_step_matches_stage_by_stage(order, nodes, prec):
+    """sbp_adjoint_step (each stage's pointwise prep formed in the previous stage's L^T pass)
+    against five sbp_adjoint_stage calls per step: the whole misfit gradient, and Ub at the end."""
+    c = _misfit_case(nsteps=8, order=order, nodes=nodes)
+    grads = []
+    for fused in (True, False):
+        p = _gpu_problem(c, prec)
+        p.fused = fused
+        _set(p, c["mat"])
+        p.forward()
+        grads.append(p.gradient().double().cpu().numpy())
+    for f in range(3):
+        sc = np.abs(grads[1][f]).max()
+        assert sc > 0
+        assert np.abs(grads[0][f] - grads[1][f]).max() < (1e-12 if prec == 64 else 1e-5) * sc, f

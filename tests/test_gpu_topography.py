@@ -84,3 +84,44 @@ def test_path_not_chosen_off_topography_maps():
     u.set_kernel_path(0)
     u.set_map_path("general")
     assert u.map_path() == "general"
+
+
+@pytest.mark.parametrize("order,nodes", [(4, (45, 33, 30)), (6, (40, 27, 31)), (2, (35, 20, 18))])
+@pytest.mark.parametrize("precision", [64, 32])
+def test_adjoint_passes_on_topography_path(order, nodes, precision):
+    """The adjoint's tiled passes on the topography path against the general path: L^T w
+    (sbp_rhs_adjoint) and one adjoint stage with its material gradient (sbp_adjoint_stage)."""
+    from paper_2011_02600_gb300 import _lib as L
+    from paper_2011_02600_gb300.solver import _stream
+    from paper_2011_02600_gb300.workload_setup import build_solver
+    from workloads.fields import random_state
+    cfg = dataclasses.replace(config_by_name("adjoint129_o4"), nodes=nodes, order=order)
+    s, info = build_solver(cfg, precision=precision, keep_metrics=True)
+    assert s.map_path() == "topography"
+    st = _stream()
+    rlmj = s.new_fields(4, torch.float64)
+    r = s.view(rlmj, 4)
+    J = s.view(s.jmet, 10)[0]
+    mat = s.view(s.mat, 3).double()
+    r[3].copy_(J)
+    r[0].copy_(1.0 / (mat[0] * J))
+    r[1].copy_(mat[1] * J)
+    r[2].copy_(mat[2] * J)
+    y = s.to_layout(torch.from_numpy(random_state(nodes, 71, 1.0e-6, 1.0)), s.dtype)
+    u = s.to_layout(torch.from_numpy(random_state(nodes, 72, 1.0, 1.0e6)), s.dtype)
+    ub0 = s.to_layout(torch.from_numpy(random_state(nodes, 73, 1.0e-6, 1.0)), s.dtype)
+    wb0 = s.to_layout(torch.from_numpy(random_state(nodes, 74, 1.0e-6, 1.0)), s.dtype)
+    out = {}
+    for path in ("auto", "general"):
+        s.set_map_path(path)
+        lt, scratch = s.new_fields(9), s.new_fields(9)
+        L.sbp_rhs_adjoint(s.h, y, lt, scratch, st)
+        ub, wb, grad = ub0.clone(), wb0.clone(), s.new_fields(3, torch.float64)
+        L.sbp_adjoint_stage(s.h, 2, info["dt"], u, ub, wb, scratch, rlmj, grad, st)
+        torch.cuda.synchronize()
+        out[path] = [s.view(x, n).double().cpu().numpy() for x, n in ((lt, 9), (ub, 9), (wb, 9), (grad, 3))]
+    tol = 1e-12 if precision == 64 else 1e-5
+    for a, b in zip(out["auto"], out["general"]):
+        scale = np.abs(b).max(axis=(1, 2, 3))
+        assert scale.min() > 0
+        assert (np.abs(a - b).max(axis=(1, 2, 3)) / scale).max() < tol
