@@ -288,6 +288,7 @@ int sbp_set_interface(SbpGrid* grid, int32_t face, const void* other_trace);
 /* Memory and layout flags of the copy calls below. */
 #define SBP_MEM_HOST 1      /* the caller's buffer is host memory (pageable or pinned); else device */
 #define SBP_LAYOUT_DENSE 2  /* fields packed [field][s][r][q] without padding; else the grid layout */
+#define SBP_MEM_ASYNC 4     /* sbp_get_state to host memory: enqueue only, do not wait for the copy */
 
 /* Copy the recorded traces (B*n*3*n_t elements of the solver precision,
  * trace[b][r][c][step], steps not yet recorded hold zeros) to dst: host memory
@@ -299,9 +300,11 @@ int sbp_record_receivers(SbpGrid* grid, void* dst, int32_t flags, void* stream);
  * src/dst in host (SBP_MEM_HOST) or device memory, in the grid layout (9 B
  * fields of fs elements, padding included) or packed [b*9 + field][s][r][q]
  * (SBP_LAYOUT_DENSE).  Both are enqueued on the stream; a download to host
- * memory synchronises the stream before returning; an upload from pinned host
- * memory is asynchronous, so the buffer must stay unchanged until the stream
- * has passed the copy.  The Runge-Kutta register needs no reset: a step's first
+ * memory synchronises the stream before returning unless flags include
+ * SBP_MEM_ASYNC (then dst holds the state once the stream has passed the copy:
+ * pinned dst, and the caller synchronises, e.g. to overlap the download with
+ * another grid's work); an upload from pinned host memory is asynchronous, so
+ * the buffer must stay unchanged until the stream has passed the copy.  The Runge-Kutta register needs no reset: a step's first
  * stage does not read it. */
 int sbp_set_state(SbpGrid* grid, const void* src, int32_t flags, void* stream);
 int sbp_get_state(SbpGrid* grid, void* dst, int32_t flags, void* stream);

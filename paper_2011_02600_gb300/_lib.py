@@ -15,6 +15,7 @@ SBP_BC_INTERFACE = 2
 SBP_TRADITIONAL = 100
 SBP_MEM_HOST = 1
 SBP_LAYOUT_DENSE = 2
+SBP_MEM_ASYNC = 4
 SBP_MAP_AUTO, SBP_MAP_GENERAL, SBP_MAP_TOPOGRAPHY = 0, 1, 2
 ERRORS = {1: "ARG", 2: "UNSUPPORTED", 3: "CUDA", 4: "NONFINITE", 5: "STATE", 6: "MESH"}
 

@@ -556,7 +556,7 @@ int copy_state(SbpGrid* g, void* dev, const void* ext, int flags, bool in, cudaS
                : cudaMemcpy2DAsync(x, row, d, pitch, row, rows, kind, st);
     }
   }
-  if (err == cudaSuccess && host && !in) err = cudaStreamSynchronize(st);
+  if (err == cudaSuccess && host && !in && !(flags & SBP_MEM_ASYNC)) err = cudaStreamSynchronize(st);
   return err == cudaSuccess ? SBP_OK : cuda_fail(err, in ? "state upload" : "state download");
 }
 
@@ -1120,7 +1120,7 @@ int sbp_set_state(SbpGrid* g, const void* src, int32_t flags, void* stream) {
 int sbp_get_state(SbpGrid* g, void* dst, int32_t flags, void* stream) {
   if (int rc = check_ready(g)) return rc;
   if (!dst) return fail(SBP_ERR_ARG, "null destination");
-  if (flags & ~(SBP_MEM_HOST | SBP_LAYOUT_DENSE)) return fail(SBP_ERR_ARG, "unknown flags");
+  if (flags & ~(SBP_MEM_HOST | SBP_LAYOUT_DENSE | SBP_MEM_ASYNC)) return fail(SBP_ERR_ARG, "unknown flags");
   return copy_state(g, g->q[g->cur], dst, flags, false, (cudaStream_t)stream);
 }
 

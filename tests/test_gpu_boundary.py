@@ -60,6 +60,11 @@ def test_state_upload_download_round_trip(prec):
     s.step(2, 1e-4)
     got = torch.zeros(18 * s.fs, dtype=s.dtype).pin_memory()
     L.sbp_get_state(s.h, got, L.SBP_MEM_HOST, _stream())
+    # the same download enqueued without waiting (SBP_MEM_ASYNC), read after a synchronisation
+    got_async = torch.zeros(18 * s.fs, dtype=s.dtype).pin_memory()
+    L.sbp_get_state(s.h, got_async, L.SBP_MEM_HOST | L.SBP_MEM_ASYNC, _stream())
+    torch.cuda.synchronize()
+    assert torch.equal(got_async, got)
     s2, _, _ = _setup(nodes, 4, prec, batch=2)
     s2.qbuf[0].copy_(flat.cuda())
     s2.step(2, 1e-4)
@@ -73,7 +78,8 @@ def test_copy_calls_reject_bad_arguments():
     buf = np.zeros(9 * 20 ** 3, dtype=np.float32)
     for fn, args, code in [(L.sbp_set_state, (None, 3, _stream()), 1),
                            (L.sbp_set_state, (buf, 8, _stream()), 1),
-                           (L.sbp_get_state, (buf, 5, _stream()), 1),
+                           (L.sbp_set_state, (buf, L.SBP_MEM_ASYNC, _stream()), 1),
+                           (L.sbp_get_state, (buf, 8, _stream()), 1),
                            (L.sbp_record_receivers, (buf, 1, _stream()), 5)]:
         with pytest.raises(L.SbpError) as e:
             fn(s.h, *args)
