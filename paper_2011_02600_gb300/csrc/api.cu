@@ -325,6 +325,7 @@ int encode_maps(const SbpGrid* g, const void* q, int nb, sbp::TmaSet* out) {
   if (!rc) rc = one(&out->met_s, g->met, 9, 32, 8, 3);
   if (!rc) rc = one(&out->mat, g->mat, 3, 32, 8, 3);
   if (!rc) rc = one(&out->met_j, g->met, 9, 40, 16, 1);
+  if (!rc) rc = one(&out->dq, g->dq, 9 * g->nb, 32, 8, 9);
   return rc;
 }
 

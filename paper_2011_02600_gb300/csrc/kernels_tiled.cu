@@ -58,6 +58,7 @@ struct Stage<T, 1> {
   T jq[BYH][BXH];  // a_q,x on the tile and both halos
   T as[3][TY][TX];
   T mat[3][TY][TX];
+  T dq[9][TY][TX];  // the RK register (stages 1-4 of the forward step; its last member)
 };
 
 // a_q at flux-tile row `row` (0..TY-1), smem column `col` (0..BXH-1); a_r at r-halo row `row`
@@ -88,6 +89,16 @@ __device__ __forceinline__ void ar_at(const Stage<T, 1>& st, int row, int col, T
   a[0] = T(0);
   a[1] = c_r * st.jq[row][HX + col];
   a[2] = T(0);
+}
+
+// The RK register at the thread's node from the tile copy (MAP 1 only).
+template <typename T>
+__device__ __forceinline__ T dq_at(const Stage<T, 0>&, int, int, int) {
+  return T(0);
+}
+template <typename T>
+__device__ __forceinline__ T dq_at(const Stage<T, 1>& st, int f, int ty, int tx) {
+  return st.dq[f][ty][tx];
 }
 
 // Fluxes F_q = sigma a_q, F_r = sigma a_r and the strain rows of one axis; MAP 1 skips the
@@ -150,12 +161,20 @@ struct TiledShared {
 template <typename T>
 constexpr int tiled_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
 
+// with_dq (MAP 1): the RK register's box comes with the plane (the last member of Stage<T, 1>).
 template <typename T, int MAP>
 __device__ __forceinline__ void issue_plane(TiledShared<T, MAP>& S, int stage, const TmaSet& tm, int i0, int j0,
-                                            int k, int member) {
+                                            int k, int member, bool with_dq) {
   unsigned long long* bar = &S.bar[stage];
-  mbar_expect_tx(bar, (unsigned)sizeof(Stage<T, MAP>));
   Stage<T, MAP>& st = S.st[stage];
+  if constexpr (MAP == 1) {
+    constexpr unsigned dq_bytes = (unsigned)sizeof(st.dq);
+    mbar_expect_tx(bar, (unsigned)sizeof(Stage<T, MAP>) - (with_dq ? 0u : dq_bytes));
+    if (with_dq) tma_load_4d(&st.dq[0][0][0], &tm.dq, i0, j0, k, 9 * member, bar);
+  } else {
+    (void)with_dq;
+    mbar_expect_tx(bar, (unsigned)sizeof(Stage<T, MAP>));
+  }
   tma_load_4d(&st.state[0][0][0], &tm.state, i0 - HX, j0 - HX, k, 9 * member, bar);
   if constexpr (MAP == 1) {
     tma_load_4d(&st.jq[0][0], &tm.met_j, i0 - HX, j0 - HX, k, 0, bar);
@@ -233,7 +252,10 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
   }
   if (q_edge && ty == 0) fill_q_rows<T, O>(S.qrows, tx, i0, ax.own0, ax.own1, d.nq);  // read after the first plane's barrier
   __syncthreads();
-  if (tid == 0) issue_plane(S, 0, tm, i0, j0, kb, member);
+  // the topography-map variant's stages read the RK register from the tile copy
+  constexpr bool kDqTile = MAP == 1 && KIND == 0;
+  const bool dq_tma = kDqTile && A.mode == kModeStage;
+  if (tid == 0) issue_plane(S, 0, tm, i0, j0, kb, member, dq_tma);
   // closure-row sums of the s closure planes this chunk reaches (while the first copy flies)
   if (active && face_lo && kb < BC) s_closure_sums<T, O, false>(q, met, d, col, scl);
   if (active && face_hi && ke > d.ns - BC) s_closure_sums<T, O, true>(q, met, d, col, scl);
@@ -284,7 +306,7 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
     // Wb_k (L^T pass), Wb_k, rho and J (gradient pass)
     T dqi[9], pre[9];
     double rj[2];
-    if (KIND == 0 && A.mode == kModeStage) {
+    if (KIND == 0 && !kDqTile && A.mode == kModeStage) {
 #pragma unroll
       for (int c = 0; c < 9; ++c) dqi[c] = ld_stream(fld(dqm, c), off);
     }
@@ -344,7 +366,7 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
     }
     if (tid == 0 && k + 1 < ke) {
       fence_proxy_async_smem();
-      issue_plane(S, sidx ^ 1, tm, i0, j0, k + 1, member);
+      issue_plane(S, sidx ^ 1, tm, i0, j0, k + 1, member, dq_tma);
     }
 
     T rv[3] = {T(0), T(0), T(0)};
@@ -482,7 +504,12 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
 #pragma unroll
         for (int f = 0; f < 9; ++f) {
           T dn = A.dt * dd[f];
-          if (A.mode == kModeStage) dn += A.rk_a * dqi[f];
+          if (A.mode == kModeStage) {
+            if constexpr (kDqTile)
+              dn += A.rk_a * dq_at(st, f, ty, tx);
+            else
+              dn += A.rk_a * dqi[f];
+          }
           __stcs(fldw(dqm, f) + off, dn);                    // read again one stage later
           __stcs(fldw(qout, f) + off, qc[f] + A.rk_b * dn);
         }

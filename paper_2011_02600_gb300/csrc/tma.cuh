@@ -17,6 +17,7 @@ struct TmaSet {
   CUtensorMap met_s;
   CUtensorMap mat;
   CUtensorMap met_j;
+  CUtensorMap dq;  // the Runge-Kutta register (centre; the topography-map variant's stages)
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
