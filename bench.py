@@ -579,8 +579,8 @@ def main():
 
     # end to end through the C ABI: per step, a state uploaded from pinned host memory
     # (sbp_set_state), one RK step (sbp_step_n), the state downloaded to pinned host memory
-    # (sbp_get_state).  Two grids on two streams take the steps in turn, so that one grid's
-    # download, the other's upload and a step overlap (independent problems streamed through
+    # (sbp_get_state).  Two or three grids on as many streams take the steps in turn, so that one
+    # grid's download, another's upload and a step overlap (independent problems streamed through
     # the device); every step still moves its whole state in and out.  The same sequence on one
     # grid, each download waited for, is reported beside it.
     e2e = None
@@ -588,8 +588,8 @@ def main():
     nbytes = 9 * s.fs * elem
     try:
         tdt = torch.float32 if elem == 4 else torch.float64
-        host_in = [torch.empty(9 * s.fs, dtype=tdt, pin_memory=True) for _ in range(2)]
-        host_out = [torch.empty(9 * s.fs, dtype=tdt, pin_memory=True) for _ in range(2)]
+        host_in = [torch.empty(9 * s.fs, dtype=tdt, pin_memory=True)]
+        host_out = [torch.empty(9 * s.fs, dtype=tdt, pin_memory=True)]
         for b in host_in + host_out:
             L.sbp_get_state(h, b, L.SBP_MEM_HOST, _stream())
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
@@ -602,14 +602,36 @@ def main():
         ev[1].record(stream)
         torch.cuda.synchronize()
         seq_ms = ev[0].elapsed_time(ev[1]) / args.e2e_steps
-        free, _total = torch.cuda.mem_get_info()
+        # as many grids as fit (up to three): each stream's chain (upload, step, download) then
+        # spans as many steps, and the copy engines and the SMs stay busy
+        extra = []
         footprint = (39 * s.fs + 2 * 9 * s.fs) * elem      # a grid's fields and its set-up buffers
-        if free < 1.2 * footprint:
+        while len(extra) < 2:
+            free, _total = torch.cuda.mem_get_info()
+            if free < 1.2 * footprint:
+                break
+            try:   # host memory for two more pinned state buffers, with room to spare
+                if os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") < 3 * 2 * nbytes:
+                    break
+            except (ValueError, OSError):
+                pass
+            try:
+                nb_in = torch.empty(9 * s.fs, dtype=tdt, pin_memory=True)
+                nb_out = torch.empty(9 * s.fs, dtype=tdt, pin_memory=True)
+            except Exception:
+                break
+            g2, _ = build_solver(cfg, precision=args.precision, device=f"cuda:{local}")
+            L.sbp_get_state(g2.h, nb_in, L.SBP_MEM_HOST, _stream())
+            L.sbp_get_state(g2.h, nb_out, L.SBP_MEM_HOST, _stream())
+            extra.append(g2)
+            host_in.append(nb_in)
+            host_out.append(nb_out)
+        if not extra:
             raise RuntimeError(f"no room for a second grid ({free / 1e9:.0f} GB free): sequential only")
-        s2, _ = build_solver(cfg, precision=args.precision, device=f"cuda:{local}")
-        grids = [h, s2.h]
-        streams = [torch.cuda.Stream(), torch.cuda.Stream()]
-        nsteps = max(2, 2 * args.e2e_steps)
+        grids = [h] + [g2.h for g2 in extra]
+        ng = len(grids)
+        streams = [torch.cuda.Stream() for _ in range(ng)]
+        nsteps = max(ng, ng * args.e2e_steps)
 
         def pipelined():
             start = torch.cuda.Event()
@@ -617,17 +639,17 @@ def main():
             for st_ in streams:
                 st_.wait_event(start)
             for n in range(nsteps):
-                g, st_ = grids[n % 2], streams[n % 2]
+                g, st_ = grids[n % ng], streams[n % ng]
                 sp = st_.cuda_stream
-                L.sbp_set_state(g, host_in[n % 2], L.SBP_MEM_HOST, sp)
+                L.sbp_set_state(g, host_in[n % ng], L.SBP_MEM_HOST, sp)
                 L.sbp_step_n(g, 1, dt, sp)
-                L.sbp_get_state(g, host_out[n % 2], L.SBP_MEM_HOST | L.SBP_MEM_ASYNC, sp)
+                L.sbp_get_state(g, host_out[n % ng], L.SBP_MEM_HOST | L.SBP_MEM_ASYNC, sp)
             for st_ in streams:
                 done = torch.cuda.Event()
                 done.record(st_)
                 stream.wait_event(done)
 
-        pipelined()  # warm-up of the second grid
+        pipelined()  # warm-up of the added grids
         torch.cuda.synchronize()
         ev[0].record(stream)
         pipelined()
@@ -635,14 +657,14 @@ def main():
         torch.cuda.synchronize()
         e_ms = ev[0].elapsed_time(ev[1]) / nsteps
         e2e = {"value": nodes * 5 / (e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "ms_per_step": e_ms, "steps": nsteps,
+               "d2h_bytes_per_step": nbytes, "ms_per_step": e_ms, "steps": nsteps, "grids": ng,
                "what": "per step, all through the C ABI: sbp_set_state from pinned host memory (the 9-field "
-                       "state in the grid layout), sbp_step_n(1), sbp_get_state to pinned host memory; two grids "
-                       "on two streams take the steps in turn (one grid's download, the other's upload and a "
+                       f"state in the grid layout), sbp_step_n(1), sbp_get_state to pinned host memory; {ng} grids "
+                       f"on {ng} streams take the steps in turn (one grid's download, another's upload and a "
                        "step overlap)",
                "sequential_one_grid": {"value": nodes * 5 / (seq_ms / 1e3) / 1e6, "ms_per_step": seq_ms,
                                        "steps": args.e2e_steps}}
-        del host_in, host_out, s2
+        del host_in, host_out, extra
     except Exception as ex:  # pinned memory or a second grid's device memory can be unavailable
         if seq_ms is not None:
             e2e = {"value": nodes * 5 / (seq_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,

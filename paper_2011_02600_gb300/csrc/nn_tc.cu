@@ -124,17 +124,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Work item w (of tm x tn x splits): m tiles fastest, so that the CTAs running at the same time
-// share their B tiles (the larger operand) through L2.
+// Work item w (of tm x tn x splits).  m tiles fastest: the CTAs running at the same time share
+// their B tiles (the larger operand) through L2, which suits a B larger than L2.  n tiles fastest
+// (n_fast): one wave of CTAs reads every B tile once, from DRAM, and the later waves (the other m
+// tiles) find B in L2 at L2 latency instead of all waiting together on the same DRAM reads.
 struct Item {
   int m0, n0, kb, ke;
 };
-__device__ __forceinline__ Item item(int w, int tm, int tn, int k_per, int K) {
+__device__ __forceinline__ Item item(int w, int tm, int tn, int k_per, int K, int n_fast) {
   Item it;
   const int per = tm * tn;
   const int z = w / per, r = w % per;
-  it.m0 = (r % tm) * BM;
-  it.n0 = (r / tm) * BN;
+  it.m0 = (n_fast ? r / tn : r % tm) * BM;
+  it.n0 = (n_fast ? r % tn : r / tm) * BN;
   it.kb = z * k_per;
   it.ke = min(K, it.kb + k_per);
   return it;
@@ -146,7 +148,7 @@ template <bool A_MN, bool B_MN>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ Maps maps, int M, int N, int K, int k_per, int tm, int tn, int items,
                    void* C, long long ldc, int c_bf16, const float* __restrict__ bias, int relu, float beta,
-                   int epi_mode) {
+                   int epi_mode, int n_fast) {
   extern __shared__ unsigned char smem_raw[];
   // stages at the first 1 KB boundary (the swizzle pattern repeats every 1 KB), then the
   // epilogue warps' transpose tiles, then the barriers
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       // producer: TMA loads of every K slice of every item, through the ring of stages
       int it = 0;
       for (int w = blockIdx.x; w < items && !*(volatile int*)fail; w += gridDim.x) {
-        const Item I = item(w, tm, tn, k_per, K);
+        const Item I = item(w, tm, tn, k_per, K, n_fast);
         const int nk = (I.ke - I.kb + BK - 1) / BK;
         for (int kt = 0; kt < nk; ++kt, ++it) {
           const int s = it % STAGES, use = it / STAGES;
@@ -224,7 +226,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       constexpr uint32_t idesc = sbp_umma::instr_desc_bf16_f32(BM, BN, A_MN, B_MN);
       int it = 0, t = 0;
       for (int w = blockIdx.x; w < items && !*(volatile int*)fail; w += gridDim.x, ++t) {
-        const Item I = item(w, tm, tn, k_per, K);
+        const Item I = item(w, tm, tn, k_per, K, n_fast);
         const int nk = (I.ke - I.kb + BK - 1) / BK;
         const int buf = t & 1, ause = t >> 1;
         if (ause > 0 && !wait(&acc_empty[buf], (ause - 1) & 1)) {
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const bool tma = epi_mode != kEpiDirect;
     int t = 0, chunks_stored = 0;
     for (int w = blockIdx.x; w < items; w += gridDim.x, ++t) {
-      const Item I = item(w, tm, tn, k_per, K);
+      const Item I = item(w, tm, tn, k_per, K, n_fast);
       const int buf = t & 1, use = t >> 1;
       const bool got = wait(&acc_full[buf], use & 1);
       if (!__all_sync(0xffffffffu, got)) {
@@ -459,6 +461,9 @@ cudaError_t launch_gemm_tc(int M, int N, int K, const void* A, long long lda, in
                  : cudaMemset2DAsync(C, sizeof(float) * (size_t)ldc, 0, sizeof(float) * (size_t)N, (size_t)M, st);
     if (e != cudaSuccess) return e;
   }
+  // n tiles fastest when B fits in L2 with room to spare (a third of GB300's 126 MB)
+  constexpr double kL2Bytes = 126.0e6;
+  const int n_fast = (double)K * N * 2.0 <= kL2Bytes / 3.0 ? 1 : 0;
   // persistent: one CTA per SM (its shared memory and tensor memory fill the SM)
   const unsigned grid = (unsigned)(items < sms ? items : sms);
   // the shared-memory attribute belongs to the device: set once per device and kernel variant
@@ -477,7 +482,7 @@ cudaError_t launch_gemm_tc(int M, int N, int K, const void* A, long long lda, in
       }
     }
     kern<<<grid, THREADS, SMEM_BYTES, st>>>(maps, M, N, K, k_per, tm, tn, (int)items, C, ldc, c_bf16, bias, relu,
-                                           beta, epi_mode);
+                                           beta, epi_mode, n_fast);
     return cudaGetLastError();
   };
   const bool a_mn = ta != 0, b_mn = tb == 0;
