@@ -459,6 +459,14 @@ int sbp_nn_moment_combine(const float* G, const float* m, float* y, const void* 
 /* y = BF16(x). */
 int sbp_nn_cast_bf16(const float* x, void* y, int64_t n, void* stream);
 
+/* Fourier features of the network's input (not part of the paper: the standard input
+ * encoding of coordinate networks, for the surrogate's source-position input):
+ * x FP32 [n_in][B] (normalised to [-1, 1]) -> y BF16 [n_in (1 + 2 L)][B]: rows
+ * 0..n_in-1 are x, then for input i and k = 0..L-1 the rows n_in + 2 (i L + k) and
+ * n_in + 2 (i L + k) + 1 hold sin(2^k pi x_i) and cos(2^k pi x_i).  L in 0..16
+ * (L = 0: the cast alone).  Device buffers; SBP_ERR_ARG on bad sizes. */
+int sbp_nn_fourier_features(const float* x, void* y, int32_t n_in, int64_t B, int32_t L, void* stream);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* sbp_last_error(void);
 

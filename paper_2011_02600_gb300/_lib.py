@@ -29,7 +29,8 @@ EXPORTED = ("sbp_min_nodes", "sbp_create_grid", "sbp_destroy", "sbp_layout", "sb
             "sbp_nn_mlp_to_conv", "sbp_nn_cast_bf16", "sbp_nn_moment_combine", "sbp_selftest_wait_timeout", "sbp_last_error",
             "sbp_set_receivers_xyz", "sbp_record_receivers", "sbp_set_state", "sbp_get_state",
             "sbp_nn_set_gemm_path", "sbp_nn_status", "sbp_set_slab", "sbp_interface_trace", "sbp_set_interface",
-            "sbp_probe_fp64_rate", "sbp_set_map_path", "sbp_map_path", "sbp_adjoint_step")
+            "sbp_probe_fp64_rate", "sbp_set_map_path", "sbp_map_path", "sbp_adjoint_step",
+            "sbp_nn_fourier_features")
 
 
 class SbpError(RuntimeError):
@@ -104,6 +105,7 @@ def lib(path=None):
         "sbp_nn_adam": [P, P, P, P, P, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, i32, P],
         "sbp_nn_mlp_to_conv": [P, P, i32, i32, i32, i32, P],
         "sbp_nn_cast_bf16": [P, P, i64, P],
+        "sbp_nn_fourier_features": [P, P, i32, i64, i32, P],
         "sbp_nn_moment_combine": [P, P, P, P, P, i32, i32, i32, i32, P],
         "sbp_selftest_wait_timeout": [P, ctypes.c_uint32, P],
         "sbp_set_sources": [P, i32, ctypes.POINTER(SbpSource), P, P],
@@ -409,6 +411,10 @@ def sbp_nn_mlp_to_conv(H, X, C, T0, B, backward, stream):
 
 def sbp_nn_cast_bf16(x, y, n, stream):
     _check(lib().sbp_nn_cast_bf16(_ptr(x), _ptr(y), n, stream))
+
+
+def sbp_nn_fourier_features(x, y, n_in, B, L, stream):
+    _check(lib().sbp_nn_fourier_features(_ptr(x), _ptr(y), n_in, B, L, stream))
 
 
 def sbp_nn_moment_combine(G, m, y, dy, dG, n_out, B, T, backward, stream):

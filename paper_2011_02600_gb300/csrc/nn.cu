@@ -448,6 +448,12 @@ __global__ void moment_combine_bwd_kernel(const __nv_bfloat16* __restrict__ dy, 
   }
 }
 
+__global__ void fourier_features_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, int n_in, int B,
+                                        int L, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+    fourier_features_at(x, y, n_in, B, L, e);
+}
+
 __global__ void cast_kernel(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, long long n) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
     y[e] = __float2bfloat16(x[e]);
@@ -652,6 +658,13 @@ int sbp_nn_moment_combine(const float* G, const float* m, float* y, const void* 
     if (!G || !y) return nn_bad("moment_combine needs G and y");
     moment_combine_kernel<<<grid_for((long long)n_out * B * T), 256, 0, (cudaStream_t)stream>>>(G, m, y, n_out, B, T);
   }
+  return nn_status(cudaGetLastError());
+}
+
+int sbp_nn_fourier_features(const float* x, void* y, int32_t n_in, int64_t B, int32_t L, void* stream) {
+  if (!x || !y || n_in <= 0 || B <= 0 || L < 0 || L > 16) return nn_bad("bad Fourier feature arguments");
+  const long long n = (long long)n_in * (1 + 2 * L) * B;
+  fourier_features_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(x, (__nv_bfloat16*)y, n_in, (int)B, L, n);
   return nn_status(cudaGetLastError());
 }
 

@@ -7,6 +7,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <math.h>
 
 namespace sbp_nn {
 
@@ -56,6 +57,24 @@ __device__ __forceinline__ void moment_combine_bwd_at(const __nv_bfloat16* __res
   const int c = (int)(row / n_out), o = (int)(row % n_out);
   const int b = (int)(col / T);
   dG[e] = __float2bfloat16(m[c * B + b] * __bfloat162float(dy[(long long)o * B * T + col]));
+}
+
+// Fourier features of the network input: y[j][b] (BF16, [n_in (1 + 2 L)][B]) for x[i][b] (FP32,
+// [n_in][B], normalised to [-1, 1]): rows 0..n_in-1 are x itself, then for each input i and
+// k = 0..L-1 the pair sin(2^k pi x), cos(2^k pi x) (row n_in + 2 (i L + k) + 0 / 1).
+__device__ __forceinline__ void fourier_features_at(const float* __restrict__ x, __nv_bfloat16* __restrict__ y,
+                                                    int n_in, int B, int L, long long e) {
+  const int j = (int)(e / B), b = (int)(e % B);
+  float v;
+  if (j < n_in) {
+    v = x[(long long)j * B + b];
+  } else {
+    const int r = j - n_in;
+    const int i = r / (2 * L), k = (r / 2) % L;
+    const float a = 3.14159265358979f * ldexpf(x[(long long)i * B + b], k);
+    v = (r & 1) ? cosf(a) : sinf(a);
+  }
+  y[e] = __float2bfloat16(v);
 }
 
 }  // namespace sbp_nn

@@ -1,7 +1,8 @@
 """Learned surrogate of the solver: source parameters -> receiver traces.
 
 Network (BF16 weights and activations, FP32 accumulation on tensor cores):
-    x (normalised source position q, r, s)
+    x (normalised source position q, r, s), with n_freq > 0 followed by its Fourier features
+    sin(2^k pi x), cos(2^k pi x), k < n_freq (sbp_nn_fourier_features)
     -> 3 fully connected layers with ReLU (3 -> H -> H -> C*T0), reshaped to C channels x T0 samples
     -> n_up times [nearest x2 upsampling in time, 1D convolution (width 5) C -> C, ReLU]
     -> 1D convolution (width 5) C -> 6 * n_out, linear: six trace sets G_c
@@ -37,7 +38,7 @@ PAD = 2
 
 class SurrogateNet:
     def __init__(self, n_in=3, hidden=512, C=128, T0=32, n_up=5, n_out=192, n_mom=6, seed=0, device="cuda",
-                 lo=None, hi=None):
+                 lo=None, hi=None, n_freq=0):
         """n_mom = 6: moment-linear output (forward needs m); n_mom = 0: the last layer is the output.
         lo, hi: the box of source positions (q, r, s) the network is trained on; inputs are
         mapped from it to [-1, 1]."""
@@ -47,11 +48,13 @@ class SurrogateNet:
         self.hi = tuple(hi if hi is not None else PARAM_HI[:n_in])
         self.n_in, self.hidden, self.C, self.T0, self.n_up, self.n_out = n_in, hidden, C, T0, n_up, n_out
         self.n_mom = n_mom
+        self.n_freq = n_freq
+        self.n_feat = n_in * (1 + 2 * n_freq)   # the first layer's inputs
         self.n_last = n_out * max(1, n_mom)
         self.T = T0 * 2 ** n_up
         self.device = torch.device(device)
         g = torch.Generator(device="cpu").manual_seed(seed)
-        shapes = [("fc1", hidden, n_in), ("fc2", hidden, hidden), ("fc3", C * T0, hidden)]
+        shapes = [("fc1", hidden, self.n_feat), ("fc2", hidden, hidden), ("fc3", C * T0, hidden)]
         shapes += [(f"conv{i}", C, C * KW) for i in range(n_up)]
         shapes += [("out", self.n_last, C * KW)]
         self.names = [s[0] for s in shapes]
@@ -81,7 +84,8 @@ class SurrogateNet:
 
     # ---- forward -------------------------------------------------------------
     def forward(self, x, m=None, keep=False):
-        """x: BF16 [n_in][B] (normalised parameters); m: FP32 [6][B] moment components
+        """x: BF16 [n_feat][B] (normalised parameters and their Fourier features: to_input);
+        m: FP32 [6][B] moment components
         (n_mom = 6).  Returns FP32 [n_out][B * T]."""
         if (m is None) != (self.n_mom == 0):
             raise ValueError("m must be given exactly when n_mom = 6")
@@ -90,7 +94,7 @@ class SurrogateNet:
         bf = dict(dtype=torch.bfloat16, device=dev)
         H, C, T0 = self.hidden, self.C, self.T0
         h1 = torch.empty(H, B, **bf)
-        self._gemm(H, B, self.n_in, self.wb["fc1"], self.n_in, 0, x, B, 0, h1, B, True, self.b["fc1"], 1)
+        self._gemm(H, B, self.n_feat, self.wb["fc1"], self.n_feat, 0, x, B, 0, h1, B, True, self.b["fc1"], 1)
         h2 = torch.empty(H, B, **bf)
         self._gemm(H, B, H, self.wb["fc2"], H, 0, h1, B, 0, h2, B, True, self.b["fc2"], 1)
         h3 = torch.empty(C * T0, B, **bf)
@@ -176,7 +180,7 @@ class SurrogateNet:
         self._gemm(H, B, H, self.wb["fc2"], H, 1, dz2, B, 0, dh1, B, False)
         dz1 = torch.empty(H, B, **bf)
         L.sbp_nn_relu_backward(dh1, c["h1"], dz1, H * B, st)
-        self._fc_backward("fc1", dz1, c["x"], H, self.n_in, B)
+        self._fc_backward("fc1", dz1, c["x"], H, self.n_feat, B)
 
     def _fc_backward(self, name, dz, xin, o, i, B):
         self._gemm(o, i, B, dz, B, 0, xin, B, 1, self.gw[name], i, False)
@@ -202,14 +206,16 @@ def mse(y, target, want_grad=True, nblocks=256):
     return float(partial.sum()) / n, dy
 
 
-def to_input(params, lo, hi):
-    """Normalise [B][n_in] position parameters into the network's BF16 [n_in][B] input (cast in the library)."""
+def to_input(params, lo, hi, n_freq=0):
+    """Normalise [B][n_in] position parameters to [-1, 1] and form the network's BF16
+    [n_in (1 + 2 n_freq)][B] input (the parameters and their Fourier features, in the library)."""
     p = torch.as_tensor(params, dtype=torch.float32)
     x = (2.0 * (p - torch.as_tensor(lo, dtype=torch.float32)) /
          torch.as_tensor(np.asarray(hi) - np.asarray(lo), dtype=torch.float32) - 1.0).t().contiguous()
     x = x.cuda()
-    xb = torch.empty_like(x, dtype=torch.bfloat16)
-    L.sbp_nn_cast_bf16(x, xb, x.numel(), _stream())
+    n_in, B = x.shape
+    xb = torch.empty(n_in * (1 + 2 * n_freq), B, dtype=torch.bfloat16, device=x.device)
+    L.sbp_nn_fourier_features(x, xb, n_in, B, n_freq, _stream())
     return xb
 
 
@@ -292,7 +298,7 @@ def train(net, X, Y, epochs, batch=32, lr=1e-3, seed=0, log_every=0):
         tot = 0.0
         for b0 in range(0, n - batch + 1, batch):
             idx = perm[b0:b0 + batch]
-            x = to_input(X[idx, :net.n_in], net.lo, net.hi)
+            x = to_input(X[idx, :net.n_in], net.lo, net.hi, net.n_freq)
             m = moment_inputs(X[idx], unit=True) if net.n_mom else None
             tgt = Y[torch.as_tensor(idx, device=Y.device)].permute(1, 0, 2).reshape(net.n_out, -1).contiguous()
             y = net.forward(x, m, keep=True)
@@ -311,7 +317,7 @@ def predict(net, X, batch=64):
     solver's traces divided by the training's global scale."""
     outs = []
     for b0 in range(0, len(X), batch):
-        x = to_input(X[b0:b0 + batch, :net.n_in], net.lo, net.hi)
+        x = to_input(X[b0:b0 + batch, :net.n_in], net.lo, net.hi, net.n_freq)
         y = net.forward(x, moment_inputs(X[b0:b0 + batch]) if net.n_mom else None)
         B = x.shape[1]
         outs.append(y.view(net.n_out, B, net.T).permute(1, 0, 2))
@@ -356,30 +362,38 @@ class SeismogramModel:
         return out, ~inside
 
 
-def run_workload(cfg, n_train=None, n_test=None, epochs=200, batch=32, lr=1e-3, hidden=512, C=128, T0=32,
-                 seed=0, gen_batch=64, log=print):
-    """Generate the workload's training and held-out sets with the batched solver, train the
-    network with the library's kernels, and judge it against the solver on the held-out
-    sources.  Returns a dict of sizes, timings, errors and the speed-up."""
+def make_dataset(cfg, n_train=None, n_test=None, seed=0, gen_batch=64, log=print):
+    """The workload's training and held-out sources (seeded) and their traces from the batched
+    solver: (P [n][7], Y [n][n_out][T] FP32 device, info dict)."""
     n_train = n_train or cfg.extra["n_train"]
     n_test = n_test or cfg.extra["n_test"]
     T = cfg.extra.get("n_samples", cfg.steps)
     every = cfg.steps // T
-    n_up = int(round(math.log2(T / T0)))
-    if T0 * 2 ** n_up != T:
-        raise ValueError("samples per trace must be T0 times a power of two")
     f0, n_side = cfg.extra["f0"], cfg.extra.get("n_side", 8)
     P = sample_params(seed, n_train + n_test)
     t0 = time.perf_counter()
-    Y, t_solve, info = generate_dataset(cfg, P, batch=gen_batch, f0=f0, n_side=n_side, every=every)
+    Y, t_solve, _ = generate_dataset(cfg, P, batch=gen_batch, f0=f0, n_side=n_side, every=every)
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t0
-    log(f"dataset {tuple(Y.shape)} in {t_gen:.1f} s, solver {t_solve * 1e3:.2f} ms per source")
+    if log:
+        log(f"dataset {tuple(Y.shape)} in {t_gen:.1f} s, solver {t_solve * 1e3:.2f} ms per source")
+    return P, Y, dict(n_train=n_train, n_test=n_test, samples=T, f0=f0, dataset_s=t_gen, solver_s=t_solve)
+
+
+def train_and_judge(cfg, P, Y, info, epochs=200, batch=32, lr=1e-3, hidden=512, C=128, T0=32, n_freq=0, seed=0,
+                    log=print):
+    """Train the network on the first n_train sources with the library's kernels and judge it
+    against the solver's traces of the held-out ones.  Returns sizes, timings, errors and the
+    speed-up."""
+    n_train, n_test, T = info["n_train"], info["n_test"], info["samples"]
+    n_up = int(round(math.log2(T / T0)))
+    if T0 * 2 ** n_up != T:
+        raise ValueError("samples per trace must be T0 times a power of two")
     per = torch.as_tensor(M_REF / 10.0 ** P[:, 6], dtype=torch.float32, device=Y.device)[:, None, None]
     Yt = Y[:n_train] * per[:n_train]
     norm = float(Yt.pow(2).mean().sqrt())
     Yt /= norm
-    net = SurrogateNet(n_in=3, hidden=hidden, C=C, T0=T0, n_up=n_up, n_out=Y.shape[1], seed=seed)
+    net = SurrogateNet(n_in=3, hidden=hidden, C=C, T0=T0, n_up=n_up, n_out=Y.shape[1], seed=seed, n_freq=n_freq)
     t0 = time.perf_counter()
     losses = train(net, P[:n_train], Yt, epochs=epochs, batch=batch, lr=lr, seed=seed,
                    log_every=max(1, epochs // 10) if log else 0)
@@ -397,12 +411,23 @@ def run_workload(cfg, n_train=None, n_test=None, epochs=200, batch=32, lr=1e-3, 
     mt = moment_inputs(P[:n_train], unit=True).double()
     G = torch.linalg.lstsq(mt.t(), (Y[:n_train] * per[:n_train] / norm).double().reshape(n_train, -1)).solution
     base = relative_l2((moment_inputs(P[n_train:]).double().t() @ G).reshape(truth.shape).float(), truth)
+    t_solve = info["solver_s"]
     return dict(nodes=list(cfg.nodes), order=cfg.order, steps=cfg.steps, samples=T, receivers=Y.shape[1] // 3,
-                f0=f0, n_train=n_train, n_test=n_test, epochs=epochs, params=net.n_params(),
-                dataset_s=t_gen, train_s=t_train, solver_ms_per_source=t_solve * 1e3,
-                net_ms_per_source=t_net * 1e3, speedup=t_solve / t_net,
+                f0=info["f0"], n_train=n_train, n_test=n_test, epochs=epochs, hidden=hidden, n_freq=n_freq,
+                params=net.n_params(), dataset_s=info["dataset_s"], train_s=t_train,
+                solver_ms_per_source=t_solve * 1e3, net_ms_per_source=t_net * 1e3, speedup=t_solve / t_net,
                 err_median=float(np.median(err)), err_p90=float(np.quantile(err, 0.9)),
                 position_blind_err_median=float(np.median(base)), loss_first=losses[0], loss_last=losses[-1])
+
+
+def run_workload(cfg, n_train=None, n_test=None, epochs=200, batch=32, lr=1e-3, hidden=512, C=128, T0=32,
+                 seed=0, gen_batch=64, n_freq=0, log=print):
+    """Generate the workload's training and held-out sets with the batched solver, train the
+    network with the library's kernels, and judge it against the solver on the held-out
+    sources.  Returns a dict of sizes, timings, errors and the speed-up."""
+    P, Y, info = make_dataset(cfg, n_train, n_test, seed=seed, gen_batch=gen_batch, log=log)
+    return train_and_judge(cfg, P, Y, info, epochs=epochs, batch=batch, lr=lr, hidden=hidden, C=C, T0=T0,
+                           n_freq=n_freq, seed=seed, log=log)
 
 
 def main(argv=None):
@@ -414,10 +439,13 @@ def main(argv=None):
     ap.add_argument("--n-test", type=int, default=None)
     ap.add_argument("--epochs", type=int, default=200)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--hidden", type=int, default=512)
+    ap.add_argument("--n-freq", type=int, default=0, help="Fourier features of the position input (0: none)")
     a = ap.parse_args(argv)
     from . import build
     build.build()
-    res = run_workload(config_by_name("surrogate97_o4"), a.n_train, a.n_test, epochs=a.epochs, lr=a.lr)
+    res = run_workload(config_by_name("surrogate97_o4"), a.n_train, a.n_test, epochs=a.epochs, lr=a.lr,
+                       hidden=a.hidden, n_freq=a.n_freq)
     print(json.dumps(res))
 
 

@@ -50,3 +50,11 @@ extern "C" void host_moment_combine(const float* G, const float* m, float* y, co
   for (long long e = 0; e < 6 * n_out * BT; ++e) moment_combine_bwd_at(dyb.data(), m, dgb.data(), n_out, B, T, e);
   for (long long i = 0; i < 6 * n_out * BT; ++i) dG[i] = __bfloat162float(dgb[i]);
 }
+
+// y [n_in (1 + 2 L)][B] (BF16, returned as FP32): the Fourier features of x [n_in][B]
+extern "C" void host_fourier_features(const float* x, float* y, int n_in, int B, int L) {
+  const long long n = (long long)n_in * (1 + 2 * L) * B;
+  std::vector<__nv_bfloat16> yb(n);
+  for (long long e = 0; e < n; ++e) fourier_features_at(x, yb.data(), n_in, B, L, e);
+  for (long long e = 0; e < n; ++e) y[e] = __bfloat162float(yb[e]);
+}

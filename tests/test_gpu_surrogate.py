@@ -216,3 +216,28 @@ def test_solver_fallback_outside_the_training_box():
     want, _, _ = S.generate_dataset(cfg, P[3:], batch=3, f0=0.5, n_side=3)
     assert torch.equal(y[3:], want)
     assert torch.allclose(y[:3], S.predict(net, P[:3]) * 2.5)
+
+
+@pytest.mark.parametrize("n_in,B,L", [(3, 37, 4), (3, 64, 6), (7, 5, 0)])
+def test_fourier_features_kernel(n_in, B, L):
+    """sbp_nn_fourier_features: x, then sin(2^k pi x), cos(2^k pi x) per input (BF16), as to_input
+    forms the network's input."""
+    from paper_2011_02600_gb300 import _lib as L_
+    from paper_2011_02600_gb300.solver import _stream
+    from paper_2011_02600_gb300.surrogate import to_input
+    rng = np.random.default_rng(B + L)
+    x = torch.as_tensor(rng.uniform(-1, 1, size=(n_in, B)), dtype=torch.float32).cuda()
+    y = torch.empty(n_in * (1 + 2 * L), B, dtype=torch.bfloat16, device="cuda")
+    L_.sbp_nn_fourier_features(x, y, n_in, B, L, _stream())
+    xd = x.double().cpu().numpy()
+    rows = [xd[i] for i in range(n_in)]
+    for i in range(n_in):
+        for k in range(L):
+            rows += [np.sin(2.0 ** k * np.pi * xd[i]), np.cos(2.0 ** k * np.pi * xd[i])]
+    want = np.stack(rows)
+    assert np.abs(y.float().cpu().numpy() - want).max() <= 2.0 ** -7 * max(1.0, np.abs(want).max())
+    # to_input: the normalised parameters' features
+    P = rng.uniform(0.3, 0.7, size=(B, n_in))
+    xb = to_input(P, [0.3] * n_in, [0.7] * n_in, L)
+    assert xb.shape == (n_in * (1 + 2 * L), B)
+    assert np.abs(xb[:n_in].float().cpu().numpy() - (5.0 * (P.T - 0.3) - 1.0)).max() < 1e-2

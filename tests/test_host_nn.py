@@ -2,7 +2,8 @@
 bodies of csrc/nn_elem.cuh (im2col, col2im, the moment combination and its backward) as host
 C++.  Composed with plain matrix products (what the tensor-core GEMM computes) they give the
 oracle network's direct-sum convolution and its input gradient, over ragged shapes, kernel
-widths and paddings; the moment combination gives its definition, sum_c m_c G_c."""
+widths and paddings; the moment combination gives its definition, sum_c m_c G_c; the input's
+Fourier features are x, then sin(2^k pi x), cos(2^k pi x) per input in the documented rows."""
 import ctypes
 
 import numpy as np
@@ -21,6 +22,7 @@ def hostnn(tmp_path_factory):
     lib.host_conv_forward.argtypes = [P, P, P] + [I] * 6
     lib.host_conv_backward_dx.argtypes = [P, P, P] + [I] * 6
     lib.host_moment_combine.argtypes = [P] * 5 + [I] * 3
+    lib.host_fourier_features.argtypes = [P, P] + [I] * 3
     return lib
 
 
@@ -60,3 +62,19 @@ def test_moment_combination_and_backward(hostnn, n_out, B, T):
     assert np.abs(y - want).max() < 1e-5 * max(1.0, np.abs(want).max())
     want_dG = m[:, None, :, None].astype(np.float64) * round_bf16(dy.astype(np.float64))[None]
     assert np.abs(dG - round_bf16(want_dG)).max() <= 2.0 ** -8 * np.abs(want_dG).max()
+
+
+@pytest.mark.parametrize("n_in,B,L", [(3, 5, 4), (1, 7, 1), (2, 3, 0), (3, 2, 6)])
+def test_fourier_features(hostnn, n_in, B, L):
+    rng = np.random.default_rng(n_in * 7 + L)
+    x = _f32(rng.uniform(-1, 1, size=(n_in, B)))
+    y = np.zeros((n_in * (1 + 2 * L), B), np.float32)
+    hostnn.host_fourier_features(x.ctypes.data, y.ctypes.data, n_in, B, L)
+    xd = x.astype(np.float64)
+    rows = [xd[i] for i in range(n_in)]
+    for i in range(n_in):
+        for k in range(L):
+            rows += [np.sin(2.0 ** k * np.pi * xd[i]), np.cos(2.0 ** k * np.pi * xd[i])]
+    want = round_bf16(np.stack(rows))
+    # BF16 rounding of FP32 sines: within one BF16 unit of the rounded FP64 value
+    assert np.abs(y - want).max() <= 2.0 ** -7 * max(1.0, np.abs(want).max())
