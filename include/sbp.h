@@ -452,9 +452,10 @@ int sbp_nn_adam(float* w, const float* g, float* m, float* v, void* w_bf16, int6
 int sbp_nn_mlp_to_conv(void* H, void* X, int32_t C, int32_t T0, int32_t B, int32_t backward, void* stream);
 /* Traces are linear in the moment tensor: y[o][b T + t] = sum_{c<6} m[c][b]
  * G[(c n_out + o)][b T + t] with G the network's six Green's-function trace sets
- * (FP32) and m the Voigt moment components per sample (FP32 [6][B]); backward
- * (backward = 1): dG[(c n_out + o)][b T + t] = m[c][b] dy[o][b T + t] (dy, dG BF16). */
-int sbp_nn_moment_combine(const float* G, const float* m, float* y, const void* dy, void* dG, int32_t n_out,
+ * (BF16, like the network's other activations) and m the Voigt moment components per
+ * sample (FP32 [6][B]), y FP32; backward (backward = 1): dG[(c n_out + o)][b T + t] =
+ * m[c][b] dy[o][b T + t] (dy, dG BF16). */
+int sbp_nn_moment_combine(const void* G, const float* m, float* y, const void* dy, void* dG, int32_t n_out,
                           int32_t B, int32_t T, int32_t backward, void* stream);
 /* y = BF16(x). */
 int sbp_nn_cast_bf16(const float* x, void* y, int64_t n, void* stream);

@@ -90,7 +90,7 @@ def forward(params, x, C, T0, n_up, m=None, bf16=False):
     y = conv1d(a, W, b)
     cache["out"] = (a, y)
     if m is not None:
-        G = y.reshape(6, -1, *y.shape[1:])
+        G = rb(y.reshape(6, -1, *y.shape[1:]))   # the six trace sets, stored in BF16 like the activations
         y = np.einsum("cb,cobt->obt", m, G)
     return y, cache
 

@@ -432,7 +432,7 @@ __global__ void mlp_to_conv_kernel(const __nv_bfloat16* __restrict__ H, __nv_bfl
 
 // Moment combination: y[o][b*T + t] = sum_c m[c][b] G[(c*n_out + o)][b*T + t] (G FP32);
 // backward: dG[(c*n_out + o)][b*T + t] = m[c][b] dy[o][b*T + t] (BF16).
-__global__ void moment_combine_kernel(const float* __restrict__ G, const float* __restrict__ m, float* __restrict__ y,
+__global__ void moment_combine_kernel(const __nv_bfloat16* __restrict__ G, const float* __restrict__ m, float* __restrict__ y,
                                       int n_out, int B, int T) {
   const long long n = (long long)n_out * B * T;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
@@ -647,7 +647,7 @@ int sbp_nn_mlp_to_conv(void* H, void* X, int32_t C, int32_t T0, int32_t B, int32
   return nn_status(cudaGetLastError());
 }
 
-int sbp_nn_moment_combine(const float* G, const float* m, float* y, const void* dy, void* dG, int32_t n_out,
+int sbp_nn_moment_combine(const void* G, const float* m, float* y, const void* dy, void* dG, int32_t n_out,
                           int32_t B, int32_t T, int32_t backward, void* stream) {
   if (!m || n_out <= 0 || B <= 0 || T <= 0) return nn_bad("bad moment_combine arguments");
   if (backward) {
@@ -656,7 +656,8 @@ int sbp_nn_moment_combine(const float* G, const float* m, float* y, const void* 
         (const __nv_bfloat16*)dy, m, (__nv_bfloat16*)dG, n_out, B, T);
   } else {
     if (!G || !y) return nn_bad("moment_combine needs G and y");
-    moment_combine_kernel<<<grid_for((long long)n_out * B * T), 256, 0, (cudaStream_t)stream>>>(G, m, y, n_out, B, T);
+    moment_combine_kernel<<<grid_for((long long)n_out * B * T), 256, 0, (cudaStream_t)stream>>>(
+        (const __nv_bfloat16*)G, m, y, n_out, B, T);
   }
   return nn_status(cudaGetLastError());
 }

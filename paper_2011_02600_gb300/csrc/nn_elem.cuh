@@ -36,15 +36,15 @@ __device__ __forceinline__ void col2im_at(const float* __restrict__ dXc, float* 
   dX[e] = s;
 }
 
-// y[o][b*T + t] = sum_c m[c][b] G[(c*n_out + o)][b*T + t]  (G FP32)
-__device__ __forceinline__ void moment_combine_at(const float* __restrict__ G, const float* __restrict__ m,
+// y[o][b*T + t] = sum_c m[c][b] G[(c*n_out + o)][b*T + t]  (G BF16, y FP32)
+__device__ __forceinline__ void moment_combine_at(const __nv_bfloat16* __restrict__ G, const float* __restrict__ m,
                                                   float* __restrict__ y, int n_out, int B, int T, long long e) {
   const int o = (int)(e / ((long long)B * T));
   const long long col = e % ((long long)B * T);
   const int b = (int)(col / T);
   float s = 0.f;
 #pragma unroll
-  for (int c = 0; c < 6; ++c) s += m[c * B + b] * G[((long long)c * n_out + o) * B * T + col];
+  for (int c = 0; c < 6; ++c) s += m[c * B + b] * __bfloat162float(G[((long long)c * n_out + o) * B * T + col]);
   y[e] = s;
 }
 

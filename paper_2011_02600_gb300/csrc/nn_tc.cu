@@ -13,11 +13,11 @@
 //    accumulators of 128 lanes x 256 columns in tensor memory (all 512 columns), and frees each
 //    stage with tcgen05.commit; a commit on the accumulator's barrier hands it to the epilogue;
 //  * warps 2-9 drain the other accumulator meanwhile, two warps per group of 32 accumulator lanes
-//    (half of the columns each): tcgen05.ld, bias and ReLU in registers, then for FP32 outputs a
-//    32 x 32 box into swizzled shared memory and a TMA store (a TMA reduce-add when K is split
-//    over work items), otherwise a transpose through shared memory and stores that cover 32
-//    consecutive columns of a row; then an arrival that gives the accumulator back to the MMA
-//    warp.
+//    (half of the columns each): tcgen05.ld, bias and ReLU in registers, then a 32 x 32 box (FP32
+//    or BF16) into swizzled shared memory and a TMA store (a TMA reduce-add when K is split over
+//    work items), or, when C is accumulated into or does not suit TMA, a transpose through shared
+//    memory and stores that cover 32 consecutive columns of a row; then an arrival that gives the
+//    accumulator back to the MMA warp.
 // Every mbarrier wait is bounded: on a timeout the CTA records it in a device status word
 // (sbp_nn_status), its roles stop, and it still waits for its MMAs and frees its tensor memory.
 #include <cuda.h>
@@ -48,7 +48,7 @@ static_assert(SMEM_BYTES <= 232448, "shared memory per block");
 // How the epilogue writes C: through the warp's transpose tile with plain stores (BF16 output or
 // accumulation into C), or from swizzled shared-memory buffers by TMA (store, or reduce-add
 // when K is split over work items).
-enum EpiMode : int { kEpiDirect = 0, kEpiTmaStore = 1, kEpiTmaAdd = 2 };
+enum EpiMode : int { kEpiDirect = 0, kEpiTmaStore = 1, kEpiTmaAdd = 2, kEpiTmaStoreBf16 = 3 };
 constexpr unsigned kWaitLimit = 1u << 24;         // polls of about 64 ns: roughly a second
 
 __device__ unsigned g_tc_status;  // bit 1: a wait timed out
@@ -302,10 +302,26 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (lane == 0 && chunks_stored >= 1)
             asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // the last store has read the buffer
           __syncwarp();
-          float4* row = reinterpret_cast<float4*>(sb + lane * 128);
+          if (epi_mode == kEpiTmaStoreBf16) {
+            // BF16 rows of 64 bytes in the 64-byte swizzle (16-byte granule g of row r at
+            // g ^ ((r / 2) % 4)), for a 32 x 32 BF16 box
+            uint4* row = reinterpret_cast<uint4*>(sb + lane * 64);
 #pragma unroll
-          for (int j4 = 0; j4 < 8; ++j4)
-            row[j4 ^ (lane & 7)] = make_float4(v[4 * j4], v[4 * j4 + 1], v[4 * j4 + 2], v[4 * j4 + 3]);
+            for (int g = 0; g < 4; ++g) {
+              uint32_t w[4];
+#pragma unroll
+              for (int h = 0; h < 4; ++h) {
+                const __nv_bfloat162 p = __floats2bfloat162_rn(v[8 * g + 2 * h], v[8 * g + 2 * h + 1]);
+                w[h] = *reinterpret_cast<const uint32_t*>(&p);
+              }
+              row[g ^ ((lane >> 1) & 3)] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+          } else {
+            float4* row = reinterpret_cast<float4*>(sb + lane * 128);
+#pragma unroll
+            for (int j4 = 0; j4 < 8; ++j4)
+              row[j4 ^ (lane & 7)] = make_float4(v[4 * j4], v[4 * j4 + 1], v[4 * j4 + 2], v[4 * j4 + 3]);
+          }
           sbp::fence_proxy_async_smem();
           __syncwarp();
           if (lane == 0) tma_store_2d(&maps.c, nb, I.m0 + lg * 32, sb, epi_mode == kEpiTmaAdd);
@@ -385,7 +401,8 @@ bool encode_uncached(CUtensorMap* m, const void* base, long long rows, long long
                      int box_rows, bool fp32);
 
 // 2D tensor map of a row-major bf16 (or FP32) matrix with `rows` rows of `cols` elements (row
-// pitch ld elements), box of box_cols x box_rows, 128-byte swizzle, zero fill outside the matrix.
+// pitch ld elements), box of box_cols x box_rows, zero fill outside the matrix; the swizzle spans
+// one box row: 128 bytes (operand tiles, FP32 output boxes) or 64 bytes (BF16 output boxes).
 bool encode(CUtensorMap* m, const void* base, long long rows, long long cols, long long ld, int box_cols,
             int box_rows, bool fp32 = false) {
   int dev = 0;
@@ -412,13 +429,16 @@ bool encode_uncached(CUtensorMap* m, const void* base, long long rows, long long
   PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
   if (!enc) return false;
   const int es_bytes = fp32 ? 4 : 2;
+  const int row_bytes = box_cols * es_bytes;
+  if (row_bytes != 128 && row_bytes != 64) return false;
+  const CUtensorMapSwizzle swz = row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)ld * es_bytes};
   const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   const cuuint32_t es[2] = {1, 1};
   return enc(m, fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
              dims, strides, box, es,
-             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -448,12 +468,16 @@ cudaError_t launch_gemm_tc(int M, int N, int K, const void* A, long long lda, in
     if (splits > 1) k_per = (int)(((K + splits - 1) / splits + BK - 1) / BK * BK);
   }
   const long long items = tiles * ((K + k_per - 1) / k_per);
-  // TMA epilogue for FP32 outputs without accumulation (store, or reduce-add of split K) when C
-  // suits TMA (16-byte aligned base, rows a multiple of 16 bytes); the direct path otherwise
+  // TMA epilogue for outputs without accumulation (FP32: store, or reduce-add of split K; BF16:
+  // store) when C suits TMA (16-byte aligned base, rows a multiple of 16 bytes); the direct path
+  // otherwise
   int epi_mode = kEpiDirect;
   if (!c_bf16 && beta == 0.f && ldc % 4 == 0 && (uintptr_t)C % 16 == 0 &&
       encode(&maps.c, C, M, N, ldc, 32, 32, true))
     epi_mode = k_per < K ? kEpiTmaAdd : kEpiTmaStore;
+  if (c_bf16 && beta == 0.f && k_per == K && ldc % 8 == 0 && (uintptr_t)C % 16 == 0 &&
+      encode(&maps.c, C, M, N, ldc, 32, 32, false))
+    epi_mode = kEpiTmaStoreBf16;
   if (items > (1LL << 30)) return cudaErrorInvalidValue;
   cudaError_t e = cudaSuccess;
   if (k_per < K) {

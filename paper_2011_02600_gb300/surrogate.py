@@ -117,9 +117,11 @@ class SurrogateNet:
             cols.append(col)
         col = torch.empty(C * KW, B * T, **bf)
         L.sbp_nn_im2col(a, col, C, B, T, KW, PAD, _stream())
-        g = torch.empty(self.n_last, B * T, dtype=torch.float32, device=dev)
-        self._gemm(self.n_last, B * T, C * KW, self.wb["out"], C * KW, 0, col, B * T, 0, g, B * T, False,
-                   self.b["out"], 0)
+        # the six trace sets in BF16 like the other activations (the traces y combined from them
+        # are FP32); the output itself (n_mom = 0) in FP32
+        g = torch.empty(self.n_last, B * T, dtype=torch.bfloat16 if self.n_mom else torch.float32, device=dev)
+        self._gemm(self.n_last, B * T, C * KW, self.wb["out"], C * KW, 0, col, B * T, 0, g, B * T,
+                   bool(self.n_mom), self.b["out"], 0)
         y = g
         if self.n_mom:
             y = torch.empty(self.n_out, B * T, dtype=torch.float32, device=dev)

@@ -40,11 +40,14 @@ extern "C" void host_conv_backward_dx(const float* W, const float* dY, float* dX
   for (long long e = 0; e < C * BT; ++e) col2im_at(dxc.data(), dX, B, T, kw, pad, e);
 }
 
-// y [n_out][B*T] from G [6*n_out][B*T] and m [6][B]; dG [6*n_out][B*T] (BF16, returned as FP32) from dy
+// y [n_out][B*T] from G [6*n_out][B*T] (rounded to BF16) and m [6][B]; dG [6*n_out][B*T] (BF16,
+// returned as FP32) from dy
 extern "C" void host_moment_combine(const float* G, const float* m, float* y, const float* dy, float* dG, int n_out,
                                     int B, int T) {
   const long long BT = (long long)B * T;
-  for (long long e = 0; e < n_out * BT; ++e) moment_combine_at(G, m, y, n_out, B, T, e);
+  std::vector<__nv_bfloat16> gb(6 * n_out * BT);
+  for (long long i = 0; i < 6 * n_out * BT; ++i) gb[i] = __float2bfloat16(G[i]);
+  for (long long e = 0; e < n_out * BT; ++e) moment_combine_at(gb.data(), m, y, n_out, B, T, e);
   std::vector<__nv_bfloat16> dyb(n_out * BT), dgb(6 * n_out * BT);
   for (long long i = 0; i < n_out * BT; ++i) dyb[i] = __float2bfloat16(dy[i]);
   for (long long e = 0; e < 6 * n_out * BT; ++e) moment_combine_bwd_at(dyb.data(), m, dgb.data(), n_out, B, T, e);

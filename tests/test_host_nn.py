@@ -58,7 +58,7 @@ def test_moment_combination_and_backward(hostnn, n_out, B, T):
     dG = np.zeros((6, n_out, B, T), np.float32)
     hostnn.host_moment_combine(G.ctypes.data, m.ctypes.data, y.ctypes.data, dy.ctypes.data, dG.ctypes.data,
                                n_out, B, T)
-    want = np.einsum("cb,cobt->obt", m.astype(np.float64), G.astype(np.float64))
+    want = np.einsum("cb,cobt->obt", m.astype(np.float64), round_bf16(G.astype(np.float64)))
     assert np.abs(y - want).max() < 1e-5 * max(1.0, np.abs(want).max())
     want_dG = m[:, None, :, None].astype(np.float64) * round_bf16(dy.astype(np.float64))[None]
     assert np.abs(dG - round_bf16(want_dG)).max() <= 2.0 ** -8 * np.abs(want_dG).max()
