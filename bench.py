@@ -4,8 +4,12 @@ Workload: 1025 x 1025 x 401 nodes (421M), order-6 upwind SBP, FP32, 60 x 60 x 24
 block with a seeded sum-of-sinusoids top surface (free) and absorbing faces
 elsewhere, von Karman perturbed gradient medium.  A step is one full
 Runge-Kutta step: five fused stages over every node (one launch of the tiled
-stage kernel per stage).  Metric: million node-stage updates per second,
-nodes * 5 * steps / time.
+stage kernel per stage; the grid is a topography map, so the stage reads the 4
+metric fields of that path and its roofline counts 172 B per node-stage, 136 in
+the first stage).  Metric: million node-stage updates per second,
+nodes * 5 * steps / time.  The end-to-end figure moves every step's state in from
+and out to pinned host memory through the C ABI, with two or three grids taking
+the steps in turn so that copies and steps overlap.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
     python bench.py --workload adjoint129_o4 [--adj-steps N]

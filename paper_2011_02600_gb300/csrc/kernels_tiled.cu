@@ -27,7 +27,11 @@
 // chunk launch in groups of tile columns (swizzle_tiles) so that tiles sharing halos run
 // together and read them from L2.  The same kernel, templated on a pass kind, also runs
 // the two stencil passes of the discrete adjoint (L^T on yhat, the material gradient on
-// U_k) with their own epilogues.
+// U_k) with their own epilogues; the L^T pass of an adjoint step can also form the next
+// stage's pointwise prep (Wb and yhat) in its epilogue.  A second template argument selects
+// the metric storage: MAP 0 reads the nine metric components; MAP 1, for topography maps
+// (a_q and a_r along x and y only), reads a_q,x with both halos and a_s, and its forward
+// stage takes the RK register's tile in the same copy as the plane.
 #include "adjoint_terms.cuh"
 #include "common.cuh"
 #include "launch.h"
