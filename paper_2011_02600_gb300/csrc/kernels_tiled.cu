@@ -30,8 +30,8 @@
 // U_k) with their own epilogues; the L^T pass of an adjoint step can also form the next
 // stage's pointwise prep (Wb and yhat) in its epilogue.  A second template argument selects
 // the metric storage: MAP 0 reads the nine metric components; MAP 1, for topography maps
-// (a_q and a_r along x and y only), reads a_q,x with both halos and a_s, and its forward
-// stage takes the RK register's tile in the same copy as the plane.
+// (a_q and a_r along x and y only), reads a_q,x with both halos and a_s; MAP 2, the forward
+// stage on such maps, also takes the RK register's tile in the same copy as the plane.
 #include "adjoint_terms.cuh"
 #include "common.cuh"
 #include "launch.h"
@@ -62,7 +62,12 @@ struct Stage<T, 1> {
   T jq[BYH][BXH];  // a_q,x on the tile and both halos
   T as[3][TY][TX];
   T mat[3][TY][TX];
-  T dq[9][TY][TX];  // the RK register (stages 1-4 of the forward step; its last member)
+};
+// MAP 2: the topography map's forward stage, which also takes the RK register's tile with the
+// plane (stages 1-4 of a step); the adjoint passes keep MAP 1 and the smaller stage.
+template <typename T>
+struct Stage<T, 2> : Stage<T, 1> {
+  T dq[9][TY][TX];
 };
 
 // a_q at flux-tile row `row` (0..TY-1), smem column `col` (0..BXH-1); a_r at r-halo row `row`
@@ -95,21 +100,25 @@ __device__ __forceinline__ void ar_at(const Stage<T, 1>& st, int row, int col, T
   a[2] = T(0);
 }
 
-// The RK register at the thread's node from the tile copy (MAP 1 only).
+// The RK register at the thread's node from the tile copy (MAP 2 only).
 template <typename T>
 __device__ __forceinline__ T dq_at(const Stage<T, 0>&, int, int, int) {
   return T(0);
 }
 template <typename T>
-__device__ __forceinline__ T dq_at(const Stage<T, 1>& st, int f, int ty, int tx) {
+__device__ __forceinline__ T dq_at(const Stage<T, 1>&, int, int, int) {
+  return T(0);
+}
+template <typename T>
+__device__ __forceinline__ T dq_at(const Stage<T, 2>& st, int f, int ty, int tx) {
   return st.dq[f][ty][tx];
 }
 
-// Fluxes F_q = sigma a_q, F_r = sigma a_r and the strain rows of one axis; MAP 1 skips the
+// Fluxes F_q = sigma a_q, F_r = sigma a_r and the strain rows of one axis; MAP 1, 2 skip the
 // products with the components that vanish.
 template <int MAP, typename T>
 __device__ __forceinline__ void flux_q(const T a[3], const T s[6], T F[3]) {
-  if constexpr (MAP == 1) {
+  if constexpr (MAP >= 1) {
     F[0] = a[0] * s[0];
     F[1] = a[0] * s[3];
     F[2] = a[0] * s[4];
@@ -119,7 +128,7 @@ __device__ __forceinline__ void flux_q(const T a[3], const T s[6], T F[3]) {
 }
 template <int MAP, typename T>
 __device__ __forceinline__ void flux_r(const T a[3], const T s[6], T F[3]) {
-  if constexpr (MAP == 1) {
+  if constexpr (MAP >= 1) {
     F[0] = a[1] * s[3];
     F[1] = a[1] * s[1];
     F[2] = a[1] * s[5];
@@ -129,7 +138,7 @@ __device__ __forceinline__ void flux_r(const T a[3], const T s[6], T F[3]) {
 }
 template <int MAP, typename T>
 __device__ __forceinline__ void strain_q(const T a[3], const T dv[3], T e[6]) {
-  if constexpr (MAP == 1) {
+  if constexpr (MAP >= 1) {
     e[0] += a[0] * dv[0];
     e[3] += a[0] * dv[1];
     e[4] += a[0] * dv[2];
@@ -139,7 +148,7 @@ __device__ __forceinline__ void strain_q(const T a[3], const T dv[3], T e[6]) {
 }
 template <int MAP, typename T>
 __device__ __forceinline__ void strain_r(const T a[3], const T dv[3], T e[6]) {
-  if constexpr (MAP == 1) {
+  if constexpr (MAP >= 1) {
     e[1] += a[1] * dv[1];
     e[3] += a[1] * dv[0];
     e[5] += a[1] * dv[2];
@@ -165,13 +174,13 @@ struct TiledShared {
 template <typename T>
 constexpr int tiled_min_blocks() { return sizeof(T) == 4 ? 2 : 1; }
 
-// with_dq (MAP 1): the RK register's box comes with the plane (the last member of Stage<T, 1>).
+// with_dq (MAP 2): the RK register's box comes with the plane (the member Stage<T, 2> adds).
 template <typename T, int MAP>
 __device__ __forceinline__ void issue_plane(TiledShared<T, MAP>& S, int stage, const TmaSet& tm, int i0, int j0,
                                             int k, int member, bool with_dq) {
   unsigned long long* bar = &S.bar[stage];
   Stage<T, MAP>& st = S.st[stage];
-  if constexpr (MAP == 1) {
+  if constexpr (MAP == 2) {
     constexpr unsigned dq_bytes = (unsigned)sizeof(st.dq);
     mbar_expect_tx(bar, (unsigned)sizeof(Stage<T, MAP>) - (with_dq ? 0u : dq_bytes));
     if (with_dq) tma_load_4d(&st.dq[0][0][0], &tm.dq, i0, j0, k, 9 * member, bar);
@@ -180,7 +189,7 @@ __device__ __forceinline__ void issue_plane(TiledShared<T, MAP>& S, int stage, c
     mbar_expect_tx(bar, (unsigned)sizeof(Stage<T, MAP>));
   }
   tma_load_4d(&st.state[0][0][0], &tm.state, i0 - HX, j0 - HX, k, 9 * member, bar);
-  if constexpr (MAP == 1) {
+  if constexpr (MAP >= 1) {
     tma_load_4d(&st.jq[0][0], &tm.met_j, i0 - HX, j0 - HX, k, 0, bar);
   } else {
     tma_load_4d(&st.aq[0][0][0], &tm.met_q, i0 - HX, j0, k, 0, bar);
@@ -206,7 +215,7 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
   static_assert(Q <= HX && R <= HX, "halo too small");
   extern __shared__ __align__(128) unsigned char smem_raw[];
   TiledShared<T, MAP>& S = *reinterpret_cast<TiledShared<T, MAP>*>(smem_raw);
-  const T c_r = A.ar_ratio;  // MAP 1: a_r,y / a_q,x
+  const T c_r = A.ar_ratio;  // MAP 1, 2: a_r,y / a_q,x
 
   const Dims d = A.d;
   const long long fs = d.fs;
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(TX* TY, tiled_min_blocks<T>())
   if (q_edge && ty == 0) fill_q_rows<T, O>(S.qrows, tx, i0, ax.own0, ax.own1, d.nq);  // read after the first plane's barrier
   __syncthreads();
   // the topography-map variant's stages read the RK register from the tile copy
-  constexpr bool kDqTile = MAP == 1 && KIND == 0;
+  constexpr bool kDqTile = MAP == 2;
   const bool dq_tma = kDqTile && A.mode == kModeStage;
   if (tid == 0) issue_plane(S, 0, tm, i0, j0, kb, member, dq_tma);
   // closure-row sums of the s closure planes this chunk reaches (while the first copy flies)
@@ -667,12 +676,14 @@ cudaError_t launch_tiled_order(const StageArgs<T>& A, const TmaSet& tm, cudaStre
 template <typename T, int KIND>
 cudaError_t launch_kind(const StageArgs<T>& A, int order, const TmaSet& tm, cudaStream_t st) {
   if (!A.sclose) return cudaErrorInvalidValue;
-  // the stage and the adjoint passes on a topography map: 4 metric fields (upwind orders 2, 4, 6)
+  // the stage and the adjoint passes on a topography map: 4 metric fields (upwind orders 2, 4, 6);
+  // the forward stage also takes the RK register with the plane (MAP 2)
+  constexpr int kTopo = KIND == 0 ? 2 : 1;
   if (A.map == 1) {
     switch (order) {
-      case 2: return launch_tiled_order<T, 2, KIND, 1>(A, tm, st);
-      case 4: return launch_tiled_order<T, 4, KIND, 1>(A, tm, st);
-      case 6: return launch_tiled_order<T, 6, KIND, 1>(A, tm, st);
+      case 2: return launch_tiled_order<T, 2, KIND, kTopo>(A, tm, st);
+      case 4: return launch_tiled_order<T, 4, KIND, kTopo>(A, tm, st);
+      case 6: return launch_tiled_order<T, 6, KIND, kTopo>(A, tm, st);
       default: break;
     }
   }
