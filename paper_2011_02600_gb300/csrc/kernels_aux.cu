@@ -4,6 +4,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "topo_check.h"
 
 namespace sbp {
 
@@ -35,27 +36,15 @@ cudaError_t launch_metrics(const double* xyz, double* jmet, const Dims& d, int o
 }
 
 // ---------------------------------------------------------------------------
-// Is the map a topography map (x = L_x q, y = L_y r, z = z(q, r, s))?  Then a_q = x_r x x_s =
-// (L_y z_s, 0, 0) and a_r = x_s x x_q = (0, L_x z_s, 0) = (0, c a_q,x, 0) with c = L_x / L_y, up to
-// the rounding of D_c applied to the linear x and y.
+// Is the map a topography map (x = L_x q, y = L_y r, z = z(q, r, s))?  The largest deviation
+// over all nodes (topography_deviation in topo_check.h).
 __global__ void topography_check_kernel(const double* __restrict__ jmet, Dims d, double c,
                                         unsigned long long* dev) {
   const long long total = (long long)d.nq * d.nr * d.ns;
   double worst = 0.0;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t % d.nq);
-    const int j = (int)((t / d.nq) % d.nr);
-    const int k = (int)(t / ((long long)d.nq * d.nr));
-    const long long n0 = (long long)k * d.plane + (long long)j * d.ldq + i;
-    const double aqx = jmet[1 * d.fs + n0], aqy = jmet[2 * d.fs + n0], aqz = jmet[3 * d.fs + n0];
-    const double arx = jmet[4 * d.fs + n0], ary = jmet[5 * d.fs + n0], arz = jmet[6 * d.fs + n0];
-    const double off = fmax(fmax(fabs(aqy), fabs(aqz)), fmax(fabs(arx), fabs(arz))) / fabs(aqx);
-    const double ratio = fabs(ary - c * aqx) / fabs(ary);
-    double m = fmax(off, ratio);
-    if (!(m <= 1.0e300)) m = INFINITY;  // NaN or infinite: not a topography map
-    worst = fmax(worst, m);
-  }
+       t += (long long)gridDim.x * blockDim.x)
+    worst = fmax(worst, topography_deviation(jmet, d, c, t));
   for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
   if ((threadIdx.x & 31) == 0) atomicMax(dev, (unsigned long long)__double_as_longlong(worst));
 }
