@@ -185,3 +185,20 @@ def test_interface_face_validation(lib):
     _expect(1, L.sbp_set_interface, h, 6, None)
     _expect(5, L.sbp_interface_trace, h, 1, None, 0x1000, None)   # not bound
     L.sbp_destroy(h)
+
+
+def test_map_path_and_adjoint_step_checks_on_the_host(lib):
+    """The metric-path calls and the whole-step adjoint validate on the host: an unknown path is
+    refused, an unbound grid reports the general path and refuses the adjoint step, and the
+    Fourier-feature entry point checks its sizes before any launch."""
+    h = L.sbp_create_grid((20, 20, 20), 4, 32, [("free",)] * 6)
+    assert L.sbp_map_path(h) == L.SBP_MAP_GENERAL          # no material yet
+    _expect(1, L.sbp_set_map_path, h, 2)                    # TOPOGRAPHY is reported, not requested
+    _expect(1, L.sbp_set_map_path, h, -1)
+    L.sbp_set_map_path(h, L.SBP_MAP_GENERAL)
+    L.sbp_set_map_path(h, L.SBP_MAP_AUTO)
+    _expect(5, L.sbp_adjoint_step, h, 1e-3, 4096, 8192, 16384, 32768, 65536, 131072, None)   # before sbp_bind
+    L.sbp_destroy(h)
+    _expect(1, L.sbp_nn_fourier_features, None, 4096, 3, 8, 4, None)     # null input
+    _expect(1, L.sbp_nn_fourier_features, 4096, 8192, 0, 8, 4, None)     # no inputs
+    _expect(1, L.sbp_nn_fourier_features, 4096, 8192, 3, 8, 17, None)    # too many frequencies
