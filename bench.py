@@ -611,10 +611,11 @@ def main():
         # as many grids as fit (up to three): each stream's chain (upload, step, download) then
         # spans as many steps, and the copy engines and the SMs stay busy
         extra = []
-        footprint = (39 * s.fs + 2 * 9 * s.fs) * elem      # a grid's fields and its set-up buffers
+        # a grid's fields (39) and its set-up buffers (coordinates, metrics and material in FP64: 16)
+        footprint = (39 * elem + 16 * 8) * s.fs
         while len(extra) < 2:
             free, _total = torch.cuda.mem_get_info()
-            if free < 1.2 * footprint:
+            if free < footprint:     # (a failed set-up below also stops here)
                 break
             try:   # host memory for two more pinned state buffers, with room to spare
                 if os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") < 3 * 2 * nbytes:
@@ -626,7 +627,12 @@ def main():
                 nb_out = torch.empty(9 * s.fs, dtype=tdt, pin_memory=True)
             except Exception:
                 break
-            g2, _ = build_solver(cfg, precision=args.precision, device=f"cuda:{local}")
+            try:
+                g2, _ = build_solver(cfg, precision=args.precision, device=f"cuda:{local}")
+            except Exception:   # no room after all (the set-up's FP64 buffers): keep the grids so far
+                del nb_in, nb_out
+                torch.cuda.empty_cache()
+                break
             L.sbp_get_state(g2.h, nb_in, L.SBP_MEM_HOST, _stream())
             L.sbp_get_state(g2.h, nb_out, L.SBP_MEM_HOST, _stream())
             extra.append(g2)
