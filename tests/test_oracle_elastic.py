@@ -16,7 +16,9 @@ from workloads.geometry import make_map, node_coordinates
 from workloads.media import make_medium
 
 
-def _grid(order, nodes=(16, 17, 18), geometry="curvy", ext=(1.0, 1.2, 0.9)):
+def _grid(order, nodes=None, geometry="curvy", ext=(1.0, 1.2, 0.9)):
+    if nodes is None:   # order 8 needs 21 nodes per axis (two 8-row closures + its reach 5)
+        nodes = (16, 17, 18) if order <= 7 else (21, 22, 23)
     x, y, z = node_coordinates(make_map(geometry, ext), nodes)
     J, a = metrics(x, y, z, order)
     return x, y, z, J, a
@@ -51,7 +53,7 @@ def test_antisymmetry_lemma_pointwise():
         assert abs(val) < 1e-13
 
 
-@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7, 8])
 def test_semidiscrete_energy_without_penalties(order):
     """Theorem (semi-discrete energy): <Q, P~^-1 dQ/dt>_H = I(v^T T) before penalties."""
     x, y, z, J, a = _grid(order)
@@ -66,7 +68,7 @@ def test_semidiscrete_energy_without_penalties(order):
     assert abs(lhs - want) < 1e-12 * max(1.0, abs(want))
 
 
-@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7, 8])
 def test_free_surface_scheme_conserves_energy(order):
     """Theorem (free-surface procedure): d/dt ||Q||^2_HP = 0, i.e. <Q, P~^-1 dQ/dt>_H = 0
     for random Q, random medium, every face free, fully curvilinear mesh."""
@@ -80,7 +82,7 @@ def test_free_surface_scheme_conserves_energy(order):
     assert abs(inner_H(Q, rv, e, sch)) < 1e-14 * scale
 
 
-@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7, 8])
 def test_general_bc_energy_identity(order):
     """Theorem (general boundary conditions): <Q, P~^-1 dQ/dt>_H = F_luc + I(vhat^T That),
     with F_luc and the hat term evaluated separately, gamma in [-1, 1] per face."""
@@ -209,7 +211,7 @@ def test_polynomial_state_reproduces_continuous_equations(order):
         assert np.abs(got[c] - want[c]).max() < 1e-9 * scale, c
 
 
-@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("order", [2, 3, 4, 5, 6, 7, 8])
 def test_linearity(order):
     x, y, z, J, a = _grid(order)
     sch = Scheme(order, J.shape[::-1])
@@ -387,6 +389,15 @@ def test_interior_truncation_error_at_design_order(order, kind):
     e1 = _interior_truncation(order, 24, kind, "identity")
     e2 = _interior_truncation(order, 48, kind, "identity")
     assert math.log2(e1 / e2) > order - 0.1, (e1, e2)
+
+
+@pytest.mark.parametrize("kind", ["P", "S"])
+def test_interior_truncation_error_order8(kind):
+    """The same for order 8 (Table 1 with alpha_4 = -1/28): its closures reach 13 rows in, so
+    the grids are n = 32 and 64 (measured slope 7.98)."""
+    e1 = _interior_truncation(8, 32, kind, "identity")
+    e2 = _interior_truncation(8, 64, kind, "identity")
+    assert math.log2(e1 / e2) > 7.9, (e1, e2)
 
 
 @pytest.mark.parametrize("kind", ["P", "S"])

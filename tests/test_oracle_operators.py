@@ -78,7 +78,7 @@ def _exact(order, N):
     return op.upwind_pair_exact(order, N)
 
 
-ORDERS = [2, 3, 4, 5, 6, 7]   # even orders as the kernels use them; odd orders of the oracle (Table 1)
+ORDERS = [2, 3, 4, 5, 6, 7, 8]   # orders 2-7 as the kernels use them; order 8 in the oracle only (Table 1)
 
 
 @pytest.mark.parametrize("order", ORDERS)
@@ -261,3 +261,35 @@ def test_group_velocity_and_spurious_modes():
         frac = np.mean(np.diff(w) < 0)
         assert min_slope(w) <= -1 + 1e-6 and 0.35 <= frac <= 0.5 + 1e-9, (order, frac)
     assert abs(np.mean(np.diff(op.dispersion_traditional(2, k)) < 0) - 0.5) < 1e-4
+
+
+def test_order8_closure_norm_forced_and_order9_refused():
+    """Order 8 with b = 8: the weights follow from the closure-row accuracy conditions alone
+    (other values of the nine free entries give the same ones), integrate constants exactly
+    (sum b - 1/2), and every free entry of CLOSURE[8] lies in the 3 x 3 block of rows and
+    columns 5..7.  Order 9 has no closure and is refused."""
+    w = op.closure(8)[1]
+    assert sum(w) == 8 - Fr(1, 2) and min(w) > 0
+    assert set(op.CLOSURE[8]["free"]) == {(i, j) for i in range(5, 8) for j in range(5, 8)}
+    saved = op.CLOSURE[8]["free"]
+    try:
+        op.CLOSURE[8]["free"] = {k: Fr(0) for k in saved}
+        assert op.closure(8)[1] == w
+    finally:
+        op.CLOSURE[8]["free"] = saved
+    with pytest.raises(ValueError):
+        op.upwind_pair_exact(9, 40)
+
+
+def test_order8_closure_needs_the_corrected_table_sign():
+    """With alpha_4 = +1/28 as Table 1 prints it the interior stencil is inconsistent, so the
+    closure system built on it has no solution for the same free entries."""
+    alpha = op.interior_stencil(8)
+    assert alpha[4] == Fr(-1, 28)
+    bad = dict(alpha)
+    bad[4] = Fr(1, 28)
+    assert sum(bad.values()) == Fr(1, 14)
+    rows, rhs, nunk = op._accuracy_system(bad, 8, 4)
+    op._pin(rows, rhs, 8, nunk, op.CLOSURE[8]["free"])
+    with pytest.raises(ValueError, match="inconsistent"):
+        op._solve_exact(rows, rhs, nunk)
