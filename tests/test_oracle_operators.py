@@ -78,7 +78,7 @@ def _exact(order, N):
     return op.upwind_pair_exact(order, N)
 
 
-ORDERS = [2, 3, 4, 5, 6, 7, 8]   # orders 2-7 as the kernels use them; order 8 in the oracle only (Table 1)
+ORDERS = [2, 3, 4, 5, 6, 7, 8, 9]   # orders 2-7 as the kernels use them; 8 and 9 in the oracle only (Table 1)
 
 
 @pytest.mark.parametrize("order", ORDERS)
@@ -263,22 +263,23 @@ def test_group_velocity_and_spurious_modes():
     assert abs(np.mean(np.diff(op.dispersion_traditional(2, k)) < 0) - 0.5) < 1e-4
 
 
-def test_order8_closure_norm_forced_and_order9_refused():
-    """Order 8 with b = 8: the weights follow from the closure-row accuracy conditions alone
-    (other values of the nine free entries give the same ones), integrate constants exactly
-    (sum b - 1/2), and every free entry of CLOSURE[8] lies in the 3 x 3 block of rows and
-    columns 5..7.  Order 9 has no closure and is refused."""
-    w = op.closure(8)[1]
+@pytest.mark.parametrize("order", [8, 9])
+def test_order8_9_closure_norms_forced(order):
+    """Orders 8 and 9 with b = 8: the weights follow from the closure-row accuracy conditions
+    alone (other values of the nine free entries give the same ones), integrate constants
+    exactly (sum b - 1/2), and every free entry lies in the 3 x 3 block of rows and columns
+    5..7.  Order 10 is refused."""
+    w = op.closure(order)[1]
     assert sum(w) == 8 - Fr(1, 2) and min(w) > 0
-    assert set(op.CLOSURE[8]["free"]) == {(i, j) for i in range(5, 8) for j in range(5, 8)}
-    saved = op.CLOSURE[8]["free"]
+    assert set(op.CLOSURE[order]["free"]) == {(i, j) for i in range(5, 8) for j in range(5, 8)}
+    saved = op.CLOSURE[order]["free"]
     try:
-        op.CLOSURE[8]["free"] = {k: Fr(0) for k in saved}
-        assert op.closure(8)[1] == w
+        op.CLOSURE[order]["free"] = {k: Fr(0) for k in saved}
+        assert op.closure(order)[1] == w
     finally:
-        op.CLOSURE[8]["free"] = saved
+        op.CLOSURE[order]["free"] = saved
     with pytest.raises(ValueError):
-        op.upwind_pair_exact(9, 40)
+        op.upwind_pair_exact(10, 40)
 
 
 def test_order8_closure_needs_the_corrected_table_sign():
