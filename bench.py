@@ -44,6 +44,7 @@ WORKLOAD = "topo1025_o6_fp32"
 BYTES_PER_NODE_STAGE = 192        # 48 FP32 values per node per stage (algorithmic)
 BYTES_PER_NODE_STAGE0 = 156       # first stage: A_0 = 0, the RK register is not read
 NOMINAL_HBM_GBS = 7900.0          # HBM3e nominal, for the second fraction
+L2_BYTES = 129e6                  # L2 capacity: the bench inputs must exceed it (no flush between steps)
 FLOP_PER_NODE_STAGE = 444         # order 6, interior node, counted from the tiled kernel's arithmetic (an FMA
                                   # is 2): fluxes F_q, F_r on the tile and halo (1.19 + 1.75 per node) and F_s,
                                   # 15 each: 59; D- and D+ on 3 axes x 3 components, 7 taps and a scaling: 270;
@@ -295,6 +296,9 @@ def run_adjoint(args, local):
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     topo = s.map_path() == "topography"
     adj_bytes = ADJ_BYTES_PER_NODE_STAGE_TOPO if topo else ADJ_BYTES_PER_NODE_STAGE
+    # the forward stage kernel's bytes, averaged over the five stages (stage 0 reads no RK register)
+    stage_bytes = ((BYTES_PER_NODE_STAGE0_TOPO + 4 * BYTES_PER_NODE_STAGE_TOPO) / 5 if topo else
+                   (BYTES_PER_NODE_STAGE0 + 4 * BYTES_PER_NODE_STAGE) / 5)
     achieved = adj_bytes * nodes / (adj_avg / 1e3) / 1e9
     value = nodes * 5 * nsteps / ((t_fwd + t_grad) / 1e3) / 1e6
     line = {
@@ -306,6 +310,8 @@ def run_adjoint(args, local):
                    "checkpoint_every": p.C, "receivers": len(p.receivers), "sources": p.B,
                    "batch": "the sources' states advance together (one launch per kernel)",
                    "warmup": "one untimed forward run and gradient over the same steps",
+                   "l2": f"not flushed: each adjoint stage moves {adj_bytes * nodes / 1e9:.2f} GB, "
+                         f"{adj_bytes * nodes / L2_BYTES:.0f} x L2",
                    "what": "node-stages of the forward problem (nodes x sources x 5 x steps) per second of "
                            "forward run + gradient"},
         "forward_ms": t_fwd, "gradient_ms": t_grad, "misfit": phi,
@@ -319,7 +325,8 @@ def run_adjoint(args, local):
                      "avg_launch_ms": adj_avg, "launches": kn[2],
                      "peak_source": "measured" if peaks else "fallback"},
         "stage_kernel": {"avg_launch_ms": stage_avg, "launches": kn[0],
-                         "achieved_gbs": 184.8 * nodes / (stage_avg / 1e3) / 1e9},
+                         "achieved_gbs": stage_bytes * nodes / (stage_avg / 1e3) / 1e9,
+                         "algorithmic_bytes_per_node_stage": stage_bytes},
         "kernel_ms": {"tiled": kms[0], "general": kms[1], "adjoint": kms[2], "launches": kn},
         "clocks": clk, "gpu_launches": int(kn[0] + kn[1] + 2 * kn[2]),
     }
@@ -416,7 +423,10 @@ def run_surrogate_kernels(args, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "clocks": clk,
         "data": "synthetic",
         "config": {"workload": "surrogate97_o4 network", "batch": B, "samples": net.T, "outputs": net.n_out,
-                   "hidden": net.hidden, "channels": net.C, "params": net.n_params()},
+                   "hidden": net.hidden, "channels": net.C, "params": net.n_params(),
+                   "l2": (f"not flushed: the largest GEMM's operands and output ({(M * K + K * N + M * N) * 2 / 1e6:.0f}"
+                          " MB) stay in L2 across the graph's back-to-back launches; the product is bound by the "
+                          "tensor pipe, not by memory")},
         "ms_per_iteration": it_ms, "gemm_tflop_per_iteration": it_flops / 1e12,
         "gemm_tflops_in_iterations": it_flops / (it_ms / 1e3) / 1e12,
         "roofline": {"bound": "tensor", "kernel": "gemm_tc_kernel (TMA, tcgen05.mma kind::f16, TMEM accumulator, "
@@ -706,7 +716,9 @@ def main():
         "config": {"workload": WORKLOAD if not args.nodes else WORKLOAD + " (reduced: profiling only)",
                    "nodes": list(cfg.nodes), "order": cfg.order,
                    "extent_m": list(cfg.extent), "stages_per_step": 5, "dt_s": dt,
-                   "l2": "inputs larger than L2 (39 fields x 1.74 GB resident)",
+                   "l2": (f"inputs larger than L2 (39 fields x {s.fs * elem / 1e9:.2f} GB resident)"
+                          if 39 * s.fs * elem > L2_BYTES else
+                          f"inputs smaller than L2 (39 fields x {s.fs * elem / 1e6:.1f} MB): reduced case"),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof,
         "kernel_ms": {"tiled": kms[0], "general": kms[1], "launches": kn},
