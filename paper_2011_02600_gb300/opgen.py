@@ -17,8 +17,9 @@ upper-left b x b block of P and the first b entries of H are unknown.  The
 accuracy equations leave free entries (none for orders 2 and 3, one for orders
 4 and 5, four for orders 6 and 7); they are pinned to the values in
 FREE_ENTRIES, which keep P + P^T - B negative semi-definite and the spectral
-radius of D+ small.  The kernels are launched for orders 2, 4 and 6; the odd
-orders' tables are there for the kernel source's CPU checks.
+radius of D+ small.  The kernels are launched for all six orders and for the
+traditional operators of orders 2, 4 and 6 (Table 2); orders 8 and 9 reach 5
+nodes, more than the kernels' tile halo of 4, and have no tables here.
 
 This module is independent of any other implementation of the operators in
 the repository: it carries its own statement of Table 1 and its own exact
