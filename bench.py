@@ -28,6 +28,7 @@ workload instead.
 """
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -128,6 +129,45 @@ def max_over_ranks(x, dist, device="cpu"):
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def host_memory_share(local_world):
+    """Bytes of host memory this rank may pin: what the node has free now, split evenly among
+    the ranks on the node (they all pin at once); unlimited when the platform does not say."""
+    try:
+        avail = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    except (ValueError, OSError):
+        return math.inf
+    return avail / max(1, local_world)
+
+
+def e2e_record(nodes, world, nbytes, seq_ms, e_ms, grids, seq_steps, e_steps, note=None):
+    """The bench line's `e2e` object from the job's milliseconds per step (the slowest rank's;
+    inf where some rank has no number): the pipelined figure when every rank has one, else the
+    one-grid sequential figure, else none.  Each of the `world` ranks streams its own grid's
+    state of `nbytes` in and out every step, so the job moves world x nbytes each way."""
+    def rate(ms):
+        return world * nodes * 5 / (ms / 1e3) / 1e6
+    ranks = f" on each of the {world} ranks" if world > 1 else ""
+    if math.isfinite(e_ms) and math.isfinite(seq_ms):
+        rec = {"value": rate(e_ms), "unit": UNIT, "h2d_bytes_per_step": world * nbytes,
+               "d2h_bytes_per_step": world * nbytes, "ms_per_step": e_ms, "steps": e_steps, "grids": grids,
+               "what": "per step, all through the C ABI: sbp_set_state from pinned host memory (the 9-field "
+                       f"state in the grid layout), sbp_step_n(1), sbp_get_state to pinned host memory{ranks}; "
+                       f"{grids} grids on {grids} streams take the steps in turn (one grid's download, another's "
+                       "upload and a step overlap)",
+               "sequential_one_grid": {"value": rate(seq_ms), "ms_per_step": seq_ms, "steps": seq_steps}}
+    elif math.isfinite(seq_ms):
+        rec = {"value": rate(seq_ms), "unit": UNIT, "h2d_bytes_per_step": world * nbytes,
+               "d2h_bytes_per_step": world * nbytes, "ms_per_step": seq_ms, "steps": seq_steps,
+               "what": "per step, all through the C ABI on one grid: sbp_set_state from pinned host memory, "
+                       f"sbp_step_n(1), sbp_get_state to pinned host memory (waited for){ranks}"}
+    else:
+        return {"value": None, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "error": note or "no end-to-end time"}
+    if note:
+        rec["note"] = note
+    return rec
 
 
 _BARRIER = None
@@ -598,11 +638,17 @@ def main():
     # (sbp_get_state).  Two or three grids on as many streams take the steps in turn, so that one
     # grid's download, another's upload and a step overlap (independent problems streamed through
     # the device); every step still moves its whole state in and out.  The same sequence on one
-    # grid, each download waited for, is reported beside it.
-    e2e = None
-    seq_ms = None
+    # grid, each download waited for, is reported beside it.  Every rank runs this leg on its own
+    # grids; the job's time is the slowest rank's, and the ranks on a node share its host memory.
+    seq_ms, e_ms, ng, e_steps, note = None, None, 1, 0, None
     nbytes = 9 * s.fs * elem
+    if dist:
+        dist.barrier()   # every rank reads the free host memory before any of them pins some
+    host_share = host_memory_share(int(os.environ.get("LOCAL_WORLD_SIZE", "1")))
     try:
+        if host_share < 2 * 2 * nbytes:   # one pair of state buffers, with room to spare
+            raise RuntimeError(f"{host_share / 1e9:.0f} GB of free host memory per rank: too little to pin "
+                               f"two {nbytes / 1e9:.1f} GB state buffers")
         tdt = torch.float32 if elem == 4 else torch.float64
         host_in = [torch.empty(9 * s.fs, dtype=tdt, pin_memory=True)]
         host_out = [torch.empty(9 * s.fs, dtype=tdt, pin_memory=True)]
@@ -627,11 +673,9 @@ def main():
             free, _total = torch.cuda.mem_get_info()
             if free < footprint:     # (a failed set-up below also stops here)
                 break
-            try:   # host memory for two more pinned state buffers, with room to spare
-                if os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") < 3 * 2 * nbytes:
-                    break
-            except (ValueError, OSError):
-                pass
+            # host memory for this rank's pairs with the new one, and room for two more
+            if host_share < (len(extra) + 4) * 2 * nbytes:
+                break
             try:
                 nb_in = torch.empty(9 * s.fs, dtype=tdt, pin_memory=True)
                 nb_out = torch.empty(9 * s.fs, dtype=tdt, pin_memory=True)
@@ -678,25 +722,17 @@ def main():
         ev[1].record(stream)
         torch.cuda.synchronize()
         e_ms = ev[0].elapsed_time(ev[1]) / nsteps
-        e2e = {"value": nodes * 5 / (e_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-               "d2h_bytes_per_step": nbytes, "ms_per_step": e_ms, "steps": nsteps, "grids": ng,
-               "what": "per step, all through the C ABI: sbp_set_state from pinned host memory (the 9-field "
-                       f"state in the grid layout), sbp_step_n(1), sbp_get_state to pinned host memory; {ng} grids "
-                       f"on {ng} streams take the steps in turn (one grid's download, another's upload and a "
-                       "step overlap)",
-               "sequential_one_grid": {"value": nodes * 5 / (seq_ms / 1e3) / 1e6, "ms_per_step": seq_ms,
-                                       "steps": args.e2e_steps}}
+        e_steps = nsteps
         del host_in, host_out, extra
     except Exception as ex:  # pinned memory or a second grid's device memory can be unavailable
-        if seq_ms is not None:
-            e2e = {"value": nodes * 5 / (seq_ms / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
-                   "d2h_bytes_per_step": nbytes, "ms_per_step": seq_ms, "steps": args.e2e_steps,
-                   "what": "per step, all through the C ABI on one grid: sbp_set_state from pinned host memory, "
-                           "sbp_step_n(1), sbp_get_state to pinned host memory (waited for)",
-                   "note": str(ex)[:200]}
-        else:
-            e2e = {"value": None, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
-                   "error": str(ex)[:200]}
+        note = str(ex)[:200]
+        if e_ms is None:
+            ng = 1
+    # the job's times are the slowest rank's (a rank without a number counts as infinitely slow)
+    seq_job = max_over_ranks(math.inf if seq_ms is None else seq_ms, dist, dev)
+    e_job = max_over_ranks(math.inf if e_ms is None else e_ms, dist, dev)
+    ng_job = -max_over_ranks(-ng, dist, dev)   # the fewest grids any rank streamed through
+    e2e = e2e_record(nodes, world, nbytes, seq_job, e_job, int(ng_job), args.e2e_steps, e_steps, note)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
