@@ -12,7 +12,7 @@ none of the method's arithmetic.
 
 Modules
   operators  exact rational upwind SBP dual pairs of orders 2 to 9 (Section 4.1,
-             Table 1) and the traditional central operators of orders 2, 4, 6
+             Table 1) and the traditional central operators of orders 2, 4, 6, 8
              (Table 2)
   rk         Carpenter-Kennedy 2N-storage RK4 (cited in Sections 1 and 7)
   metrics    Jacobian and metric terms (Section 2.2)

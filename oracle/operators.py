@@ -306,11 +306,15 @@ def upwind_pair(order, N, length=1.0):
 
 
 # Traditional (central) diagonal-norm SBP operators of Table 2: closure width b and the chosen
-# values of the free entries of M = H D (upper-left block).
+# values of the free entries of M = H D (upper-left block).  Order 8 (b = 8, boundary accuracy 4)
+# leaves three entries free and forces the norm; they were chosen (numerically, once) where the
+# spectral radius of D stays at the interior stencil's 1.73 for N = 20 to 101.  That radius is
+# sensitive to them (rounding to denominators of 100 gives 2 to 4.6), hence denominators of 500.
 TRADITIONAL = {
     2: dict(b=1, free={}),
     4: dict(b=4, free={}),
     6: dict(b=6, free={(4, 2): Fr(-1, 10)}),
+    8: dict(b=8, free={(6, 5): Fr(-299, 500), (7, 5): Fr(41, 500), (7, 6): Fr(-187, 250)}),
 }
 
 
@@ -358,7 +362,7 @@ def traditional_exact(order, N):
     """(H, D, M, B) of the traditional operator on N nodes, unit spacing, as Fractions:
     D = H^-1 M with M + M^T = B."""
     if order not in TRADITIONAL:
-        raise ValueError("traditional closures are built for orders 2, 4, 6")
+        raise ValueError("traditional closures are built for orders 2, 4, 6, 8")
     if N < traditional_min_nodes(order):
         raise ValueError(f"order {order} needs at least {traditional_min_nodes(order)} nodes")
     Mc, w = traditional_closure(order)

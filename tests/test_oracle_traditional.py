@@ -2,7 +2,7 @@
 them, the operator the paper sets against the upwind pair:
 
 * the diagonal norms are the classical ones of central diagonal-norm SBP operators of orders
-  2, 4, 6 (boundary accuracy 1, 2, 3), exactly;
+  2, 4, 6, 8 (boundary accuracy 1, 2, 3, 4), exactly;
 * H D + D^T H = B and zero dissipation M + M^T = B (Section 4.1 with D- = D+), exactly;
 * accuracy of every row (Eq. acc), the mirror relation, a positive norm, the sparse builder;
 * the scheme with every face free conserves the discrete energy, as the upwind one does;
@@ -23,19 +23,43 @@ from oracle.metrics import metrics
 from workloads.fields import random_state
 from workloads.geometry import make_map, node_coordinates
 
-ORDERS = [2, 4, 6]
+ORDERS = [2, 4, 6, 8]
 
-# Classical diagonal norms of the central SBP operators of interior order 2, 4, 6.
+# Classical diagonal norms of the central SBP operators of interior order 2, 4, 6, 8.
 CLASSICAL_NORMS = {
     2: [Fr(1, 2)],
     4: [Fr(17, 48), Fr(59, 48), Fr(43, 48), Fr(49, 48)],
     6: [Fr(13649, 43200), Fr(12013, 8640), Fr(2711, 4320), Fr(5359, 4320), Fr(7877, 8640), Fr(43801, 43200)],
+    8: [Fr(1498139, 5080320), Fr(1107307, 725760), Fr(20761, 80640), Fr(1304999, 725760),
+        Fr(299527, 725760), Fr(103097, 80640), Fr(670091, 725760), Fr(5127739, 5080320)],
 }
 
 
 @pytest.mark.parametrize("order", ORDERS)
 def test_norms_are_the_classical_ones(order):
     assert op.traditional_closure(order)[1] == CLASSICAL_NORMS[order]
+
+
+def test_order_8_norm_is_forced():
+    """Order 8 with b = 8: three entries of the corner block are free, the norm is not."""
+    saved = op.TRADITIONAL[8]["free"]
+    assert set(saved) == {(6, 5), (7, 5), (7, 6)}
+    try:
+        op.TRADITIONAL[8]["free"] = {k: Fr(0) for k in saved}
+        w_other = op.traditional_closure(8)[1]
+    finally:
+        op.TRADITIONAL[8]["free"] = saved
+    assert w_other == CLASSICAL_NORMS[8]
+
+
+def test_order_8_spectral_radius_at_the_interior_level():
+    """The chosen free entries keep the spectral radius of D at the interior stencil's maximum
+    of |omega| (Eq. dispersion_relation_traditional) on small and large grids."""
+    interior = op.dispersion_traditional(8, np.linspace(0, np.pi, 4001)).max()
+    for N in (20, 41, 101):
+        _, D = op.traditional_op(8, N, length=float(N - 1))
+        rho = np.abs(np.linalg.eigvals(D.toarray())).max()
+        assert rho <= interior * 1.01, (N, rho, interior)
 
 
 def test_orders_2_and_4_are_unique_and_the_order_6_norm_is_forced():
@@ -89,7 +113,7 @@ def test_sparse_builder_equals_exact(order):
 
 @pytest.mark.parametrize("order", ORDERS)
 def test_traditional_scheme_conserves_energy_with_free_surfaces(order):
-    nodes = (16, 17, 18)
+    nodes = (16, 17, 18) if order <= 6 else (21, 22, 23)
     X = node_coordinates(make_map("curvy", (1.0, 1.2, 0.9)), nodes)
     J, a = metrics(*X, order)
     rng = np.random.default_rng(3)
@@ -118,10 +142,11 @@ def test_grid_scale_mode_standing_for_traditional_moving_for_upwind(order, omega
 def test_interior_truncation_at_design_order(order):
     """Interior accuracy of Table 2's stencil: the whole right-hand side's local truncation error
     for an exact oblique plane wave falls as h^order away from the faces (measured 2.00, 3.99,
-    5.99 between n = 24 and 48)."""
+    5.99 between n = 24 and 48; order 8, 7.98 between 32 and 64, its closures being wider)."""
     from test_oracle_elastic import _interior_truncation
-    e1 = _interior_truncation(order, 24, "P", "identity", operator="traditional")
-    e2 = _interior_truncation(order, 48, "P", "identity", operator="traditional")
+    n = 24 if order <= 6 else 32
+    e1 = _interior_truncation(order, n, "P", "identity", operator="traditional")
+    e2 = _interior_truncation(order, 2 * n, "P", "identity", operator="traditional")
     assert np.log2(e1 / e2) > order - 0.1, (e1, e2)
 
 
