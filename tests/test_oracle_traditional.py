@@ -7,8 +7,8 @@ them, the operator the paper sets against the upwind pair:
 * accuracy of every row (Eq. acc), the mirror relation, a positive norm, the sparse builder;
 * the scheme with every face free conserves the discrete energy, as the upwind one does;
 * the grid-scale mode (-1)^j: the traditional D annihilates it inside the grid (a standing
-  spurious mode), the upwind D+ maps it to (-1)^j omega(pi) / h with omega(pi) = 4, 8/3, 32/15
-  (Section 6.2, Eq. dispersion_relation_upwind against Eq. dispersion_relation_traditional);
+  spurious mode), the upwind D+ maps it to (-1)^j omega(pi) / h with omega(pi) = 4, 8/3, 32/15,
+  64/35 (Section 6.2, Eq. dispersion_relation_upwind against Eq. dispersion_relation_traditional);
 * on a marginally resolved pulse, the traditional scheme and the odd upwind orders leave
   several times more error behind the pulse than the even upwind orders (Sections 6.2, 7.2),
   orders 4 to 9.
@@ -127,7 +127,10 @@ def test_traditional_scheme_conserves_energy_with_free_surfaces(order):
     assert abs(inner_H(Q, rv, e, sch)) < 1e-14 * scale
 
 
-@pytest.mark.parametrize("order,omega_pi", [(2, Fr(4)), (4, Fr(8, 3)), (6, Fr(32, 15))])
+# omega(pi) = |sum_j alpha_j (-1)^j| of Table 1 (Eq. dispersion_relation_upwind at k = pi): 4, 8/3,
+# 32/15; for order 8, by hand from the table with alpha_4 = -1/28, (5 + 60 + 420 - 378 - 1050
+# - 420 - 140 - 30 - 3)/840 = -64/35.
+@pytest.mark.parametrize("order,omega_pi", [(2, Fr(4)), (4, Fr(8, 3)), (6, Fr(32, 15)), (8, Fr(64, 35))])
 def test_grid_scale_mode_standing_for_traditional_moving_for_upwind(order, omega_pi):
     N = 40
     f = [Fr((-1) ** j) for j in range(N)]
