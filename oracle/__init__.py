@@ -23,6 +23,8 @@ Modules
   surrogate_net  the surrogate network in FP64 (with optional BF16 rounding points)
   source     discrete moment-tensor point source (Section 7.1)
   solver     time loop, receivers, energy history
+  closure_search  how the free closure entries of upwind orders 8, 9 and traditional
+             order 8 were chosen (run by hand; its output is in operators' tables)
 
 Where the paper is silent, garbled or ambiguous, the reading taken is stated
 in the docstring of the function that depends on it.

@@ -44,8 +44,8 @@ by tests/test_oracle_operators.py):
 * Order 8 (Table 1 with alpha_4 = -1/28) takes b = 8, closure accuracy p = 4.
   The accuracy conditions fix the eight weights and all of M's corner block
   but the 3 x 3 sub-block of rows and columns 5..7, whose nine entries are
-  free.  They were chosen by a numerical search inside the solution set of
-  the accuracy system (minimise the largest nonzero eigenvalue of
+  free.  They were chosen by a numerical search (oracle/closure_search.py)
+  inside the solution set of the accuracy system (minimise the largest nonzero eigenvalue of
   M + M^T - B, then the spectral radius of D+, with H > 0), rounded to
   denominators up to 10^5 and checked exactly.  Coarser rounding (10^4)
   breaks the semi-definiteness.  Its spectral radius (1.75 at N = 61) sits
@@ -307,9 +307,9 @@ def upwind_pair(order, N, length=1.0):
 
 # Traditional (central) diagonal-norm SBP operators of Table 2: closure width b and the chosen
 # values of the free entries of M = H D (upper-left block).  Order 8 (b = 8, boundary accuracy 4)
-# leaves three entries free and forces the norm; they were chosen (numerically, once) where the
-# spectral radius of D stays at the interior stencil's 1.73 for N = 20 to 101.  That radius is
-# sensitive to them (rounding to denominators of 100 gives 2 to 4.6), hence denominators of 500.
+# leaves three entries free and forces the norm; they were chosen (oracle/closure_search.py)
+# where the spectral radius of D stays at the interior stencil's 1.73 for N = 20 to 101.  That
+# radius is sensitive to them (rounding to denominators of 100 gives 2 to 4.6), hence 500.
 TRADITIONAL = {
     2: dict(b=1, free={}),
     4: dict(b=4, free={}),

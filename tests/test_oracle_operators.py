@@ -294,3 +294,18 @@ def test_order8_closure_needs_the_corrected_table_sign():
     op._pin(rows, rhs, 8, nunk, op.CLOSURE[8]["free"])
     with pytest.raises(ValueError, match="inconsistent"):
         op._solve_exact(rows, rhs, nunk)
+
+
+def test_closure_search_rounding_check_accepts_the_tables_and_rejects_a_coarse_rounding():
+    """oracle/closure_search.py (how the order-8 and 9 entries were chosen): its exact check
+    accepts the tables' entries and rejects order 8's entries rounded to 10^-4, the rounding that
+    breaks semi-definiteness; the free entries it finds are the 3 x 3 block of rows 5..7."""
+    from oracle import closure_search as cs
+    for order, den in ((8, 100000), (9, 1000000)):
+        vals = {ij: float(v) for ij, v in op.CLOSURE[order]["free"].items()}
+        assert set(cs._free_entries(op.interior_stencil(order), 8, 4)) == set(vals)
+        [(d, fr, ok, rho)] = cs.round_upwind(order, vals, [den])
+        assert ok and fr == op.CLOSURE[order]["free"] and rho < 1.85
+    vals8 = {ij: float(v) for ij, v in op.CLOSURE[8]["free"].items()}
+    [(_, _, ok, _)] = cs.round_upwind(8, vals8, [10000])
+    assert not ok
